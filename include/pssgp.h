@@ -1,0 +1,214 @@
+/*
+ * pssgp.h -- C ABI of libpssgp: the parallel (associative-scan) Kalman filter,
+ * RTS smoother and log marginal likelihood of a stationary temporal Gaussian
+ * process in state-space form, with missing measurements at the prediction
+ * times, in FP64 on one NVIDIA B300 (sm_103a).
+ *
+ * Method: Corenflos, Zhao, Sarkka, "Temporal Gaussian Process Regression in
+ * Logarithmic Time".  Section, equation and proposition references below are
+ * to that paper and its supplement.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns an int status: 0 (PSSGP_OK) or a negative value
+ *    for an argument error detected on the host before anything is launched.
+ *    Errors detected on the device are OR-ed into a status word kept in the
+ *    workspace (positive bits below), cleared at the start of every call and
+ *    read back with pssgp_get_status.
+ *  - Array pointers are DEVICE pointers owned by the caller unless stated
+ *    otherwise; the library never allocates, frees or retains them.  All
+ *    scratch memory is a caller-provided device workspace `ws` (256-byte
+ *    aligned) of at least pssgp_workspace_size(d, n) bytes.
+ *  - Every device entry point is asynchronous on the CUDA stream `stream`
+ *    (a cudaStream_t passed as void*, NULL = legacy default stream).  Two
+ *    calls that share a workspace must not overlap on the GPU.
+ *  - Time steps are indexed k = 0..n-1 (the paper's k = 1..n).  Times must be
+ *    non-decreasing; equal times are allowed (zero-length step).
+ *  - Per-step state outputs use an entry-major ("struct of arrays") layout
+ *    with leading dimension ld >= n: entry e of step k is at [e * ld + k].
+ *    Symmetric d x d matrices are stored packed, upper triangle row by row:
+ *    entry (i, j), i <= j, has index i*d - i*(i-1)/2 + (j - i).
+ *  - State vectors and covariances are reported in the coordinates of the
+ *    model's SDE (Sec. 4.2 balancing is internal).
+ *  - State dimension 1 <= d <= PSSGP_DMAX.  Measurements are scalar,
+ *    y_k = H x(t_k) + e_k, e_k ~ N(0, R_k) with R_k > 0 (Eq. (gp-def)).
+ */
+#ifndef PSSGP_H
+#define PSSGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PSSGP_DMAX 8
+
+/* ---- status codes ------------------------------------------------------ */
+#define PSSGP_OK 0
+#define PSSGP_EINVAL (-1)      /* null pointer, n < 1, ld < n, bad flag       */
+#define PSSGP_EDIM (-2)        /* d outside 1..PSSGP_DMAX                      */
+#define PSSGP_EKERNEL (-3)     /* unknown kernel kind or invalid hyperparameter */
+#define PSSGP_EWORKSPACE (-4)  /* workspace too small or misaligned            */
+#define PSSGP_ECUDA (-5)       /* a CUDA runtime call failed                   */
+#define PSSGP_EMODEL (-6)      /* model formation failed (Lyapunov/roots)      */
+/* device-detected errors, OR-ed into the workspace status word */
+#define PSSGP_ENAN 1           /* non-finite time or observed y                 */
+#define PSSGP_EUNSORTED 2      /* times decrease somewhere                      */
+#define PSSGP_ENOTPD 4         /* innovation variance or a pivot <= 0 / singular */
+
+/* ---- model ------------------------------------------------------------- */
+#define PSSGP_MATERN12 1
+#define PSSGP_MATERN32 2
+#define PSSGP_MATERN52 3
+#define PSSGP_RBF 4            /* Taylor approximation of the spectral density */
+
+typedef struct pssgp_kernel {
+  int32_t kind;          /* PSSGP_MATERN12 / 32 / 52 / PSSGP_RBF             */
+  int32_t order;         /* RBF Taylor order n (state dimension d = n), 1..8 */
+  double lengthscale;    /* > 0                                              */
+  double variance;       /* > 0 (sigma^2 of the covariance function)         */
+  int32_t balance;       /* 1: Sec. 4.2 diagonal balancing, 0: none          */
+  int32_t reserved;
+} pssgp_kernel;
+
+/* Number of Taylor coefficients kept per matrix entry for the on-device
+ * discretisation (see pssgp_model.fc / qc). */
+#define PSSGP_NTAYLOR 16
+
+/* Host-side model: the continuous SDE of Eq. (ssmodel) in balanced
+ * coordinates z = D^{-1} x (Sec. 4.2), with the stationary covariance of
+ * Sec. 4.1 and the tables the device discretisation uses.  Filled by
+ * pssgp_model_build or pssgp_model_from_sde; plain data, copyable. */
+typedef struct pssgp_model {
+  int32_t d;
+  int32_t kind;                          /* as pssgp_kernel.kind, 0 for a user SDE */
+  double G[PSSGP_DMAX * PSSGP_DMAX];     /* drift, balanced, row-major d x d    */
+  double W[PSSGP_DMAX * PSSGP_DMAX];     /* L q L^T, balanced                  */
+  double Pinf[PSSGP_DMAX * PSSGP_DMAX];  /* stationary covariance, balanced    */
+  double D[PSSGP_DMAX];                  /* x = D z; then H = e_0^T            */
+  double gnorm;                          /* ||G||_1, balanced                  */
+  /* Taylor tables (row-major entry e = i*d+j):
+   *   F_e(h) = sum_m fc[e*PSSGP_NTAYLOR + m] h^m            (G^m / m!)
+   *   Q_e(h) = h * sum_m qc[e*PSSGP_NTAYLOR + m] h^m         (W_{m+1} / (m+1)!,
+   *            W_1 = W, W_{m+1} = G W_m + W_m G^T)
+   * valid for gnorm * h <= theta_max; longer steps are halved and doubled. */
+  double fc[PSSGP_DMAX * PSSGP_DMAX * PSSGP_NTAYLOR];
+  double qc[PSSGP_DMAX * PSSGP_DMAX * PSSGP_NTAYLOR];
+  double theta_max;
+  float kthr_f[PSSGP_NTAYLOR + 1];       /* largest theta for which m terms suffice */
+  float kthr_q[PSSGP_NTAYLOR + 1];
+  double lengthscale, variance;          /* metadata                            */
+} pssgp_model;
+
+/* Kernel -> SDE (G, L, q, H) (Sec. 2: exact for Matern nu = 1/2, 3/2, 5/2;
+ * order-n Taylor approximation of the RBF spectral density followed by
+ * spectral factorisation), stationary covariance by the vectorised Lyapunov
+ * solve (Sec. 4.1), optional balancing (Sec. 4.2), discretisation tables.
+ * Host only.  Returns PSSGP_EKERNEL for bad hyperparameters, PSSGP_EDIM for
+ * an RBF order outside 1..8, PSSGP_EMODEL if the factorisation or the
+ * Lyapunov solve fails. */
+int pssgp_model_build(const pssgp_kernel* kernel, pssgp_model* out);
+
+/* Same from an explicit SDE dx = G x dt + L dw, E[w w^T] = q, y = H x + e
+ * (Eq. (ssmodel)).  Host pointers, G row-major d x d, L and H length d.
+ * H must be a multiple of the first unit vector (H = h0 e_0^T, h0 != 0). */
+int pssgp_model_from_sde(int32_t d, const double* G, const double* L, double q,
+                         const double* H, int32_t balance, pssgp_model* out);
+
+/* ---- workspace --------------------------------------------------------- */
+/* Bytes of device workspace for a call on n merged steps with state
+ * dimension d (valid for every entry point below with the same n, d). */
+size_t pssgp_workspace_size(int32_t d, int64_t n);
+
+/* Copies the device status word of the last call that used `ws` to *status,
+ * synchronising `stream`.  Returns PSSGP_ECUDA on a CUDA error. */
+int pssgp_get_status(void* ws, void* stream, int32_t* status);
+
+/* ---- merge (Sec. 4.3) -------------------------------------------------- */
+/* Inserts the M sorted prediction times into the N sorted training times as
+ * missing measurements (stable: a training time precedes an equal prediction
+ * time).  Outputs (device, length N+M): t, y (0 at prediction steps), mask
+ * (1 observed, 0 missing); test_pos[j] = merged index of prediction j.
+ * Unsorted input sets PSSGP_EUNSORTED, non-finite times PSSGP_ENAN.  The
+ * workspace only carries the status word (>= 256 bytes). */
+int pssgp_merge(const double* t_train, const double* y_train, int64_t N,
+                const double* t_test, int64_t M,
+                double* t, double* y, uint8_t* mask, int64_t* test_pos,
+                void* ws, size_t ws_bytes, void* stream);
+
+/* ---- discretisation (supplement Eq. (ss-gp-formation)) ------------------ */
+/* For each step k: F_k = exp(G (t_k - t_{k-1})), Q_k = int_0^h e^{(h-s)G} W
+ * e^{(h-s)G}^T ds, k >= 1; F_0 = 0, Q_0 = P_inf (the prior at the first time).
+ * F: d*d entries x ld (entry i*d+j), Q: packed d(d+1)/2 x ld, in SDE
+ * coordinates.  The workspace only carries the status word (>= 256 bytes). */
+int pssgp_discretize(const pssgp_model* model, const double* t, int64_t n,
+                     double* F, double* Q, int64_t ld,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* ---- filter (Sec. 3, Prop. 1) ------------------------------------------ */
+/* Parallel Kalman filter: elements (A, b, C, eta, J) with missing
+ * measurements (Sec. 3), combined by the filtering operator in a two-level
+ * parallel scan; x_k = b*_k, P_k = C*_k (Prop. 1).  mask[k] = 0 marks a
+ * missing measurement.  R: device pointer to one noise variance (R_per_step
+ * = 0) or n of them (R_per_step = 1).  Outputs (nullable): xf d x ld,
+ * Pf packed x ld, loglik (one device double, the log marginal likelihood by
+ * prediction-error decomposition over the observed steps). */
+int pssgp_filter(const pssgp_model* model, const double* t, const double* y,
+                 const uint8_t* mask, const double* R, int32_t R_per_step,
+                 int64_t n, double* xf, double* Pf, int64_t ld, double* loglik,
+                 void* ws, size_t ws_bytes, void* stream);
+
+/* ---- smoother (supplement Prop. 2) ------------------------------------- */
+/* Parallel RTS smoother from the filter outputs xf, Pf (as written by
+ * pssgp_filter, same ld): elements (E, g, L), reverse two-level scan of the
+ * smoothing operator; m^s_k = g*_k, P^s_k = L*_k.  Outputs (nullable):
+ * f_mean[k] = H m^s_k, f_var[k] = H P^s_k H^T (length n), xs d x ld,
+ * Ps packed x ld. */
+int pssgp_smooth(const pssgp_model* model, const double* t,
+                 const double* xf, const double* Pf, int64_t n, int64_t ld,
+                 double* f_mean, double* f_var, double* xs, double* Ps,
+                 void* ws, size_t ws_bytes, void* stream);
+
+/* ---- log marginal likelihood (Sec. 2, parameter estimation) ------------- */
+/* The filter's log-likelihood only (no per-step output). */
+int pssgp_loglik(const pssgp_model* model, const double* t, const double* y,
+                 const uint8_t* mask, const double* R, int32_t R_per_step,
+                 int64_t n, double* loglik, void* ws, size_t ws_bytes, void* stream);
+
+/* ---- fused prediction path (Sec. 4.4, stages 4-5) ---------------------- */
+/* merge -> discretise -> parallel filter -> parallel smoother -> gather, with
+ * the smoother elements produced inside the filter pass.  Inputs: N sorted
+ * training times/observations, M sorted prediction times, scalar noise
+ * variance R (host value, > 0).  Outputs (device, length M): posterior mean
+ * and variance of f at the prediction times; loglik (nullable, one device
+ * double) of the training data.  Workspace: pssgp_workspace_size(d, N+M). */
+int pssgp_predict(const pssgp_model* model, const double* t_train,
+                  const double* y_train, int64_t N, const double* t_test,
+                  int64_t M, double R, double* mean_test, double* var_test,
+                  double* loglik, void* ws, size_t ws_bytes, void* stream);
+
+/* ---- diagnostics ------------------------------------------------------- */
+/* Chunk aggregates of the filter's first scan level, for tests: runs the
+ * filter on (t, y, mask, R) with `lanes` lanes (a multiple of 128, 0 =
+ * automatic) and copies lane c's within-chunk aggregate (A, b, C, eta, J in SDE
+ * coordinates, row-major d x d / d, 3 d^2 + 2 d doubles) to the HOST array
+ * agg + c*(3d^2+2d), and chunk c's first step to first[c] (host), after
+ * synchronising.  Needs pssgp_workspace_size(d, n) + lanes*(2d^2+3d)*8 bytes
+ * of workspace.  The lane count used is returned in *lanes_out. */
+int pssgp_debug_filter_aggregates(const pssgp_model* model, const double* t,
+                                  const double* y, const uint8_t* mask,
+                                  const double* R, int64_t n, int32_t lanes,
+                                  double* agg, int64_t* first, int32_t* lanes_out,
+                                  void* ws, size_t ws_bytes, void* stream);
+
+/* Measured FP64 fused-multiply-add rate of this device (lane FMAs per
+ * second) from a short kernel with independent FMA chains on all SMs: the
+ * denominator of the FP64 roofline.  Synchronous; allocates a small probe
+ * buffer of its own. */
+int pssgp_fp64_fma_rate(double* fma_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSSGP_H */
