@@ -1,0 +1,503 @@
+// scan_ops.cuh -- the parallel filter / smoother algebra of Corenflos, Zhao,
+// Sarkka, "Temporal Gaussian Process Regression in Logarithmic Time", as
+// per-thread register code.
+//
+// Coordinates: everything on the device is in the balanced basis z = D^{-1} x
+// of Sec. 4.2 scaled so that the measurement row is H = e_0^T; then
+// S = P_00 + R and K = P[:,0] / S need no multiplication by H.
+#pragma once
+#include "linalg.cuh"
+
+namespace pssgp {
+
+constexpr int NT = 16;          // Taylor coefficients per entry (pssgp.h: PSSGP_NTAYLOR)
+
+template <int D> struct Sym { static constexpr int N = D * (D + 1) / 2; };
+template <int D>
+__host__ __device__ constexpr int pidx(int i, int j) {   // packed upper index, i <= j
+  return i * D - i * (i - 1) / 2 + (j - i);
+}
+
+// Model constants for the kernels (passed by value: constant bank, uniform
+// across the warp).  F_e(h) = sum_m fc[e][m] h^m; Q_e(h) = h sum_m qc[e][m] h^m
+// for packed upper entries e; valid for gnorm*h <= theta_max.
+template <int D>
+struct DevModel {
+  double Pinf[Sym<D>::N];
+  double Dsc[D];                // x = Dsc .* z
+  double fc[D * D][NT];
+  double qc[Sym<D>::N][NT];
+  float kthr_f[NT + 1];         // largest theta for which m terms suffice
+  float kthr_q[NT + 1];
+  float gnorm;                  // ||G||_1 (balanced), as float for term selection
+  float theta_max;
+};
+
+// ---------------------------------------------------------------------------
+// Discretisation (supplement Eq. (ss-gp-formation)): F = exp(hG),
+// Q = int_0^h e^{sG} W e^{sG}^T ds, by the Taylor series of both in h with
+// host-precomputed coefficients.  The term count is chosen per warp from the
+// largest ||G|| h in the warp (float arithmetic, off the FP64 pipe); steps with
+// ||G|| h > theta_max are halved s times and doubled back with
+// F(2h) = F(h)^2, Q(2h) = F(h) Q(h) F(h)^T + Q(h).
+// first = true gives the prior at a series' first time: F = 0, Q = P_inf.
+// Must be called by all 32 lanes of a warp (warp reductions inside).
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void discretize(const DevModel<D>& m, double h, bool first, bool active,
+                                           Mat<D>& F, Mat<D>& Q) {
+  float th = m.gnorm * (float)h;
+  int s = 0;
+  if (active && !first && th > m.theta_max) {
+    s = (int)ceilf(log2f(th / m.theta_max));
+    if (s < 0) s = 0;
+    if (s > 60) s = 60;
+    th = ldexpf(th, -s);
+  }
+  if (!active || first) th = 0.0f;
+  const unsigned kmax = __reduce_max_sync(0xffffffffu, __float_as_uint(th));
+  const float thw = __uint_as_float(kmax);
+  int kf = NT, kq = NT;
+#pragma unroll 1
+  for (int k = 1; k <= NT; ++k) if (thw <= m.kthr_f[k]) { kf = k; break; }
+#pragma unroll 1
+  for (int k = 1; k <= NT; ++k) if (thw <= m.kthr_q[k]) { kq = k; break; }
+  const int smax = (int)__reduce_max_sync(0xffffffffu, (unsigned)s);
+  double hs = (s > 0) ? h * __longlong_as_double((long long)(1023 - s) << 52) : h;
+  if (first || !active) hs = 0.0;
+  // Horner in h
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) F[i][j] = m.fc[i * D + j][kf - 1];
+#pragma unroll 1
+  for (int t = kf - 2; t >= 0; --t) {
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) F[i][j] = fma(F[i][j], hs, m.fc[i * D + j][t]);
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) Q[i][j] = m.qc[pidx<D>(i, j)][kq - 1];
+#pragma unroll 1
+  for (int t = kq - 2; t >= 0; --t) {
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = i; j < D; ++j) Q[i][j] = fma(Q[i][j], hs, m.qc[pidx<D>(i, j)][t]);
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) { Q[i][j] *= hs; Q[j][i] = Q[i][j]; }
+  // doubling for long steps (rare; each lane applies its own count)
+#pragma unroll 1
+  for (int r = 0; r < smax; ++r) {
+    if (r < s) {
+      Mat<D> T, Q2, F2;
+      mul<D>(F, Q, T);
+      mul_Bt_sym_add<D>(T, F, Q, Q2);
+      mul<D>(F, F, F2);
+      copy<D>(Q2, Q);
+      copy<D>(F2, F);
+    }
+  }
+  if (first) {
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        F[i][j] = 0.0;
+        Q[i][j] = m.Pinf[i <= j ? pidx<D>(i, j) : pidx<D>(j, i)];
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Filtering elements and operator (Sec. 3).
+// ---------------------------------------------------------------------------
+template <int D>
+struct FAgg {
+  Mat<D> A;
+  Vec<D> b;
+  Mat<D> C;     // symmetric
+  Vec<D> eta;
+  Mat<D> J;     // symmetric
+};
+template <int D> struct FAggSize { static constexpr int N = D * D + 2 * D + 2 * Sym<D>::N; };
+
+template <int D>
+__device__ __forceinline__ void fagg_identity(FAgg<D>& a) {
+  set_eye<D>(a.A);
+  set_zero<D>(a.C);
+  set_zero<D>(a.J);
+#pragma unroll
+  for (int i = 0; i < D; ++i) { a.b[i] = 0.0; a.eta[i] = 0.0; }
+}
+
+// Aggregate of a run of consecutive elements, folded one raw element at a
+// time.  The tuple (A, b, C, eta, J) of elements s+1..k encodes the affine
+// conditional p(x_k | x_s, y_{s+1:k}) = N(A x_s + b, C) and the likelihood
+// p(y_{s+1:k} | x_s) = N_I(eta, J).  Applying the operator with the element
+// of step k+1 (Sec. 3) reduces -- as in the proof of Prop. 1, where the
+// operator with an element is shown to be a Kalman step -- to a prediction
+// through (F, Q) followed by a scalar update whose innovation is affine in
+// x_s:  v = r - w^T x_s, with w = row 0 of F A and r = y - (F b)_0, which adds
+// w w^T / S to J and w r / S to eta.  An unobserved step keeps only the
+// prediction (the missing-element case of Sec. 3).  A series' first step has
+// F = 0, Q = P_inf, giving A = 0, eta = 0, J = 0 as for the k = 1 elements.
+template <int D>
+__device__ __forceinline__ void fagg_fold_step(FAgg<D>& a, const Mat<D>& F, const Mat<D>& Q,
+                                               bool observed, double y, double R, bool& bad) {
+  Mat<D> Am, T, Pm;
+  Vec<D> bm;
+  mul<D>(F, a.A, Am);
+  mulv<D>(F, a.b, bm);
+  mul<D>(F, a.C, T);
+  mul_Bt_sym_add<D>(T, F, Q, Pm);
+  if (observed) {
+    const double S = Pm[0][0] + R;
+    if (bad_pos(S)) bad = true;
+    const double Si = __drcp_rn(S);
+    const double r = y - bm[0];
+    Vec<D> ws, K;
+#pragma unroll
+    for (int i = 0; i < D; ++i) ws[i] = Am[0][i] * Si;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+#pragma unroll
+      for (int j = i; j < D; ++j) { a.J[i][j] = fma(ws[i], Am[0][j], a.J[i][j]); a.J[j][i] = a.J[i][j]; }
+      a.eta[i] = fma(ws[i], r, a.eta[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) K[i] = Pm[i][0] * Si;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) a.A[i][j] = fma(-K[i], Am[0][j], Am[i][j]);
+      a.b[i] = fma(K[i], r, bm[i]);
+#pragma unroll
+      for (int j = i; j < D; ++j) { a.C[i][j] = fma(-K[i], Pm[0][j], Pm[i][j]); a.C[j][i] = a.C[i][j]; }
+    }
+  } else {
+    copy<D>(Am, a.A);
+    copy<D>(Pm, a.C);
+#pragma unroll
+    for (int i = 0; i < D; ++i) a.b[i] = bm[i];
+  }
+}
+
+// General filtering operator of Sec. 3, o = a (earlier) x b (later):
+//   M = I + C_a J_b,  X_A = M^{-1} A_a,  x_b = M^{-1}(b_a + C_a eta_b),
+//   X_C = M^{-1} C_a,  v = eta_b - J_b b_a,  x_v = M^{-1} C_a v,
+//   A = A_b X_A,  b = A_b x_b + b_b,  C = A_b X_C A_b^T + C_b,
+//   eta = A_a^T (v - J_b x_v) + eta_a     [(I + J C)^{-1} = I - J M^{-1} C],
+//   J = A_a^T (J_b X_A) + J_a             [(I + J C)^{-1} J = J M^{-1}],
+// one LU factorisation with partial pivoting of M for all right-hand sides.
+template <int D>
+__device__ __noinline__ bool fagg_combine(const FAgg<D>& a, const FAgg<D>& b, FAgg<D>& o) {
+  Mat<D> M;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double s = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) s = fma(a.C[i][k], b.J[k][j], s);
+      M[i][j] = s;
+    }
+  Vec<D> v;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double s = b.eta[i];
+#pragma unroll
+    for (int k = 0; k < D; ++k) s = fma(-b.J[i][k], a.b[k], s);
+    v[i] = s;
+  }
+  constexpr int NR = 2 * D + 2;
+  double X[D][NR];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double sb = a.b[i], sv = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) { sb = fma(a.C[i][k], b.eta[k], sb); sv = fma(a.C[i][k], v[k], sv); }
+#pragma unroll
+    for (int j = 0; j < D; ++j) { X[i][j] = a.A[i][j]; X[i][D + 1 + j] = a.C[i][j]; }
+    X[i][D] = sb;
+    X[i][2 * D + 1] = sv;
+  }
+  int perm[D];
+  double invd[D];
+  const bool ok = lu_factor<D>(M, perm, invd);
+  lu_solve<D, NR>(M, perm, invd, X);
+  Mat<D> T;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double s = 0.0, t = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) { s = fma(b.A[i][k], X[k][j], s); t = fma(b.A[i][k], X[k][D + 1 + j], t); }
+      o.A[i][j] = s;
+      T[i][j] = t;
+    }
+    double sb = b.b[i];
+#pragma unroll
+    for (int k = 0; k < D; ++k) sb = fma(b.A[i][k], X[k][D], sb);
+    o.b[i] = sb;
+  }
+  mul_Bt_sym_add<D>(T, b.A, b.C, o.C);
+  Mat<D> U;
+  Vec<D> w;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) s = fma(b.J[i][k], X[k][j], s);
+      U[i][j] = s;
+    }
+    double sw = v[i];
+#pragma unroll
+    for (int k = 0; k < D; ++k) sw = fma(-b.J[i][k], X[k][2 * D + 1], sw);
+    w[i] = sw;
+  }
+  mul_At_sym_add<D>(a.A, U, a.J, o.J);
+  mulTv_add<D>(a.A, w, a.eta, o.eta);
+  return ok;
+}
+
+// A filter state (x, P) -- a prefix aggregate, which has A = 0, eta = 0, J = 0
+// because it contains the first step -- combined with an aggregate b:
+//   M = I + P J_b,  x' = A_b M^{-1} (x + P eta_b) + b_b,
+//   P' = A_b M^{-1} P A_b^T + C_b.
+template <int D>
+__device__ __noinline__ bool fstate_combine(const Vec<D>& x, const Mat<D>& P, const FAgg<D>& b,
+                                            Vec<D>& xo, Mat<D>& Po) {
+  Mat<D> M;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double s = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) s = fma(P[i][k], b.J[k][j], s);
+      M[i][j] = s;
+    }
+  constexpr int NR = D + 1;
+  double X[D][NR];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double s = x[i];
+#pragma unroll
+    for (int k = 0; k < D; ++k) s = fma(P[i][k], b.eta[k], s);
+    X[i][0] = s;
+#pragma unroll
+    for (int j = 0; j < D; ++j) X[i][1 + j] = P[i][j];
+  }
+  int perm[D];
+  double invd[D];
+  const bool ok = lu_factor<D>(M, perm, invd);
+  lu_solve<D, NR>(M, perm, invd, X);
+  Mat<D> T;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double sx = b.b[i];
+#pragma unroll
+    for (int k = 0; k < D; ++k) sx = fma(b.A[i][k], X[k][0], sx);
+    xo[i] = sx;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) t = fma(b.A[i][k], X[k][1 + j], t);
+      T[i][j] = t;
+    }
+  }
+  mul_Bt_sym_add<D>(T, b.A, b.C, Po);
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
+// Smoothing elements and operator (supplement, Prop. 2).
+// ---------------------------------------------------------------------------
+template <int D>
+struct SAgg {
+  Mat<D> E;
+  Vec<D> g;
+  Mat<D> L;     // symmetric
+};
+template <int D> struct SAggSize { static constexpr int N = D * D + D + Sym<D>::N; };
+
+template <int D>
+__device__ __forceinline__ void sagg_identity(SAgg<D>& a) {
+  set_eye<D>(a.E);
+  set_zero<D>(a.L);
+#pragma unroll
+  for (int i = 0; i < D; ++i) a.g[i] = 0.0;
+}
+
+// (E_a, g_a, L_a) x (E_b, g_b, L_b) = (E_a E_b, E_a g_b + g_a, E_a L_b E_a^T + L_a),
+// a earlier.  Used for the in-chunk fold and for the scan levels.
+template <int D>
+__device__ __forceinline__ void sagg_combine(const SAgg<D>& a, const SAgg<D>& b, SAgg<D>& o) {
+  Mat<D> T;
+  mul<D>(a.E, b.E, o.E);
+  mulv_add<D>(a.E, b.g, a.g, o.g);
+  mul<D>(a.E, b.L, T);
+  mul_Bt_sym_add<D>(T, a.E, a.L, o.L);
+}
+
+// Smoother element of step k from the filter state (x_k, P_k) and the
+// transition into step k+1, given T = F P_k, x^- = F x_k and
+// P^- = F P_k F^T + Q (the Kalman prediction of step k+1):
+//   E = P_k F^T (P^-)^{-1}, g = x_k - E x^-, L = P_k - E F P_k,
+// with P^- = Lc Lc^T (Cholesky), W = Lc^{-1} T, E^T = Lc^{-T} W, L = P_k - W^T W.
+template <int D>
+__device__ __forceinline__ bool smoother_element(const Vec<D>& x, const Mat<D>& P, const Mat<D>& T,
+                                                 const Vec<D>& xm, const Mat<D>& Pm, SAgg<D>& e) {
+  Mat<D> Lc, Wm;
+  double invd[D];
+  const bool ok = cholesky<D>(Pm, Lc, invd);
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double s = T[i][j];
+#pragma unroll
+      for (int k = 0; k < i; ++k) s = fma(-Lc[i][k], Wm[k][j], s);
+      Wm[i][j] = s * invd[i];
+    }
+#pragma unroll
+  for (int i = D - 1; i >= 0; --i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double s = Wm[i][j];
+#pragma unroll
+      for (int k = i + 1; k < D; ++k) s = fma(-Lc[k][i], e.E[j][k], s);
+      e.E[j][i] = s * invd[i];
+    }
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double s = x[i];
+#pragma unroll
+    for (int k = 0; k < D; ++k) s = fma(-e.E[i][k], xm[k], s);
+    e.g[i] = s;
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) {
+      double s = P[i][j];
+#pragma unroll
+      for (int k = 0; k < D; ++k) s = fma(-Wm[k][i], Wm[k][j], s);
+      e.L[i][j] = s;
+      e.L[j][i] = s;
+    }
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
+// (De)serialisation of aggregates: entry-major with a stride, so that the
+// lanes of a warp touch consecutive addresses.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void store_fagg(double* p, int64_t st, const FAgg<D>& a) {
+  int e = 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) p[(e++) * st] = a.A[i][j];
+#pragma unroll
+  for (int i = 0; i < D; ++i) p[(e++) * st] = a.b[i];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) p[(e++) * st] = a.C[i][j];
+#pragma unroll
+  for (int i = 0; i < D; ++i) p[(e++) * st] = a.eta[i];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) p[(e++) * st] = a.J[i][j];
+}
+template <int D>
+__device__ __forceinline__ void load_fagg(const double* p, int64_t st, FAgg<D>& a) {
+  int e = 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) a.A[i][j] = p[(e++) * st];
+#pragma unroll
+  for (int i = 0; i < D; ++i) a.b[i] = p[(e++) * st];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) { a.C[i][j] = p[(e++) * st]; a.C[j][i] = a.C[i][j]; }
+#pragma unroll
+  for (int i = 0; i < D; ++i) a.eta[i] = p[(e++) * st];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) { a.J[i][j] = p[(e++) * st]; a.J[j][i] = a.J[i][j]; }
+}
+template <int D>
+__device__ __forceinline__ void store_sagg(double* p, int64_t st, const SAgg<D>& a) {
+  int e = 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) p[(e++) * st] = a.E[i][j];
+#pragma unroll
+  for (int i = 0; i < D; ++i) p[(e++) * st] = a.g[i];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) p[(e++) * st] = a.L[i][j];
+}
+template <int D>
+__device__ __forceinline__ void load_sagg(const double* p, int64_t st, SAgg<D>& a) {
+  int e = 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) a.E[i][j] = p[(e++) * st];
+#pragma unroll
+  for (int i = 0; i < D; ++i) a.g[i] = p[(e++) * st];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) { a.L[i][j] = p[(e++) * st]; a.L[j][i] = a.L[i][j]; }
+}
+
+template <int D>
+__device__ __forceinline__ void shfl_up_fagg(FAgg<D>& a, int off) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) a.A[i][j] = __shfl_up_sync(0xffffffffu, a.A[i][j], off);
+    a.b[i] = __shfl_up_sync(0xffffffffu, a.b[i], off);
+    a.eta[i] = __shfl_up_sync(0xffffffffu, a.eta[i], off);
+#pragma unroll
+    for (int j = i; j < D; ++j) {
+      a.C[i][j] = __shfl_up_sync(0xffffffffu, a.C[i][j], off); a.C[j][i] = a.C[i][j];
+      a.J[i][j] = __shfl_up_sync(0xffffffffu, a.J[i][j], off); a.J[j][i] = a.J[i][j];
+    }
+  }
+}
+template <int D>
+__device__ __forceinline__ void shfl_down_sagg(SAgg<D>& a, int off) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) a.E[i][j] = __shfl_down_sync(0xffffffffu, a.E[i][j], off);
+    a.g[i] = __shfl_down_sync(0xffffffffu, a.g[i], off);
+#pragma unroll
+    for (int j = i; j < D; ++j) { a.L[i][j] = __shfl_down_sync(0xffffffffu, a.L[i][j], off); a.L[j][i] = a.L[i][j]; }
+  }
+}
+
+}  // namespace pssgp
