@@ -202,6 +202,10 @@ int pssgp_debug_filter_aggregates(const pssgp_model* model, const double* t,
                                   double* agg, int64_t* first, int32_t* lanes_out,
                                   void* ws, size_t ws_bytes, void* stream);
 
+/* sizeof(pssgp_model) as compiled into the library, for bindings that mirror
+ * the struct (ABI check). */
+size_t pssgp_model_bytes(void);
+
 /* Measured FP64 fused-multiply-add rate of this device (lane FMAs per
  * second) from a short kernel with independent FMA chains on all SMs: the
  * denominator of the FP64 roofline.  Synchronous; allocates a small probe

@@ -1,0 +1,281 @@
+"""pssgp: parallel state-space GP regression on B300 (FP64, sm_103a).
+
+Thin Python binding over the C ABI of ``libpssgp.so`` (declared in
+``include/pssgp.h``).  It only marshals arguments: every step of the method
+runs in the library's CUDA kernels.  PyTorch supplies device memory and the
+current CUDA stream.  There is no CPU fallback: if the shared library is
+missing or cannot be loaded, importing the entry points raises.
+
+Method: Corenflos, Zhao, Sarkka, "Temporal Gaussian Process Regression in
+Logarithmic Time" -- parallel Kalman filter with missing measurements (Sec. 3),
+parallel RTS smoother (supplement, Prop. 2), state-space forms and
+discretisation (Sec. 2, 4), merge of prediction times (Sec. 4.3).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpssgp.so")
+
+DMAX = 8
+NTAYLOR = 16
+MATERN12, MATERN32, MATERN52, RBF = 1, 2, 3, 4
+KINDS = {"matern12": MATERN12, "matern32": MATERN32, "matern52": MATERN52, "rbf": RBF}
+
+OK = 0
+ERRORS = {-1: "EINVAL", -2: "EDIM", -3: "EKERNEL", -4: "EWORKSPACE", -5: "ECUDA", -6: "EMODEL"}
+ENAN, EUNSORTED, ENOTPD = 1, 2, 4
+
+
+class PssgpKernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("order", ctypes.c_int32), ("lengthscale", ctypes.c_double),
+                ("variance", ctypes.c_double), ("balance", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class PssgpModel(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("G", ctypes.c_double * (DMAX * DMAX)), ("W", ctypes.c_double * (DMAX * DMAX)),
+                ("Pinf", ctypes.c_double * (DMAX * DMAX)), ("D", ctypes.c_double * DMAX),
+                ("gnorm", ctypes.c_double),
+                ("fc", ctypes.c_double * (DMAX * DMAX * NTAYLOR)),
+                ("qc", ctypes.c_double * (DMAX * DMAX * NTAYLOR)),
+                ("theta_max", ctypes.c_double),
+                ("kthr_f", ctypes.c_float * (NTAYLOR + 1)), ("kthr_q", ctypes.c_float * (NTAYLOR + 1)),
+                ("lengthscale", ctypes.c_double), ("variance", ctypes.c_double)]
+
+
+class PssgpError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib():
+    """Load libpssgp.so (built by ``paper_2102_09964_b300.build``); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise PssgpError(f"libpssgp.so not found at {LIB_PATH}; run `python -m paper_2102_09964_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        sz = ctypes.c_size_t
+        L.pssgp_model_bytes.restype = sz
+        L.pssgp_model_build.argtypes = [ctypes.POINTER(PssgpKernel), ctypes.POINTER(PssgpModel)]
+        L.pssgp_model_from_sde.argtypes = [i32, vp, vp, dp, vp, i32, ctypes.POINTER(PssgpModel)]
+        L.pssgp_workspace_size.argtypes = [i32, i64]
+        L.pssgp_workspace_size.restype = sz
+        L.pssgp_get_status.argtypes = [vp, vp, ctypes.POINTER(i32)]
+        L.pssgp_merge.argtypes = [vp, vp, i64, vp, i64, vp, vp, vp, vp, vp, sz, vp]
+        L.pssgp_discretize.argtypes = [ctypes.POINTER(PssgpModel), vp, i64, vp, vp, i64, vp, sz, vp]
+        L.pssgp_filter.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, vp, i64, vp, vp, sz, vp]
+        L.pssgp_smooth.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, i64, i64, vp, vp, vp, vp, vp, sz, vp]
+        L.pssgp_loglik.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, vp, sz, vp]
+        L.pssgp_predict.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, i64, vp, i64, dp, vp, vp, vp, vp, sz, vp]
+        L.pssgp_debug_filter_aggregates.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i64, i32,
+                                                    vp, vp, ctypes.POINTER(i32), vp, sz, vp]
+        L.pssgp_fp64_fma_rate.argtypes = [ctypes.POINTER(dp)]
+        if L.pssgp_model_bytes() != ctypes.sizeof(PssgpModel):
+            raise PssgpError("pssgp_model layout mismatch between libpssgp.so and the binding")
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise PssgpError(f"{what} failed: {ERRORS.get(rc, rc)}")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@dataclass
+class Model:
+    """A built state-space model (host struct handed to every call)."""
+    raw: PssgpModel
+
+    @property
+    def d(self) -> int:
+        return int(self.raw.d)
+
+    @property
+    def D(self):
+        return [self.raw.D[i] for i in range(self.d)]
+
+    def matrix(self, name: str):
+        import numpy as np
+        a = getattr(self.raw, name)
+        d = self.d
+        return np.array([a[i] for i in range(d * d)]).reshape(d, d)
+
+
+def build_model(kind: str, lengthscale: float, variance: float, order: int = 6, balance: bool = True) -> Model:
+    """Kernel -> SDE -> P_inf -> balancing -> discretisation tables (host, O(1))."""
+    k = PssgpKernel(KINDS[kind], int(order), float(lengthscale), float(variance), int(bool(balance)), 0)
+    m = PssgpModel()
+    _check(lib().pssgp_model_build(ctypes.byref(k), ctypes.byref(m)), "pssgp_model_build")
+    return Model(m)
+
+
+def model_from_sde(G, L, q: float, H, balance: bool = True) -> Model:
+    import numpy as np
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    L = np.ascontiguousarray(L, dtype=np.float64).ravel()
+    H = np.ascontiguousarray(H, dtype=np.float64).ravel()
+    m = PssgpModel()
+    rc = lib().pssgp_model_from_sde(G.shape[0], G.ctypes.data, L.ctypes.data, float(q), H.ctypes.data,
+                                    int(bool(balance)), ctypes.byref(m))
+    _check(rc, "pssgp_model_from_sde")
+    return Model(m)
+
+
+def workspace_size(d: int, n: int) -> int:
+    return int(lib().pssgp_workspace_size(int(d), int(n)))
+
+
+def workspace(d: int, n: int, device="cuda", extra: int = 0) -> torch.Tensor:
+    """A device workspace of the size the library asks for (torch allocations
+    are 256-byte aligned)."""
+    return torch.empty(workspace_size(d, n) + int(extra), dtype=torch.uint8, device=device)
+
+
+def status(ws: torch.Tensor) -> int:
+    """Device status word of the last call on `ws` (synchronises the stream)."""
+    v = ctypes.c_int32(0)
+    _check(lib().pssgp_get_status(_ptr(ws), _stream(), ctypes.byref(v)), "pssgp_get_status")
+    return int(v.value)
+
+
+def _f64(x, dev):
+    return torch.as_tensor(x, dtype=torch.float64, device=dev).contiguous()
+
+
+def merge(t_train, y_train, t_test, ws=None):
+    dev = t_train.device
+    N, M = t_train.numel(), t_test.numel()
+    n = N + M
+    t = torch.empty(n, dtype=torch.float64, device=dev)
+    y = torch.empty(n, dtype=torch.float64, device=dev)
+    mask = torch.empty(n, dtype=torch.uint8, device=dev)
+    tpos = torch.empty(max(M, 1), dtype=torch.int64, device=dev)
+    ws = ws if ws is not None else torch.empty(256, dtype=torch.uint8, device=dev)
+    rc = lib().pssgp_merge(_ptr(t_train), _ptr(y_train), N, _ptr(t_test), M, _ptr(t), _ptr(y), _ptr(mask),
+                           _ptr(tpos), _ptr(ws), ws.numel(), _stream())
+    _check(rc, "pssgp_merge")
+    return t, y, mask, tpos[:M], ws
+
+
+def discretize(model: Model, t, ws=None):
+    """F (d*d x n, entry-major) and Q (packed x n)."""
+    d, n = model.d, t.numel()
+    F = torch.empty(d * d, n, dtype=torch.float64, device=t.device)
+    Q = torch.empty(d * (d + 1) // 2, n, dtype=torch.float64, device=t.device)
+    ws = ws if ws is not None else torch.empty(256, dtype=torch.uint8, device=t.device)
+    rc = lib().pssgp_discretize(ctypes.byref(model.raw), _ptr(t), n, _ptr(F), _ptr(Q), n, _ptr(ws), ws.numel(),
+                                _stream())
+    _check(rc, "pssgp_discretize")
+    return F, Q, ws
+
+
+def filter(model: Model, t, y, mask, R, ws=None, outputs=True, loglik=True):
+    """Parallel Kalman filter; returns (xf, Pf, loglik tensor, ws)."""
+    d, n = model.d, t.numel()
+    dev = t.device
+    R = _f64(R, dev).reshape(-1)
+    per = 1 if R.numel() == n and n > 1 else 0
+    ws = ws if ws is not None else workspace(d, n, dev)
+    xf = torch.empty(d, n, dtype=torch.float64, device=dev) if outputs else None
+    Pf = torch.empty(d * (d + 1) // 2, n, dtype=torch.float64, device=dev) if outputs else None
+    ll = torch.empty(1, dtype=torch.float64, device=dev) if loglik else None
+    rc = lib().pssgp_filter(ctypes.byref(model.raw), _ptr(t), _ptr(y), _ptr(mask), _ptr(R), per, n, _ptr(xf),
+                            _ptr(Pf), n, _ptr(ll), _ptr(ws), ws.numel(), _stream())
+    _check(rc, "pssgp_filter")
+    return xf, Pf, ll, ws
+
+
+def smooth(model: Model, t, xf, Pf, ws=None, states=False):
+    """Parallel RTS smoother from filter outputs; returns (f_mean, f_var, xs, Ps, ws)."""
+    d, n = model.d, t.numel()
+    dev = t.device
+    ws = ws if ws is not None else workspace(d, n, dev)
+    fm = torch.empty(n, dtype=torch.float64, device=dev)
+    fv = torch.empty(n, dtype=torch.float64, device=dev)
+    xs = torch.empty(d, n, dtype=torch.float64, device=dev) if states else None
+    Ps = torch.empty(d * (d + 1) // 2, n, dtype=torch.float64, device=dev) if states else None
+    rc = lib().pssgp_smooth(ctypes.byref(model.raw), _ptr(t), _ptr(xf), _ptr(Pf), n, n, _ptr(fm), _ptr(fv),
+                            _ptr(xs), _ptr(Ps), _ptr(ws), ws.numel(), _stream())
+    _check(rc, "pssgp_smooth")
+    return fm, fv, xs, Ps, ws
+
+
+def loglik(model: Model, t, y, mask, R, ws=None):
+    d, n = model.d, t.numel()
+    dev = t.device
+    R = _f64(R, dev).reshape(-1)
+    per = 1 if R.numel() == n and n > 1 else 0
+    ws = ws if ws is not None else workspace(d, n, dev)
+    ll = torch.empty(1, dtype=torch.float64, device=dev)
+    rc = lib().pssgp_loglik(ctypes.byref(model.raw), _ptr(t), _ptr(y), _ptr(mask), _ptr(R), per, n, _ptr(ll),
+                            _ptr(ws), ws.numel(), _stream())
+    _check(rc, "pssgp_loglik")
+    return ll, ws
+
+
+def predict(model: Model, t_train, y_train, t_test, R: float, ws=None, out=None, with_loglik=True):
+    """Fused merge + filter + smoother + gather.  Returns (mean, var, loglik, ws)."""
+    N, M = t_train.numel(), t_test.numel()
+    dev = t_train.device
+    ws = ws if ws is not None else workspace(model.d, N + M, dev)
+    if out is None:
+        out = (torch.empty(M, dtype=torch.float64, device=dev), torch.empty(M, dtype=torch.float64, device=dev),
+               torch.empty(1, dtype=torch.float64, device=dev))
+    mean, var, ll = out
+    rc = lib().pssgp_predict(ctypes.byref(model.raw), _ptr(t_train), _ptr(y_train), N, _ptr(t_test), M, float(R),
+                             _ptr(mean), _ptr(var), _ptr(ll) if with_loglik else None, _ptr(ws), ws.numel(),
+                             _stream())
+    _check(rc, "pssgp_predict")
+    return mean, var, ll, ws
+
+
+def debug_filter_aggregates(model: Model, t, y, mask, R, lanes: int = 0):
+    """Level-0 chunk aggregates (A, b, C, eta, J) per lane, in SDE coordinates,
+    and each chunk's first step (host numpy arrays)."""
+    import numpy as np
+    d, n = model.d, t.numel()
+    dev = t.device
+    R = _f64(R, dev).reshape(-1)[:1]
+    lanes_req = lanes
+    # room for the per-lane debug copy after the regular workspace
+    lanes_max = max(lanes_req, 148 * 4 * 32, 128)
+    ws = workspace(d, n, dev, extra=lanes_max * (2 * d * d + 3 * d) * 8 + 4096)
+    nf = 3 * d * d + 2 * d
+    agg = np.zeros((lanes_max + 128, nf))
+    first = np.zeros(lanes_max + 128, dtype=np.int64)
+    used = ctypes.c_int32(0)
+    rc = lib().pssgp_debug_filter_aggregates(ctypes.byref(model.raw), _ptr(t), _ptr(y), _ptr(mask), _ptr(R), n,
+                                             int(lanes_req), agg.ctypes.data, first.ctypes.data,
+                                             ctypes.byref(used), _ptr(ws), ws.numel(), _stream())
+    _check(rc, "pssgp_debug_filter_aggregates")
+    P0 = used.value
+    out = []
+    for c in range(P0):
+        a = agg[c]
+        out.append((a[:d * d].reshape(d, d), a[d * d:d * d + d], a[d * d + d:2 * d * d + d].reshape(d, d),
+                    a[2 * d * d + d:2 * d * d + 2 * d], a[2 * d * d + 2 * d:].reshape(d, d)))
+    return out, first[:P0], status(ws)
+
+
+def fp64_fma_rate() -> float:
+    v = ctypes.c_double(0.0)
+    _check(lib().pssgp_fp64_fma_rate(ctypes.byref(v)), "pssgp_fp64_fma_rate")
+    return float(v.value)

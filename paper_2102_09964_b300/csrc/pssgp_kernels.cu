@@ -146,8 +146,8 @@ __device__ __forceinline__ void flag(int* status, int bits) {
   if (bits) atomicOr(status, bits);
 }
 
-template <int D> constexpr int fqs_of() { return (D * D + Sym<D>::N + 1) / 2 * 2; }
-template <int D> constexpr int egs_of() { return (D * D + D + Sym<D>::N + 1) / 2 * 2; }
+template <int D> __host__ __device__ constexpr int fqs_of() { return (D * D + Sym<D>::N + 1) / 2 * 2; }
+template <int D> __host__ __device__ constexpr int egs_of() { return (D * D + D + Sym<D>::N + 1) / 2 * 2; }
 
 template <int D>
 __device__ __forceinline__ void load_fq(const double* rec, int64_t k, Mat<D>& F, Mat<D>& Q) {

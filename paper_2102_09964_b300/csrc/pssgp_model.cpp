@@ -291,3 +291,5 @@ extern "C" int pssgp_model_from_sde(int32_t d, const double* G_, const double* L
   for (int i = 0; i < d; ++i) { L[i] = L_[i]; H[i] = H_[i]; }
   return finish_model(d, 0, G, L, (ld)q_, H, do_balance, out);
 }
+
+extern "C" size_t pssgp_model_bytes(void) { return sizeof(pssgp_model); }

@@ -1,0 +1,143 @@
+"""CPU tests of libpssgp's host side: the library loads and exports every
+symbol declared in include/pssgp.h; model formation (Sec. 2, 4.1, 4.2) agrees
+with the oracle's independent construction; the Taylor tables of the device
+discretisation reproduce the matrix exponential and the Q integral; host-side
+argument errors are rejected before any launch.  No GPU needed."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+from scipy.linalg import expm
+
+import paper_2102_09964_b300 as P
+from oracle import model as om
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2102_09964_b300 import build
+    build.build()
+    return P.lib()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "pssgp.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|size_t)\s+(pssgp_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = header_functions()
+    assert len(names) >= 13
+    for nm in names:
+        assert hasattr(lib, nm), nm
+
+
+def sde_coords(m):
+    """Balanced model -> SDE coordinates x = D z."""
+    D = np.array(m.D)
+    G = m.matrix("G") * D[:, None] / D[None, :]
+    Pinf = m.matrix("Pinf") * D[:, None] * D[None, :]
+    W = m.matrix("W") * D[:, None] * D[None, :]
+    return G, Pinf, W
+
+
+@pytest.mark.parametrize("kind", ["matern12", "matern32", "matern52", "rbf"])
+@pytest.mark.parametrize("ell,s2", [(0.5, 1.0), (1.0, 2.0), (4.0, 0.7)])
+@pytest.mark.parametrize("balance", [False, True])
+def test_model_matches_oracle(lib, kind, ell, s2, balance):
+    m = P.build_model(kind, ell, s2, order=6, balance=balance)
+    o = om.make_model(kind, ell, s2)
+    G, Pinf, W = sde_coords(m)
+    sc = np.abs(o.G).max()
+    assert np.abs(G - o.G).max() <= 1e-12 * sc
+    assert np.abs(Pinf - o.Pinf).max() <= 1e-11 * np.abs(o.Pinf).max()
+    assert np.abs(W - o.W).max() <= 1e-11 * np.abs(o.W).max()
+    D = np.array(m.D)
+    assert D[0] == 1.0
+    assert np.all(np.log2(D) == np.round(np.log2(D)))
+
+
+@pytest.mark.parametrize("kind", ["matern32", "matern52", "rbf"])
+@pytest.mark.parametrize("h", [0.0, 1e-4, 3e-3, 0.008])
+def test_taylor_tables_reproduce_discretisation(lib, kind, h):
+    """F(h) = sum_m fc h^m and Q(h) = h sum_m qc h^m (as the device evaluates
+    them, with the term count from the model's thresholds) equal exp(G h) and
+    the Van Loan integral of Eq. (ss-gp-formation), computed here by scipy."""
+    m = P.build_model(kind, 1.0, 1.0)
+    d = m.d
+    G, W = m.matrix("G"), m.matrix("W")
+    theta = m.raw.gnorm * h
+    assert theta <= m.raw.theta_max
+    kf = next(k for k in range(1, 17) if theta <= m.raw.kthr_f[k])
+    kq = next(k for k in range(1, 17) if theta <= m.raw.kthr_q[k])
+    fc = np.array(m.raw.fc[:]).reshape(8 * 8, 16)[: d * d]
+    qc = np.array(m.raw.qc[:]).reshape(8 * 8, 16)[: d * d]
+    F = sum(fc[:, t] * h ** t for t in range(kf)).reshape(d, d)
+    Q = h * sum(qc[:, t] * h ** t for t in range(kq)).reshape(d, d)
+    Fr = expm(G * h)
+    C = np.zeros((2 * d, 2 * d))
+    C[:d, :d] = -G * h
+    C[:d, d:] = W * h
+    C[d:, d:] = G.T * h
+    E = expm(C)
+    Qr = E[d:, d:].T @ E[:d, d:]
+    assert np.abs(F - Fr).max() <= 4e-16 * max(1.0, np.abs(Fr).max())
+    assert np.abs(Q - Qr).max() <= 1e-14 * max(np.abs(Qr).max(), 1e-300) + 1e-300
+
+
+def test_thresholds_cover_theta_max(lib):
+    m = P.build_model("rbf", 1.0, 1.0)
+    assert m.raw.kthr_f[16] >= m.raw.theta_max and m.raw.kthr_q[16] >= m.raw.theta_max
+    assert all(m.raw.kthr_f[k] <= m.raw.kthr_f[k + 1] for k in range(16))
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_rbf_spectral_factor_all_orders(lib, order):
+    """The product's own root finder (Aberth on the truncated exponential) gives
+    the same Hurwitz factor as the oracle's numpy.roots on the degree-2n
+    polynomial."""
+    m = P.build_model("rbf", 0.8, 1.3, order=order, balance=False)
+    o = om.make_model("rbf", 0.8, 1.3, order=order)
+    G, Pinf, _ = sde_coords(m)
+    assert np.abs(G - o.G).max() <= 1e-11 * np.abs(o.G).max()
+    assert np.abs(Pinf - o.Pinf).max() <= 1e-10 * np.abs(o.Pinf).max()
+
+
+def test_model_from_sde_matches_build(lib):
+    o = om.make_model("matern52", 0.9, 1.4)
+    a = P.model_from_sde(o.G, o.L, o.q, o.H, balance=True)
+    b = P.build_model("matern52", 0.9, 1.4, balance=True)
+    np.testing.assert_allclose(a.matrix("G"), b.matrix("G"), rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(a.matrix("Pinf"), b.matrix("Pinf"), rtol=1e-12, atol=1e-14)
+    # H = 2 e_0 is absorbed into D (f = x_0 / ... stays the output)
+    c = P.model_from_sde(o.G, o.L, o.q, 2.0 * o.H, balance=False)
+    assert c.D[0] == 0.5
+
+
+def test_host_argument_errors(lib):
+    import ctypes
+    k = P.PssgpKernel(P.MATERN32, 0, -1.0, 1.0, 1, 0)
+    m = P.PssgpModel()
+    assert lib.pssgp_model_build(ctypes.byref(k), ctypes.byref(m)) == -3       # EKERNEL
+    k = P.PssgpKernel(P.RBF, 9, 1.0, 1.0, 1, 0)
+    assert lib.pssgp_model_build(ctypes.byref(k), ctypes.byref(m)) == -2       # EDIM
+    k = P.PssgpKernel(77, 0, 1.0, 1.0, 1, 0)
+    assert lib.pssgp_model_build(ctypes.byref(k), ctypes.byref(m)) == -3
+    assert lib.pssgp_workspace_size(9, 10) == 0
+    assert lib.pssgp_workspace_size(3, 0) == 0
+    mm = P.build_model("matern32", 1.0, 1.0)
+    # null pointers / bad sizes are rejected on the host (no launch)
+    assert lib.pssgp_filter(ctypes.byref(mm.raw), None, None, None, None, 0, 10, None, None, 10, None,
+                            None, 0, None) == -1
+    assert lib.pssgp_predict(ctypes.byref(mm.raw), None, None, 0, None, 0, 0.01, None, None, None,
+                             None, 0, None) == -1
+
+
+def test_workspace_size_grows_linearly(lib):
+    a = P.workspace_size(6, 1 << 16)
+    b = P.workspace_size(6, 1 << 17)
+    assert 1.8 < b / a < 2.2
