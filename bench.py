@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Benchmark of the parallel state-space GP prediction path on B300.
+
+One step = one pssgp_predict call on the large noisy-sinusoid workload:
+merge of 10,000 prediction times into 2^20 sorted training times, Taylor
+order-6 RBF state-space model (d = 6), discretisation, parallel Kalman filter
+with missing measurements, parallel RTS smoother, gather at the prediction
+times and the log marginal likelihood, all FP64.  The metric is merged time
+steps per second (N + M = 1,058,576 steps per step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload rbf6|matern52]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+on its own GPU (the path has no cross-series exchange in this configuration);
+value = all ranks' steps / max-over-ranks time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "filter+smoother time steps/s at N=2^20,d=6 FP64"
+UNIT = "steps/s"
+WORKLOADS = {
+    "rbf6": dict(kind="rbf", order=6, lengthscale=1.0, variance=1.0, noise=0.01),
+    "matern52": dict(kind="matern52", order=0, lengthscale=1.0, variance=1.0, noise=0.01),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rbf6", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--timing-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# algorithmic FP64 flop counts per merged step (FMA = 2 flops; a reciprocal,
+# square root or comparison counts 1), from the formulas each kernel evaluates
+# ---------------------------------------------------------------------------
+def flops_discretize(d, kf, kq):
+    s = d * (d + 1) // 2
+    return 2 * d * d * (kf - 1) + 2 * s * (kq - 1) + s
+
+
+def flops_filter_fold(d, observed_frac):
+    s = d * (d + 1) // 2
+    pred = (2 * d ** 3 - d * d) * 2 + (2 * d * d - d) + 2 * s * d          # F A, F C, F b, (F C) F^T + Q
+    upd = 4 + 6 * d + 4 * s + 2 * d * d                                    # S, 1/S, r, w/S, J, eta, K, A, b, C
+    return pred + observed_frac * upd
+
+
+def flops_kf_step(d, observed_frac):
+    s = d * (d + 1) // 2
+    pred = (2 * d * d - d) + (2 * d ** 3 - d * d) + 2 * s * d              # F x, F P, (F P) F^T + Q
+    upd = 6 + 3 * d + 2 * s                                                # S, 1/S, v, K, x, P, log-lik terms
+    return pred + observed_frac * upd
+
+
+def flops_smoother_element(d):
+    s = d * (d + 1) // 2
+    chol = sum(2 * j + 1 + (d - 1 - j) * (2 * j + 1) for j in range(d)) + d   # + d reciprocal square roots
+    return chol + 2 * d ** 3 + 2 * d * d + 2 * s * d                       # W, E^T, g, L
+
+
+def flops_smoother_fold(d):
+    s = d * (d + 1) // 2
+    return (2 * d ** 3 - d * d) * 2 + 2 * d * d + 2 * s * d                # E_a E, E_a L, E_a g + g_a, (.)E_a^T + L_a
+
+
+def flops_rts_step(d):
+    s = d * (d + 1) // 2
+    return 2 * d * d + (2 * d ** 3 - d * d) + 2 * s * d
+
+
+def taylor_terms(model, t, lanes, L):
+    """Per-step Taylor term counts as the device picks them: per warp and
+    per in-chunk iteration, from the largest ||G|| h over the warp's 32 lanes."""
+    h = np.diff(t, prepend=t[0])
+    h[0] = 0.0
+    n = t.size
+    pad = lanes * L
+    hp = np.zeros(pad)
+    hp[:n] = h
+    th = (hp.reshape(lanes, L) * model.raw.gnorm).astype(np.float32)
+    th = np.minimum(th, np.float32(model.raw.theta_max))
+    thw = th.reshape(lanes // 32, 32, L).max(axis=1)                      # (warps, L)
+    kf_thr = np.array(model.raw.kthr_f[:], dtype=np.float32)
+    kq_thr = np.array(model.raw.kthr_q[:], dtype=np.float32)
+    kf = np.searchsorted(kf_thr[1:], thw.ravel(), side="left") + 1
+    kq = np.searchsorted(kq_thr[1:], thw.ravel(), side="left") + 1
+    return float(kf.mean()), float(kq.mean())
+
+
+def lane_plan(n, sms=148):
+    lanes_max = sms * 4 * 32
+    want = (n + 7) // 8
+    P0 = min(lanes_max, max(want, 1))
+    P0 = (P0 + 127) // 128 * 128
+    return P0, (n + P0 - 1) // P0
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(wl_params, n_sample_train=1 << 19):
+    """The oracle as it stands on the host cores, on a bounded prefix sample of
+    the same workload; returns steps/s and a description."""
+    import oracle
+    import workloads as wl
+    from oracle import model as om
+    oracle.build()
+    s = wl.prefix(wl.sinusoid_large(), n_sample_train)
+    o = om.make_model(wl_params["kind"], wl_params["lengthscale"], wl_params["variance"],
+                      order=wl_params["order"] or 6)
+    t0 = time.perf_counter()
+    oracle.predict(o, s.t_train, s.y_train, s.t_test, wl_params["noise"])
+    dt = time.perf_counter() - t0
+    n = s.N + s.M
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {s.N} training + {s.M} prediction points of the workload ({n} merged steps), "
+                      f"{dt:.1f} s wall; long-double sequential KF + RTS, discretisation on {cores} threads"}
+
+
+def run_reference(args, wl_params):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    cb = cpu_baseline(wl_params, n_sample_train=1 << 15)
+    times = []
+    for i in range(args.warmup + args.steps):
+        c = cpu_baseline(wl_params, n_sample_train=1 << 15)
+        if i >= args.warmup:
+            times.append(c["value"])
+    v = statistics.mean(times) if times else cb["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: sampled prefix of the 2^20+10^4 noisy-sinusoid series"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, wl_params):
+    import torch
+    import paper_2102_09964_b300 as P
+    import workloads as wl
+    from paper_2102_09964_b300 import build as B
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    B.build()
+    P.lib()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    s = wl.sinusoid_large(seed=2 + rank)
+    N, M = s.N, s.M
+    n = N + M
+    m = P.build_model(wl_params["kind"], wl_params["lengthscale"], wl_params["variance"],
+                      order=wl_params["order"] or 6)
+    R = wl_params["noise"]
+    tt = torch.as_tensor(s.t_train, dtype=torch.float64, device=dev)
+    yy = torch.as_tensor(s.y_train, dtype=torch.float64, device=dev)
+    ts = torch.as_tensor(s.t_test, dtype=torch.float64, device=dev)
+    wsb = P.workspace(m.d, n, dev)
+    out = (torch.empty(M, dtype=torch.float64, device=dev), torch.empty(M, dtype=torch.float64, device=dev),
+           torch.empty(1, dtype=torch.float64, device=dev))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        P.predict(m, tt, yy, ts, R, ws=wsb, out=out)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert P.status(wsb) == 0, "device status error"
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # --- device-timed region (inputs resident in HBM) ---
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        tmax = torch.tensor([ms], device=dev)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        ms = float(tmax.item())
+    value = n * world / (ms * 1e-3)
+
+    # --- end to end through the C ABI from pinned host buffers ---
+    h_tt = torch.as_tensor(s.t_train, dtype=torch.float64).pin_memory()
+    h_yy = torch.as_tensor(s.y_train, dtype=torch.float64).pin_memory()
+    h_ts = torch.as_tensor(s.t_test, dtype=torch.float64).pin_memory()
+    h_mean = torch.empty(M, dtype=torch.float64).pin_memory()
+    h_var = torch.empty(M, dtype=torch.float64).pin_memory()
+    h_ll = torch.empty(1, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        tt.copy_(h_tt, non_blocking=True)
+        yy.copy_(h_yy, non_blocking=True)
+        ts.copy_(h_ts, non_blocking=True)
+        P.predict(m, tt, yy, ts, R, ws=wsb, out=out)
+        h_mean.copy_(out[0], non_blocking=True)
+        h_var.copy_(out[1], non_blocking=True)
+        h_ll.copy_(out[2], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    f1.record(stream)
+    f1.synchronize()
+    ms_e2e = f0.elapsed_time(f1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        tmax = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        ms_e2e = float(tmax.item())
+    e2e = {"value": n * world / (ms_e2e * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": int((2 * N + M) * 8), "d2h_bytes_per_step": int((2 * M + 1) * 8)}
+
+    # --- per-kernel times (events around each launch) for the roofline ---
+    P.timing(1)
+    for _ in range(args.timing_steps):
+        step()
+    torch.cuda.synchronize()
+    per = P.timing(2)
+    P.timing(0)
+    launches = sum(c for _, c in per.values()) // max(args.timing_steps, 1)
+    gpu_launches = launches * args.steps
+    fma_rate = P.fp64_fma_rate()
+    peak_tflops = 2 * fma_rate / 1e12
+
+    t_merged = np.sort(np.concatenate([s.t_train, s.t_test]), kind="stable")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    lanes, L = lane_plan(n, sms)
+    kf, kq = taylor_terms(m, t_merged, lanes, L)
+    d = m.d
+    obs = N / n
+    alg = {
+        "filter_reduce": n * (flops_discretize(d, kf, kq) + flops_filter_fold(d, obs)),
+        "filter_propagate": n * (flops_kf_step(d, obs) + flops_smoother_element(d) + flops_smoother_fold(d)),
+        "smoother_propagate": n * flops_rts_step(d),
+    }
+    kernels = {}
+    for name, (tot, cnt) in per.items():
+        avg = tot / cnt
+        kernels[name] = {"ms": round(avg, 4), "share": None}
+    tot_all = sum(v["ms"] for v in kernels.values())
+    for v in kernels.values():
+        v["share"] = round(v["ms"] / tot_all, 4)
+    dom = max((k for k in alg if k in kernels), key=lambda k: kernels[k]["ms"])
+    achieved = alg[dom] / (kernels[dom]["ms"] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_tflops, 4), "unit": "TFLOP/s",
+                "frac": round(achieved / peak_tflops, 4), "traffic": None, "kernel": dom,
+                "peak_source": "measured FP64 FMA rate of this GPU (pssgp_fp64_fma_rate, x2 flops)",
+                "algorithmic_flops_per_launch": alg[dom], "taylor_terms": {"F": round(kf, 2), "Q": round(kq, 2)}}
+    whole = sum(alg.values()) / (ms * 1e-3) / 1e12
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: N=2^20 training times U[0,1000] + M=10^4 prediction times, "
+                                   f"y=sin(0.3t)+0.5sin(1.7t)+N(0,0.1^2), d={d}, l=1, s2=1, R=0.01; "
+                                   "one pssgp_predict (merge+filter+smoother+gather+loglik) per step",
+                       "merged_steps": n, "per_rank_replica": True,
+                       "l2": "workspace traffic ~1 GB per step exceeds the 126 MB L2 (no explicit flush)"},
+            "e2e": e2e, "gpu_launches": int(gpu_launches), "clocks": clocks, "roofline": roofline,
+            "whole_path_tflops": round(whole, 4), "kernels": kernels}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl_params)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    wl_params = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl_params)
+    return run_ours(args, wl_params)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -202,6 +202,15 @@ int pssgp_debug_filter_aggregates(const pssgp_model* model, const double* t,
                                   double* agg, int64_t* first, int32_t* lanes_out,
                                   void* ws, size_t ws_bytes, void* stream);
 
+/* Per-kernel timing for measurement (not for use inside stream capture):
+ * mode 1 enables it and resets the totals, mode 0 disables it, mode 2 waits
+ * for the recorded CUDA events and copies the summed milliseconds and launch
+ * counts of up to nslots kernels (host arrays) to ms / counts.  While enabled
+ * every launch is bracketed by two events on its own stream. */
+int pssgp_timing(int32_t mode, double* ms, int64_t* counts, int32_t nslots);
+/* Name of timing slot `slot` ("" if unused). */
+const char* pssgp_timing_name(int32_t slot);
+
 /* sizeof(pssgp_model) as compiled into the library, for bindings that mirror
  * the struct (ABI check). */
 size_t pssgp_model_bytes(void);

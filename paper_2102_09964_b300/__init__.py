@@ -80,6 +80,9 @@ def lib():
         L.pssgp_debug_filter_aggregates.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i64, i32,
                                                     vp, vp, ctypes.POINTER(i32), vp, sz, vp]
         L.pssgp_fp64_fma_rate.argtypes = [ctypes.POINTER(dp)]
+        L.pssgp_timing.argtypes = [i32, vp, vp, i32]
+        L.pssgp_timing_name.argtypes = [i32]
+        L.pssgp_timing_name.restype = ctypes.c_char_p
         if L.pssgp_model_bytes() != ctypes.sizeof(PssgpModel):
             raise PssgpError("pssgp_model layout mismatch between libpssgp.so and the binding")
         _lib = L
@@ -279,3 +282,21 @@ def fp64_fma_rate() -> float:
     v = ctypes.c_double(0.0)
     _check(lib().pssgp_fp64_fma_rate(ctypes.byref(v)), "pssgp_fp64_fma_rate")
     return float(v.value)
+
+
+def timing(mode: int):
+    """Per-kernel event timing: timing(1) enable+reset, timing(0) disable,
+    timing(2) -> {kernel name: (total ms, launches)}."""
+    import numpy as np
+    ms = np.zeros(16)
+    cnt = np.zeros(16, dtype=np.int64)
+    _check(lib().pssgp_timing(int(mode), ms.ctypes.data if mode == 2 else None,
+                              cnt.ctypes.data if mode == 2 else None, 16), "pssgp_timing")
+    if mode != 2:
+        return None
+    out = {}
+    for i in range(16):
+        name = lib().pssgp_timing_name(i).decode()
+        if name and cnt[i] > 0:
+            out[name] = (float(ms[i]), int(cnt[i]))
+    return out

@@ -58,6 +58,39 @@ int num_sms() {
   return g_num_sms;
 }
 
+// Optional per-kernel timing (diagnostic): CUDA events recorded on the
+// launching stream around every launch, summed per kernel name.
+constexpr int TIMING_SLOTS = 16;
+const char* const kTimingNames[TIMING_SLOTS] = {
+    "merge", "filter_reduce", "filter_level2", "filter_propagate", "smoother_level2", "smoother_propagate",
+    "smoother_elements", "gather", "loglik_reduce", "discretize", "", "", "", "", "", ""};
+enum { T_MERGE = 0, T_FRED, T_FL2, T_FPROP, T_SL2, T_SPROP, T_SELEM, T_GATHER, T_LL, T_DISC };
+bool g_timing = false;
+struct TimingRec { cudaEvent_t a, b; int slot; };
+std::vector<TimingRec> g_pending;
+double g_ms[TIMING_SLOTS] = {0};
+long long g_count[TIMING_SLOTS] = {0};
+
+struct Timed {
+  cudaStream_t s;
+  int slot;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Timed(cudaStream_t s_, int slot_) : s(s_), slot(slot_) {
+    if (g_timing) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~Timed() {
+    if (g_timing) {
+      cudaEventRecord(b, s);
+      std::lock_guard<std::mutex> lk(g_mu);
+      g_pending.push_back({a, b, slot});
+    }
+  }
+};
+
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 int64_t align256(int64_t b) { return round_up(b, 256); }
 
@@ -743,6 +776,7 @@ const double* run_filter_level2(const Plan& p, double* buf0, int* status, cudaSt
   double* out = buf0 + p.P2 * p.nf;
   const int grid = (int)((p.P2 + BLOCK - 1) / BLOCK);
   for (int64_t off = 1; off < p.P2; off <<= 1) {
+    Timed tm(s, T_FL2);
     k_filter_ks<D><<<grid, BLOCK, 0, s>>>(in, out, p.P2, off, status);
     std::swap(in, out);
   }
@@ -754,6 +788,7 @@ const double* run_smoother_level2(const Plan& p, double* buf0, cudaStream_t s) {
   double* out = buf0 + p.P2 * p.ns;
   const int grid = (int)((p.P2 + BLOCK - 1) / BLOCK);
   for (int64_t off = 1; off < p.P2; off <<= 1) {
+    Timed tm(s, T_SL2);
     k_smoother_ks<D><<<grid, BLOCK, 0, s>>>(in, out, p.P2, off);
     std::swap(in, out);
   }
@@ -763,14 +798,21 @@ const double* run_smoother_level2(const Plan& p, double* buf0, cudaStream_t s) {
 template <int D>
 void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s) {
   const int grid = (int)(p.P0 / BLOCK);
-  k_filter_reduce<D><<<grid, BLOCK, 0, s>>>(m, a);
+  {
+    Timed tm(s, T_FRED);
+    k_filter_reduce<D><<<grid, BLOCK, 0, s>>>(m, a);
+  }
   a.wfin_f = run_filter_level2<D>(p, a.wagg_f, a.status, s);
-  k_filter_propagate<D><<<grid, BLOCK, 0, s>>>(m, a);
+  {
+    Timed tm(s, T_FPROP);
+    k_filter_propagate<D><<<grid, BLOCK, 0, s>>>(m, a);
+  }
 }
 template <int D>
 void run_smoother_tail(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s) {
   const int grid = (int)(p.P0 / BLOCK);
   a.wfin_s = run_smoother_level2<D>(p, a.wagg_s, s);
+  Timed tm(s, T_SPROP);
   k_smoother_propagate<D><<<grid, BLOCK, 0, s>>>(m, a);
 }
 
@@ -818,7 +860,10 @@ int filter_common(const pssgp_model* model, const double* t, const double* y, co
     const DevModel<D> m = dev_model<D>(model);
     run_filter<D>(m, p, a, s);
   });
-  if (loglik) k_loglik_reduce<<<1, 256, 0, s>>>(a.llp, p.P0, loglik);
+  if (loglik) {
+    Timed tm(s, T_LL);
+    k_loglik_reduce<<<1, 256, 0, s>>>(a.llp, p.P0, loglik);
+  }
   return cuda_rc(cudaGetLastError());
 }
 
@@ -901,7 +946,10 @@ extern "C" int pssgp_smooth(const pssgp_model* model, const double* t, const dou
   if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess) return PSSGP_ECUDA;
   PSSGP_DISPATCH(model->d, {
     const DevModel<D> m = dev_model<D>(model);
-    k_smoother_elements<D><<<grid, BLOCK, 0, s>>>(m, a, xf, Pf);
+    {
+      Timed tm(s, T_SELEM);
+      k_smoother_elements<D><<<grid, BLOCK, 0, s>>>(m, a, xf, Pf);
+    }
     run_smoother_tail<D>(m, p, a, s);
   });
   return cuda_rc(cudaGetLastError());
@@ -927,8 +975,11 @@ extern "C" int pssgp_predict(const pssgp_model* model, const double* t_train, co
   double* fvar = reinterpret_cast<double*>(ws_ptr(ws, p.o_fvar));
   if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess) return PSSGP_ECUDA;
   const int64_t threads = (n + MERGE_ITEMS - 1) / MERGE_ITEMS;
-  k_merge<<<(unsigned)((threads + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(t_train, y_train, N, t_test, M, t, y, mask,
-                                                                       tpos, a.status);
+  {
+    Timed tm(s, T_MERGE);
+    k_merge<<<(unsigned)((threads + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(t_train, y_train, N, t_test, M, t, y, mask,
+                                                                         tpos, a.status);
+  }
   a.t = t; a.y = y; a.mask = mask; a.R = nullptr; a.R_scalar = R; a.R_per_step = 0;
   a.fuse_smoother = 1;
   a.f_mean = fmean; a.f_var = fvar;
@@ -938,8 +989,14 @@ extern "C" int pssgp_predict(const pssgp_model* model, const double* t_train, co
     run_filter<D>(m, p, a, s);
     run_smoother_tail<D>(m, p, a, s);
   });
-  if (M > 0) k_gather<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(fmean, fvar, tpos, M, mean_test, var_test);
-  if (loglik) k_loglik_reduce<<<1, 256, 0, s>>>(a.llp, p.P0, loglik);
+  if (M > 0) {
+    Timed tm(s, T_GATHER);
+    k_gather<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(fmean, fvar, tpos, M, mean_test, var_test);
+  }
+  if (loglik) {
+    Timed tm(s, T_LL);
+    k_loglik_reduce<<<1, 256, 0, s>>>(a.llp, p.P0, loglik);
+  }
   return cuda_rc(cudaGetLastError());
 }
 
@@ -1013,4 +1070,38 @@ extern "C" int pssgp_fp64_fma_rate(double* fma_per_s) {
   if (e != cudaSuccess || ms <= 0.0f) return PSSGP_ECUDA;
   *fma_per_s = (double)blocks * threads * iters * 4 / (ms * 1e-3);
   return PSSGP_OK;
+}
+
+extern "C" int pssgp_timing(int32_t mode, double* ms, int64_t* counts, int32_t nslots) {
+  // mode 1: enable and reset; 0: disable; 2: collect (synchronises on the
+  // recorded events) into ms[slot], counts[slot]
+  if (mode == 1 || mode == 0) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& r : g_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    g_pending.clear();
+    for (int i = 0; i < TIMING_SLOTS; ++i) { g_ms[i] = 0; g_count[i] = 0; }
+    g_timing = (mode == 1);
+    return PSSGP_OK;
+  }
+  if (mode != 2 || !ms || !counts) return PSSGP_EINVAL;
+  std::vector<TimingRec> pend;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    pend.swap(g_pending);
+  }
+  for (auto& r : pend) {
+    float t = 0.0f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return PSSGP_ECUDA;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    g_ms[r.slot] += t;
+    g_count[r.slot] += 1;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (int i = 0; i < nslots && i < TIMING_SLOTS; ++i) { ms[i] = g_ms[i]; counts[i] = g_count[i]; }
+  return PSSGP_OK;
+}
+
+extern "C" const char* pssgp_timing_name(int32_t slot) {
+  return (slot >= 0 && slot < TIMING_SLOTS) ? kTimingNames[slot] : "";
 }
