@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--workload", default="rbf6", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--timing-steps", type=int, default=3)
+    ap.add_argument("--n-train", type=int, default=0,
+                    help="profile a prefix of the workload with this many training points (0 = full 2^20)")
     return ap.parse_args()
 
 
@@ -240,6 +242,8 @@ def run_ours(args, wl_params):
     P.lib()
     dev = torch.device("cuda", torch.cuda.current_device())
     s = wl.sinusoid_large(seed=2 + rank)
+    if args.n_train:
+        s = wl.prefix(s, args.n_train)
     N, M = s.N, s.M
     n = N + M
     m = P.build_model(wl_params["kind"], wl_params["lengthscale"], wl_params["variance"],
