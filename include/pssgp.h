@@ -52,6 +52,8 @@ extern "C" {
 #define PSSGP_EWORKSPACE (-4)  /* workspace too small or misaligned            */
 #define PSSGP_ECUDA (-5)       /* a CUDA runtime call failed                   */
 #define PSSGP_EMODEL (-6)      /* model formation failed (Lyapunov/roots)      */
+#define PSSGP_ESCRATCH (-7)    /* problem too large for the built-in scratch of
+                                  pssgp_loglik_noalloc                          */
 /* device-detected errors, OR-ed into the workspace status word */
 #define PSSGP_ENAN 1           /* non-finite time or observed y                 */
 #define PSSGP_EUNSORTED 2      /* times decrease somewhere                      */
@@ -175,6 +177,31 @@ int pssgp_smooth(const pssgp_model* model, const double* t,
 int pssgp_loglik(const pssgp_model* model, const double* t, const double* y,
                  const uint8_t* mask, const double* R, int32_t R_per_step,
                  int64_t n, double* loglik, void* ws, size_t ws_bytes, void* stream);
+
+/* Allocation-free variant of pssgp_loglik for callers that cannot allocate
+ * device memory themselves -- for instance a plugin inside a host program
+ * that owns every device allocation and does not let third-party code call
+ * cudaMalloc, or a latency-critical loop that must never enter the driver's
+ * allocator -- and therefore cannot pass a workspace.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *  - Scratch: a fixed 32 MiB array inside the library's device image, held on
+ *    every GPU that loads the library until the process exits.  That bounds
+ *    the problem size: n up to about 28,000 merged steps at d = 6 and about
+ *    160,000 at d = 2 (exactly: pssgp_workspace_size(d, n) <= 32 MiB).  Larger
+ *    problems are rejected with PSSGP_ESCRATCH before anything is launched.
+ *  - The first call on a device looks up the scratch's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - All calls share the one scratch array per device, so calls that overlap
+ *    on the GPU (different streams or threads) race and give wrong results;
+ *    serialise them.  Nothing from a previous call is reused: the status word
+ *    is cleared at the start, everything else is written before it is read.
+ *  - Arguments as pssgp_loglik; `status` (device pointer to one int32,
+ *    nullable) receives the device status bits of this call.  The per-kernel
+ *    timing diagnostic (pssgp_timing) must be off. */
+int pssgp_loglik_noalloc(const pssgp_model* model, const double* t, const double* y,
+                         const uint8_t* mask, const double* R, int32_t R_per_step,
+                         int64_t n, double* loglik, int32_t* status, void* stream);
 
 /* ---- fused prediction path (Sec. 4.4, stages 4-5) ---------------------- */
 /* merge -> discretise -> parallel filter -> parallel smoother -> gather, with

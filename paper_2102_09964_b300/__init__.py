@@ -28,7 +28,7 @@ MATERN12, MATERN32, MATERN52, RBF = 1, 2, 3, 4
 KINDS = {"matern12": MATERN12, "matern32": MATERN32, "matern52": MATERN52, "rbf": RBF}
 
 OK = 0
-ERRORS = {-1: "EINVAL", -2: "EDIM", -3: "EKERNEL", -4: "EWORKSPACE", -5: "ECUDA", -6: "EMODEL"}
+ERRORS = {-1: "EINVAL", -2: "EDIM", -3: "EKERNEL", -4: "EWORKSPACE", -5: "ECUDA", -6: "EMODEL", -7: "ESCRATCH"}
 ENAN, EUNSORTED, ENOTPD = 1, 2, 4
 
 
@@ -81,6 +81,7 @@ def lib():
                                                     vp, vp, ctypes.POINTER(i32), vp, sz, vp]
         L.pssgp_fp64_fma_rate.argtypes = [ctypes.POINTER(dp)]
         L.pssgp_timing.argtypes = [i32, vp, vp, i32]
+        L.pssgp_loglik_noalloc.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, vp, vp]
         L.pssgp_timing_name.argtypes = [i32]
         L.pssgp_timing_name.restype = ctypes.c_char_p
         if L.pssgp_model_bytes() != ctypes.sizeof(PssgpModel):

@@ -1105,3 +1105,63 @@ extern "C" int pssgp_timing(int32_t mode, double* ms, int64_t* counts, int32_t n
 extern "C" const char* pssgp_timing_name(int32_t slot) {
   return (slot >= 0 && slot < TIMING_SLOTS) ? kTimingNames[slot] : "";
 }
+
+// ===========================================================================
+// Allocation-free log-likelihood
+//
+// For callers that cannot allocate device memory themselves, e.g. a plugin
+// loaded into a host program that owns every device allocation and forbids
+// third-party code from calling cudaMalloc, or a latency-critical loop that
+// must never enter the driver's allocator.  They cannot hand the library a
+// workspace, so this entry point uses a fixed scratch array that lives in the
+// library's own device image instead.  The paper has no counterpart: it is a
+// deployment convenience around pssgp_loglik.
+// ===========================================================================
+namespace {
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;   // 32 MiB per device, held until exit
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+}  // namespace
+
+// The scratch itself.  Host code must not use this name as a device address
+// (on the host it is only a stand-in); its device address is looked up once
+// per device with cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+// Device address of the scratch on the current device (looked up on the
+// first call per device, with that device current).
+int noalloc_scratch(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PSSGP_ECUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return PSSGP_ECUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return PSSGP_OK;
+}
+}  // namespace
+
+extern "C" int pssgp_loglik_noalloc(const pssgp_model* model, const double* t, const double* y, const uint8_t* mask,
+                                    const double* R, int32_t R_per_step, int64_t n, double* loglik,
+                                    int32_t* status, void* stream) {
+  if (!model_ok(model) || !t || !y || !mask || !R || !loglik || n < 1) return PSSGP_EINVAL;
+  if ((size_t)make_plan(model->d, n, 0).total > kNoAllocScratchBytes) return PSSGP_ESCRATCH;
+  void* ws = nullptr;
+  int rc = noalloc_scratch(&ws);
+  if (rc) return rc;
+  // filter_common clears the status word before its kernels run; every other
+  // scratch region it reads is fully written earlier in the same call.
+  rc = filter_common(model, t, y, mask, R, R_per_step, n, nullptr, nullptr, n, loglik, ws, kNoAllocScratchBytes,
+                     stream, 0, nullptr);
+  if (rc) return rc;
+  if (status) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(status, ws, sizeof(int32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess) return PSSGP_ECUDA;
+  }
+  return PSSGP_OK;
+}
