@@ -58,9 +58,13 @@ def parse():
 # algorithmic FP64 flop counts per merged step (FMA = 2 flops; a reciprocal,
 # square root or comparison counts 1), from the formulas each kernel evaluates
 # ---------------------------------------------------------------------------
-def flops_discretize(d, kf, kq):
+def flops_discretize(d, kf, kq, companion=True):
     s = d * (d + 1) // 2
-    return 2 * d * d * (kf - 1) + 2 * s * (kq - 1) + s
+    if companion:   # row 0 of F by Horner, rows 1..d-1 by the companion recursion
+        f = 2 * d * (kf - 1) + (d - 1) * (1 + 3 * (d - 1))
+    else:
+        f = 2 * d * d * (kf - 1)
+    return f + 2 * s * (kq - 1) + s
 
 
 def flops_filter_fold(d, observed_frac):
@@ -94,21 +98,19 @@ def flops_rts_step(d):
 
 
 def taylor_terms(model, t, lanes, L):
-    """Per-step Taylor term counts as the device picks them: per warp and
-    per in-chunk iteration, from the largest ||G|| h over the warp's 32 lanes."""
+    """Mean Taylor term counts as the device picks them: per warp and per
+    in-chunk iteration, from the longest step over the warp's 32 lanes."""
     h = np.diff(t, prepend=t[0])
     h[0] = 0.0
     n = t.size
-    pad = lanes * L
-    hp = np.zeros(pad)
+    hp = np.zeros(lanes * L)
     hp[:n] = h
-    th = (hp.reshape(lanes, L) * model.raw.gnorm).astype(np.float32)
-    th = np.minimum(th, np.float32(model.raw.theta_max))
-    thw = th.reshape(lanes // 32, 32, L).max(axis=1)                      # (warps, L)
-    kf_thr = np.array(model.raw.kthr_f[:], dtype=np.float32)
-    kq_thr = np.array(model.raw.kthr_q[:], dtype=np.float32)
-    kf = np.searchsorted(kf_thr[1:], thw.ravel(), side="left") + 1
-    kq = np.searchsorted(kq_thr[1:], thw.ravel(), side="left") + 1
+    hf = np.minimum(hp.reshape(lanes, L).astype(np.float32), np.float32(model.raw.hmax))
+    hw = hf.reshape(lanes // 32, 32, L).max(axis=1).ravel()
+    thr_f = np.array(model.raw.hthr_f[1:], dtype=np.float32)
+    thr_q = np.array(model.raw.hthr_q[1:], dtype=np.float32)
+    kf = np.searchsorted(thr_f, hw, side="left") + 1
+    kq = np.searchsorted(thr_q, hw, side="left") + 1
     return float(kf.mean()), float(kq.mean())
 
 
@@ -348,7 +350,7 @@ def run_ours(args, wl_params):
     d = m.d
     obs = N / n
     alg = {
-        "filter_reduce": n * (flops_discretize(d, kf, kq) + flops_filter_fold(d, obs)),
+        "filter_reduce": n * (flops_discretize(d, kf, kq, bool(m.raw.companion)) + flops_filter_fold(d, obs)),
         "filter_propagate": n * (flops_kf_step(d, obs) + flops_smoother_element(d) + flops_smoother_fold(d)),
         "smoother_propagate": n * flops_rts_step(d),
     }

@@ -89,17 +89,27 @@ typedef struct pssgp_model {
   double W[PSSGP_DMAX * PSSGP_DMAX];     /* L q L^T, balanced                  */
   double Pinf[PSSGP_DMAX * PSSGP_DMAX];  /* stationary covariance, balanced    */
   double D[PSSGP_DMAX];                  /* x = D z; then H = e_0^T            */
-  double gnorm;                          /* ||G||_1, balanced                  */
+  double gnorm;                          /* ||G||_1, balanced (information)    */
   /* Taylor tables (row-major entry e = i*d+j):
    *   F_e(h) = sum_m fc[e*PSSGP_NTAYLOR + m] h^m            (G^m / m!)
    *   Q_e(h) = h * sum_m qc[e*PSSGP_NTAYLOR + m] h^m         (W_{m+1} / (m+1)!,
    *            W_1 = W, W_{m+1} = G W_m + W_m G^T)
-   * valid for gnorm * h <= theta_max; longer steps are halved and doubled. */
+   * hthr_f[K] / hthr_q[K]: largest step h for which K terms keep the
+   * truncation below 2^-54 (relative), from the exact norms ||G^m||_1 and
+   * ||W_m||_1; steps longer than hmax are halved and doubled back. */
   double fc[PSSGP_DMAX * PSSGP_DMAX * PSSGP_NTAYLOR];
   double qc[PSSGP_DMAX * PSSGP_DMAX * PSSGP_NTAYLOR];
-  double theta_max;
-  float kthr_f[PSSGP_NTAYLOR + 1];       /* largest theta for which m terms suffice */
-  float kthr_q[PSSGP_NTAYLOR + 1];
+  double hthr_f[PSSGP_NTAYLOR + 1];
+  double hthr_q[PSSGP_NTAYLOR + 1];
+  double hmax;
+  /* companion structure (rows 0..d-2 of G have only the superdiagonal
+   * entry): then row i+1 of exp(hG) = sum of row i times rsup / rlast,
+   *   F[i+1][j] = F[i][j-1] rsup[i*d+j] + F[i][d-1] rlast[i*d+j],
+   * and only row 0 needs the Taylor series. */
+  int32_t companion;
+  int32_t reserved2;
+  double rsup[PSSGP_DMAX * PSSGP_DMAX];
+  double rlast[PSSGP_DMAX * PSSGP_DMAX];
   double lengthscale, variance;          /* metadata                            */
 } pssgp_model;
 

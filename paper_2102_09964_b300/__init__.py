@@ -44,8 +44,9 @@ class PssgpModel(ctypes.Structure):
                 ("gnorm", ctypes.c_double),
                 ("fc", ctypes.c_double * (DMAX * DMAX * NTAYLOR)),
                 ("qc", ctypes.c_double * (DMAX * DMAX * NTAYLOR)),
-                ("theta_max", ctypes.c_double),
-                ("kthr_f", ctypes.c_float * (NTAYLOR + 1)), ("kthr_q", ctypes.c_float * (NTAYLOR + 1)),
+                ("hthr_f", ctypes.c_double * (NTAYLOR + 1)), ("hthr_q", ctypes.c_double * (NTAYLOR + 1)),
+                ("hmax", ctypes.c_double), ("companion", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("rsup", ctypes.c_double * (DMAX * DMAX)), ("rlast", ctypes.c_double * (DMAX * DMAX)),
                 ("lengthscale", ctypes.c_double), ("variance", ctypes.c_double)]
 
 

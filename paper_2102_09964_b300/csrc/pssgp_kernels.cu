@@ -737,14 +737,21 @@ DevModel<D> dev_model(const pssgp_model* pm) {
   for (int i = 0; i < D; ++i)
     for (int j = i; j < D; ++j)
       for (int t = 0; t < NT; ++t) m.qc[pidx<D>(i, j)][t] = pm->qc[(i * D + j) * PSSGP_NTAYLOR + t];
-  for (int t = 0; t <= NT; ++t) { m.kthr_f[t] = pm->kthr_f[t]; m.kthr_q[t] = pm->kthr_q[t]; }
-  m.gnorm = (float)pm->gnorm;
-  m.theta_max = (float)pm->theta_max;
+  // thresholds rounded toward zero in float so that a float step never passes a
+  // bound that the double value would fail
+  for (int t = 0; t <= NT; ++t) {
+    m.hthr_f[t] = std::nextafter((float)pm->hthr_f[t], 0.0f);
+    m.hthr_q[t] = std::nextafter((float)pm->hthr_q[t], 0.0f);
+  }
+  m.hmax = std::nextafter((float)pm->hmax, 0.0f);
+  m.companion = pm->companion;
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) { m.rsup[i][j] = pm->rsup[i * D + j]; m.rlast[i][j] = pm->rlast[i * D + j]; }
   return m;
 }
 
 bool model_ok(const pssgp_model* pm) {
-  return pm && pm->d >= 1 && pm->d <= PSSGP_DMAX && pm->theta_max > 0.0 && pm->D[0] != 0.0;
+  return pm && pm->d >= 1 && pm->d <= PSSGP_DMAX && pm->hmax > 0.0 && pm->D[0] != 0.0;
 }
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PSSGP_OK : PSSGP_ECUDA; }

@@ -212,19 +212,86 @@ int finish_model(int d, int kind, const ld* G0, const ld* L0, ld q, const ld* H0
       }
     std::memcpy(Wm, T, sizeof(ld) * d * d);
   }
-  out->theta_max = 0.25;
-  out->kthr_f[0] = 0.0f;
-  out->kthr_q[0] = 0.0f;
-  for (int K = 1; K <= PSSGP_NTAYLOR; ++K) {
-    // relative truncation bounds of the two series after K terms
-    out->kthr_f[K] = 0.999f * (float)threshold([K](ld th) {
-      return powl(th, K) / factorial(K) / (1.0L - th / (K + 1));
-    });
-    out->kthr_q[K] = 0.999f * (float)threshold([K](ld th) {
-      return powl(2.0L * th, K) / factorial(K + 1) / (1.0L - 2.0L * th / (K + 2));
-    });
+  // exact norms ||G^m||_1 (m = 0..MN) and ||W_m||_1 (m = 1..MN+1) for the
+  // truncation bounds of the two series
+  constexpr int MN = 120;
+  ld gnm[MN + 1], wnm[MN + 2];
+  {
+    auto norm1 = [d](const ld* A) {
+      ld best = 0.0L;
+      for (int j = 0; j < d; ++j) {
+        ld c = 0.0L;
+        for (int i = 0; i < d; ++i) c += fabsl(A[i * d + j]);
+        best = std::max(best, c);
+      }
+      return best;
+    };
+    ld Pw[DM * DM], Ww[DM * DM], nP[DM * DM], nW[DM * DM];
+    for (int i = 0; i < d * d; ++i) Pw[i] = 0.0L;
+    for (int i = 0; i < d; ++i) Pw[i * d + i] = 1.0L;
+    for (int i = 0; i < d * d; ++i) Ww[i] = W[i];
+    wnm[0] = 0.0L;
+    for (int m = 0; m <= MN; ++m) {
+      gnm[m] = norm1(Pw);         // ||G^m||
+      wnm[m + 1] = norm1(Ww);     // ||W_{m+1}||
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+          ld a = 0.0L, bb = 0.0L;
+          for (int k = 0; k < d; ++k) {
+            a += Pw[i * d + k] * G[k * d + j];
+            bb += G[i * d + k] * Ww[k * d + j] + Ww[i * d + k] * G[j * d + k];
+          }
+          nP[i * d + j] = a;
+          nW[i * d + j] = bb;
+        }
+      std::memcpy(Pw, nP, sizeof(ld) * d * d);
+      std::memcpy(Ww, nW, sizeof(ld) * d * d);
+    }
   }
-  if (out->kthr_f[PSSGP_NTAYLOR] < 0.3f || out->kthr_q[PSSGP_NTAYLOR] < 0.3f) return PSSGP_EMODEL;
+  const ld w1 = wnm[1];
+  const ld eps = ldexpl(1.0L, -54);
+  auto tail_f = [&](int K, ld h) {       // sum_{m >= K} ||G^m|| h^m / m!
+    ld s = 0.0L, hm = powl(h, K), fm = factorial(K);
+    for (int m = K; m <= MN; ++m) { s += gnm[m] * hm / fm; hm *= h; fm *= (m + 1); }
+    return s;
+  };
+  auto tail_q = [&](int K, ld h) {       // sum_{m >= K} ||W_{m+1}|| h^m / (m+1)!  relative to ||W_1||
+    ld s = 0.0L, hm = powl(h, K), fm = factorial(K + 1);
+    for (int m = K; m < MN; ++m) { s += wnm[m + 1] * hm / fm; hm *= h; fm *= (m + 2); }
+    return s / w1;
+  };
+  auto largest_h = [&](auto tail, int K) {
+    ld lo = 0.0L, hi = 1.0L;
+    while (tail(K, hi) <= eps && hi < 1e6L) { lo = hi; hi *= 2.0L; }
+    for (int it = 0; it < 200; ++it) {
+      const ld mid = 0.5L * (lo + hi);
+      if (tail(K, mid) <= eps) lo = mid; else hi = mid;
+    }
+    return lo;
+  };
+  out->hthr_f[0] = 0.0;
+  out->hthr_q[0] = 0.0;
+  for (int K = 1; K <= PSSGP_NTAYLOR; ++K) {
+    out->hthr_f[K] = (double)(0.999L * largest_h(tail_f, K));
+    out->hthr_q[K] = (double)(0.999L * largest_h(tail_q, K));
+  }
+  out->hmax = std::min(out->hthr_f[PSSGP_NTAYLOR], out->hthr_q[PSSGP_NTAYLOR]);
+  if (!(out->hmax > 0.0)) return PSSGP_EMODEL;
+  // companion structure of the balanced drift
+  bool comp = d >= 2;
+  for (int i = 0; i + 1 < d && comp; ++i)
+    for (int j = 0; j < d; ++j)
+      if ((j == i + 1) != (G[i * d + j] != 0.0L)) comp = false;
+  out->companion = comp ? 1 : 0;
+  if (comp) {
+    for (int i = 0; i + 1 < d; ++i) {
+      const ld c = 1.0L / G[i * d + i + 1];
+      for (int j = 0; j < d; ++j) {
+        out->rsup[i * d + j] = (j >= 1) ? (double)(G[(j - 1) * d + j] * c) : 0.0;
+        out->rlast[i * d + j] = (double)(G[(d - 1) * d + j] * c);
+      }
+    }
+  }
   return PSSGP_OK;
 }
 

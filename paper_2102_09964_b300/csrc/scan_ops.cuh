@@ -20,25 +20,30 @@ __host__ __device__ constexpr int pidx(int i, int j) {   // packed upper index, 
 
 // Model constants for the kernels (passed by value: constant bank, uniform
 // across the warp).  F_e(h) = sum_m fc[e][m] h^m; Q_e(h) = h sum_m qc[e][m] h^m
-// for packed upper entries e; valid for gnorm*h <= theta_max.
+// for packed upper entries e; K terms suffice for h <= hthr_*[K]; steps longer
+// than hmax are halved and doubled back.
 template <int D>
 struct DevModel {
   double Pinf[Sym<D>::N];
   double Dsc[D];                // x = Dsc .* z
   double fc[D * D][NT];
   double qc[Sym<D>::N][NT];
-  float kthr_f[NT + 1];         // largest theta for which m terms suffice
-  float kthr_q[NT + 1];
-  float gnorm;                  // ||G||_1 (balanced), as float for term selection
-  float theta_max;
+  double rsup[D][D];            // companion row recursion (see pssgp.h)
+  double rlast[D][D];
+  float hthr_f[NT + 1];
+  float hthr_q[NT + 1];
+  float hmax;
+  int companion;
 };
 
 // ---------------------------------------------------------------------------
 // Discretisation (supplement Eq. (ss-gp-formation)): F = exp(hG),
 // Q = int_0^h e^{sG} W e^{sG}^T ds, by the Taylor series of both in h with
-// host-precomputed coefficients.  The term count is chosen per warp from the
-// largest ||G|| h in the warp (float arithmetic, off the FP64 pipe); steps with
-// ||G|| h > theta_max are halved s times and doubled back with
+// host-precomputed coefficients.  The term counts are chosen per warp from the
+// warp's longest step against bounds built from the exact norms ||G^m||, ||W_m||
+// (float arithmetic, off the FP64 pipe).  For a companion-form drift only row 0
+// of F is summed; row i+1 is row i times G scaled (2 FP64 ops per entry).
+// Steps longer than hmax are halved s times and doubled back with
 // F(2h) = F(h)^2, Q(2h) = F(h) Q(h) F(h)^T + Q(h).
 // first = true gives the prior at a series' first time: F = 0, Q = P_inf.
 // Must be called by all 32 lanes of a warp (warp reductions inside).
@@ -46,36 +51,52 @@ struct DevModel {
 template <int D>
 __device__ __forceinline__ void discretize(const DevModel<D>& m, double h, bool first, bool active,
                                            Mat<D>& F, Mat<D>& Q) {
-  float th = m.gnorm * (float)h;
+  float hf = (float)h;
   int s = 0;
-  if (active && !first && th > m.theta_max) {
-    s = (int)ceilf(log2f(th / m.theta_max));
+  if (active && !first && hf > m.hmax) {
+    s = (int)ceilf(log2f(hf / m.hmax));
     if (s < 0) s = 0;
     if (s > 60) s = 60;
-    th = ldexpf(th, -s);
+    hf = ldexpf(hf, -s);
+    if (hf > m.hmax) { ++s; hf *= 0.5f; }
   }
-  if (!active || first) th = 0.0f;
-  const unsigned kmax = __reduce_max_sync(0xffffffffu, __float_as_uint(th));
-  const float thw = __uint_as_float(kmax);
+  if (!active || first || !(hf > 0.0f)) hf = 0.0f;
+  const float hw = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(hf)));
   int kf = NT, kq = NT;
 #pragma unroll 1
-  for (int k = 1; k <= NT; ++k) if (thw <= m.kthr_f[k]) { kf = k; break; }
+  for (int k = 1; k <= NT; ++k) if (hw <= m.hthr_f[k]) { kf = k; break; }
 #pragma unroll 1
-  for (int k = 1; k <= NT; ++k) if (thw <= m.kthr_q[k]) { kq = k; break; }
+  for (int k = 1; k <= NT; ++k) if (hw <= m.hthr_q[k]) { kq = k; break; }
   const int smax = (int)__reduce_max_sync(0xffffffffu, (unsigned)s);
   double hs = (s > 0) ? h * __longlong_as_double((long long)(1023 - s) << 52) : h;
   if (first || !active) hs = 0.0;
-  // Horner in h
+  if (m.companion) {
+    // row 0 by Horner, the other rows by the companion recursion
 #pragma unroll
-  for (int i = 0; i < D; ++i)
-#pragma unroll
-    for (int j = 0; j < D; ++j) F[i][j] = m.fc[i * D + j][kf - 1];
+    for (int j = 0; j < D; ++j) F[0][j] = m.fc[j][kf - 1];
 #pragma unroll 1
-  for (int t = kf - 2; t >= 0; --t) {
+    for (int t = kf - 2; t >= 0; --t) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) F[0][j] = fma(F[0][j], hs, m.fc[j][t]);
+    }
+#pragma unroll
+    for (int i = 0; i + 1 < D; ++i) {
+      F[i + 1][0] = F[i][D - 1] * m.rlast[i][0];
+#pragma unroll
+      for (int j = 1; j < D; ++j) F[i + 1][j] = fma(F[i][j - 1], m.rsup[i][j], F[i][D - 1] * m.rlast[i][j]);
+    }
+  } else {
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
-      for (int j = 0; j < D; ++j) F[i][j] = fma(F[i][j], hs, m.fc[i * D + j][t]);
+      for (int j = 0; j < D; ++j) F[i][j] = m.fc[i * D + j][kf - 1];
+#pragma unroll 1
+    for (int t = kf - 2; t >= 0; --t) {
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) F[i][j] = fma(F[i][j], hs, m.fc[i * D + j][t]);
+    }
   }
 #pragma unroll
   for (int i = 0; i < D; ++i)

@@ -236,7 +236,7 @@ def test_small_and_ragged_sizes(N, M, kind):
 
 @pytest.mark.parametrize("kind", ["matern32", "matern52", "rbf"])
 def test_long_gaps_ties_and_missing(kind):
-    """Steps far beyond theta_max (halving + doubling path), duplicate times,
+    """Steps far beyond the longest Taylor step (halving + doubling path), duplicate times,
     long runs of missing measurements and per-step noise variances."""
     rng = np.random.default_rng(9)
     h = np.concatenate([rng.exponential(0.01, 2000), [0.0, 0.0, 3.0, 40.0, 0.0], rng.exponential(0.5, 300)])

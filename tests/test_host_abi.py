@@ -62,21 +62,30 @@ def test_model_matches_oracle(lib, kind, ell, s2, balance):
 
 
 @pytest.mark.parametrize("kind", ["matern32", "matern52", "rbf"])
-@pytest.mark.parametrize("h", [0.0, 1e-4, 3e-3, 0.008])
+@pytest.mark.parametrize("h", [0.0, 1e-4, 3e-3, 0.008, 0.03])
 def test_taylor_tables_reproduce_discretisation(lib, kind, h):
-    """F(h) = sum_m fc h^m and Q(h) = h sum_m qc h^m (as the device evaluates
-    them, with the term count from the model's thresholds) equal exp(G h) and
-    the Van Loan integral of Eq. (ss-gp-formation), computed here by scipy."""
+    """F(h) (row 0 by the series, other rows by the companion recursion) and
+    Q(h) = h sum_m qc h^m, with the term counts picked from the model's step
+    thresholds, equal exp(G h) and the Van Loan integral of Eq.
+    (ss-gp-formation), computed here by scipy."""
     m = P.build_model(kind, 1.0, 1.0)
     d = m.d
     G, W = m.matrix("G"), m.matrix("W")
-    theta = m.raw.gnorm * h
-    assert theta <= m.raw.theta_max
-    kf = next(k for k in range(1, 17) if theta <= m.raw.kthr_f[k])
-    kq = next(k for k in range(1, 17) if theta <= m.raw.kthr_q[k])
+    assert h <= m.raw.hmax
+    kf = next(k for k in range(1, 17) if h <= m.raw.hthr_f[k])
+    kq = next(k for k in range(1, 17) if h <= m.raw.hthr_q[k])
     fc = np.array(m.raw.fc[:]).reshape(8 * 8, 16)[: d * d]
     qc = np.array(m.raw.qc[:]).reshape(8 * 8, 16)[: d * d]
-    F = sum(fc[:, t] * h ** t for t in range(kf)).reshape(d, d)
+    assert m.raw.companion == 1
+    rsup = np.array(m.raw.rsup[:64])[: d * d].reshape(d, d)
+    rlast = np.array(m.raw.rlast[:64])[: d * d].reshape(d, d)
+    F = np.zeros((d, d))
+    F[0] = sum(fc[:d, t] * h ** t for t in range(kf))
+    for i in range(d - 1):
+        F[i + 1, 0] = F[i, d - 1] * rlast[i, 0]
+        for j in range(1, d):
+            F[i + 1, j] = F[i, j - 1] * rsup[i, j] + F[i, d - 1] * rlast[i, j]
+    Ffull = sum(fc[:, t] * h ** t for t in range(kf)).reshape(d, d)
     Q = h * sum(qc[:, t] * h ** t for t in range(kq)).reshape(d, d)
     Fr = expm(G * h)
     C = np.zeros((2 * d, 2 * d))
@@ -86,13 +95,20 @@ def test_taylor_tables_reproduce_discretisation(lib, kind, h):
     E = expm(C)
     Qr = E[d:, d:].T @ E[:d, d:]
     assert np.abs(F - Fr).max() <= 4e-16 * max(1.0, np.abs(Fr).max())
+    assert np.abs(Ffull - Fr).max() <= 4e-16 * max(1.0, np.abs(Fr).max())
     assert np.abs(Q - Qr).max() <= 1e-14 * max(np.abs(Qr).max(), 1e-300) + 1e-300
 
 
-def test_thresholds_cover_theta_max(lib):
+def test_thresholds_are_monotone_and_bounded(lib):
     m = P.build_model("rbf", 1.0, 1.0)
-    assert m.raw.kthr_f[16] >= m.raw.theta_max and m.raw.kthr_q[16] >= m.raw.theta_max
-    assert all(m.raw.kthr_f[k] <= m.raw.kthr_f[k + 1] for k in range(16))
+    assert m.raw.hmax > 0.03
+    assert all(m.raw.hthr_f[k] <= m.raw.hthr_f[k + 1] for k in range(16))
+    assert all(m.raw.hthr_q[k] <= m.raw.hthr_q[k + 1] for k in range(16))
+    # a user drift that is not in companion form uses the full series
+    o = om.make_model("matern52", 1.0, 1.0)
+    Gm = o.G.copy()
+    Gm[0, 2] = 0.1
+    assert P.model_from_sde(Gm, o.L, o.q, o.H).raw.companion == 0
 
 
 @pytest.mark.parametrize("order", [1, 2, 3, 4, 5, 6, 7, 8])
