@@ -354,15 +354,16 @@ def run_ours(args, wl_params):
         "filter_propagate": n * (flops_kf_step(d, obs) + flops_smoother_element(d) + flops_smoother_fold(d)),
         "smoother_propagate": n * flops_rts_step(d),
     }
+    ts = max(args.timing_steps, 1)
     kernels = {}
     for name, (tot, cnt) in per.items():
-        avg = tot / cnt
-        kernels[name] = {"ms": round(avg, 4), "share": None}
-    tot_all = sum(v["ms"] for v in kernels.values())
+        kernels[name] = {"ms_per_step": round(tot / ts, 4), "launches_per_step": cnt // ts,
+                         "ms_per_launch": round(tot / cnt, 4), "share": None}
+    tot_all = sum(v["ms_per_step"] for v in kernels.values())
     for v in kernels.values():
-        v["share"] = round(v["ms"] / tot_all, 4)
-    dom = max((k for k in alg if k in kernels), key=lambda k: kernels[k]["ms"])
-    achieved = alg[dom] / (kernels[dom]["ms"] * 1e-3) / 1e12
+        v["share"] = round(v["ms_per_step"] / tot_all, 4)
+    dom = max((k for k in alg if k in kernels), key=lambda k: kernels[k]["ms_per_step"])
+    achieved = alg[dom] / (kernels[dom]["ms_per_launch"] * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_tflops, 4), "unit": "TFLOP/s",
                 "frac": round(achieved / peak_tflops, 4), "traffic": None, "kernel": dom,
                 "peak_source": "measured FP64 FMA rate of this GPU (pssgp_fp64_fma_rate, x2 flops)",

@@ -11,7 +11,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SOURCES = [os.path.join(HERE, "csrc", "pssgp_kernels.cu"), os.path.join(HERE, "csrc", "pssgp_model.cpp")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("linalg.cuh", "scan_ops.cuh")] + \
+DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("linalg.cuh", "scan_ops.cuh", "warp_ops.cuh")] + \
     [os.path.join(ROOT, "include", "pssgp.h")]
 LIB = os.path.join(HERE, "libpssgp.so")
 NVCC = os.environ.get("NVCC", "nvcc")

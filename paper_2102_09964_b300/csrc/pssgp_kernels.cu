@@ -30,6 +30,7 @@
 
 #include "../../include/pssgp.h"
 #include "scan_ops.cuh"
+#include "warp_ops.cuh"
 
 using namespace pssgp;
 
@@ -291,22 +292,27 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
   flag(a.status, bits);
 }
 
-// filter level 2: one Kogge-Stone round over the warp aggregates
+// filter level 2: one Kogge-Stone round over the warp aggregates, one warp
+// per element (warp-cooperative operator, see warp_ops.cuh)
 template <int D>
 __global__ void __launch_bounds__(BLOCK) k_filter_ks(const double* in, double* out, int64_t P2, int64_t off,
                                                      int* status) {
-  const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
-  if (i >= P2) return;
-  FAgg<D> b;
-  load_fagg<D>(in + i, P2, b);
-  if (i >= off) {
-    FAgg<D> a, r;
-    load_fagg<D>(in + i - off, P2, a);
-    if (!fagg_combine<D>(a, b, r)) flag(status, PSSGP_ENOTPD);
-    store_fagg<D>(out + i, P2, r);
-  } else {
-    store_fagg<D>(out + i, P2, b);
+  constexpr int NF = FAggSize<D>::N;
+  __shared__ double sm[BLOCK / 32][WarpFilterSmem<D>::N];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (BLOCK / 32) + wid;
+  if (i >= P2) return;                       // whole warp
+  if (i < off) {
+    for (int e = lane; e < NF; e += 32) out[e * P2 + i] = in[e * P2 + i];
+    return;
   }
+  double* sa = sm[wid];
+  double* sb = sa + NF;
+  double* work = sb + NF;
+  for (int e = lane; e < NF; e += 32) { sa[e] = in[e * P2 + i - off]; sb[e] = in[e * P2 + i]; }
+  __syncwarp();
+  const bool ok = warp_fagg_combine<D>(sa, sb, work, out + i, P2, lane);
+  if (!ok && lane == 0) flag(status, PSSGP_ENOTPD);
 }
 
 // natural log of a product of positive numbers kept as mantissa and binary
@@ -454,21 +460,25 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
   flag(a.status, bits);
 }
 
-// smoother level 2: one Kogge-Stone round of the suffix scan
+// smoother level 2: one Kogge-Stone round of the suffix scan, one warp per
+// element
 template <int D>
 __global__ void __launch_bounds__(BLOCK) k_smoother_ks(const double* in, double* out, int64_t P2, int64_t off) {
-  const int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  constexpr int NS = SAggSize<D>::N;
+  __shared__ double sm[BLOCK / 32][WarpSmootherSmem<D>::N];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (BLOCK / 32) + wid;
   if (i >= P2) return;
-  SAgg<D> a;
-  load_sagg<D>(in + i, P2, a);
-  if (i + off < P2) {
-    SAgg<D> b, r;
-    load_sagg<D>(in + i + off, P2, b);
-    sagg_combine<D>(a, b, r);
-    store_sagg<D>(out + i, P2, r);
-  } else {
-    store_sagg<D>(out + i, P2, a);
+  if (i + off >= P2) {
+    for (int e = lane; e < NS; e += 32) out[e * P2 + i] = in[e * P2 + i];
+    return;
   }
+  double* sa = sm[wid];
+  double* sb = sa + NS;
+  double* work = sb + NS;
+  for (int e = lane; e < NS; e += 32) { sa[e] = in[e * P2 + i]; sb[e] = in[e * P2 + i + off]; }
+  __syncwarp();
+  warp_sagg_combine<D>(sa, sb, work, out + i, P2, lane);
 }
 
 // smoother level 3: backward recursion through the chunk,
@@ -781,7 +791,7 @@ template <int D>
 const double* run_filter_level2(const Plan& p, double* buf0, int* status, cudaStream_t s) {
   double* in = buf0;
   double* out = buf0 + p.P2 * p.nf;
-  const int grid = (int)((p.P2 + BLOCK - 1) / BLOCK);
+  const int grid = (int)((p.P2 + BLOCK / 32 - 1) / (BLOCK / 32));
   for (int64_t off = 1; off < p.P2; off <<= 1) {
     Timed tm(s, T_FL2);
     k_filter_ks<D><<<grid, BLOCK, 0, s>>>(in, out, p.P2, off, status);
@@ -793,7 +803,7 @@ template <int D>
 const double* run_smoother_level2(const Plan& p, double* buf0, cudaStream_t s) {
   double* in = buf0;
   double* out = buf0 + p.P2 * p.ns;
-  const int grid = (int)((p.P2 + BLOCK - 1) / BLOCK);
+  const int grid = (int)((p.P2 + BLOCK / 32 - 1) / (BLOCK / 32));
   for (int64_t off = 1; off < p.P2; off <<= 1) {
     Timed tm(s, T_SL2);
     k_smoother_ks<D><<<grid, BLOCK, 0, s>>>(in, out, p.P2, off);
