@@ -239,16 +239,37 @@ __device__ __forceinline__ void load_egl(const double* rec, int64_t k, SAgg<D>& 
 // ---------------------------------------------------------------------------
 // filter levels 0 + 1: discretise, fold the chunk's elements, warp scan
 // ---------------------------------------------------------------------------
+// shared memory of k_filter_reduce: A (two buffers), J (packed) and eta per
+// thread, entry-major with stride BLOCK
+template <int D> constexpr int reduce_smem_doubles() { return (2 * D * D + Sym<D>::N + D) * BLOCK; }
+
 template <int D>
 __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m, const ScanArgs a) {
+  extern __shared__ double smem[];
+  double* sA0 = smem + threadIdx.x;
+  double* sA1 = sA0 + D * D * BLOCK;
+  double* sJ = sA1 + D * D * BLOCK;
+  double* seta = sJ + Sym<D>::N * BLOCK;
   const int64_t g = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int64_t k0 = g * a.L;
   const int64_t k1 = min(k0 + a.L, a.n);
   int bits = 0;
   bool bad = false;
-  FAgg<D> ag;
-  fagg_identity<D>(ag);
+  // chunk aggregate starts as the identity of the operator
+  Vec<D> b;
+  Mat<D> C;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    b[i] = 0.0;
+    seta[i * BLOCK] = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) { C[i][j] = 0.0; sA0[(i * D + j) * BLOCK] = (i == j) ? 1.0 : 0.0; }
+  }
+#pragma unroll
+  for (int e = 0; e < Sym<D>::N; ++e) sJ[e * BLOCK] = 0.0;
+  double* Ain = sA0;
+  double* Aout = sA1;
   double tprev = (k0 > 0 && k0 < a.n) ? a.t[k0 - 1] : 0.0;
   const double R0 = a.R ? a.R[0] : a.R_scalar;
 #pragma unroll 1
@@ -271,7 +292,22 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
       const double yk = a.y[k];
       const double Rk = a.R_per_step ? a.R[k] : R0;
       if (obs && nonfinite(yk)) bits |= PSSGP_ENAN;
-      fagg_fold_step<D>(ag, F, Q, obs, yk, Rk, bad);
+      fagg_fold_step_smem<D, BLOCK>(b, C, Ain, Aout, sJ, seta, F, Q, obs, yk, Rk, bad);
+      double* tsw = Ain;
+      Ain = Aout;
+      Aout = tsw;
+    }
+  }
+  FAgg<D> ag;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    ag.b[i] = b[i];
+    ag.eta[i] = seta[i * BLOCK];
+#pragma unroll
+    for (int jj = 0; jj < D; ++jj) {
+      ag.A[i][jj] = Ain[(i * D + jj) * BLOCK];
+      ag.C[i][jj] = C[i][jj];
+      ag.J[i][jj] = sJ[(i <= jj ? pidx<D>(i, jj) : pidx<D>(jj, i)) * BLOCK];
     }
   }
   if (a.dbg_agg) store_fagg<D>(a.dbg_agg + g, a.P0, ag);
@@ -816,8 +852,14 @@ template <int D>
 void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s) {
   const int grid = (int)(p.P0 / BLOCK);
   {
+    constexpr int smem = reduce_smem_doubles<D>() * 8;
+    static bool attr_set = false;     // per instantiation (and per process)
+    if (!attr_set) {
+      cudaFuncSetAttribute(k_filter_reduce<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      attr_set = true;
+    }
     Timed tm(s, T_FRED);
-    k_filter_reduce<D><<<grid, BLOCK, 0, s>>>(m, a);
+    k_filter_reduce<D><<<grid, BLOCK, smem, s>>>(m, a);
   }
   a.wfin_f = run_filter_level2<D>(p, a.wagg_f, a.status, s);
   {

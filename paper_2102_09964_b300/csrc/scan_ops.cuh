@@ -210,6 +210,100 @@ __device__ __forceinline__ void fagg_fold_step(FAgg<D>& a, const Mat<D>& F, cons
   }
 }
 
+// The same fold with the chunk aggregate split between registers (b, C) and
+// shared memory (A double-buffered, J and eta; element e of a thread's
+// matrix at ptr[e * SST], so a warp's accesses hit 32 consecutive banks).
+// P^- = F C F^T + Q is built one row of F C at a time, and A' = F A row by
+// row, which keeps the register footprint low enough to avoid spills.
+template <int D, int SST>
+__device__ __forceinline__ void fagg_fold_step_smem(Vec<D>& b, Mat<D>& C, const double* __restrict__ Ain,
+                                                    double* __restrict__ Aout, double* __restrict__ J,
+                                                    double* __restrict__ eta, const Mat<D>& F, const Mat<D>& Q,
+                                                    bool observed, double y, double R, bool& bad) {
+  Mat<D> Pm;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double t[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      double s = F[i][0] * C[0][k];
+#pragma unroll
+      for (int l = 1; l < D; ++l) s = fma(F[i][l], C[l][k], s);
+      t[k] = s;
+    }
+#pragma unroll
+    for (int j = i; j < D; ++j) {
+      double s = Q[i][j];
+#pragma unroll
+      for (int k = 0; k < D; ++k) s = fma(t[k], F[j][k], s);
+      Pm[i][j] = s;
+      Pm[j][i] = s;
+    }
+  }
+  Vec<D> bm, w;
+  mulv<D>(F, b, bm);
+  // w = row 0 of F A
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    double s = F[0][0] * Ain[(0 * D + j) * SST];
+#pragma unroll
+    for (int k = 1; k < D; ++k) s = fma(F[0][k], Ain[(k * D + j) * SST], s);
+    w[j] = s;
+  }
+  if (observed) {
+    const double S = Pm[0][0] + R;
+    if (bad_pos(S)) bad = true;
+    const double Si = __drcp_rn(S);
+    const double r = y - bm[0];
+    Vec<D> K;
+#pragma unroll
+    for (int i = 0; i < D; ++i) K[i] = Pm[i][0] * Si;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const double wsi = w[i] * Si;
+#pragma unroll
+      for (int j = i; j < D; ++j) J[pidx<D>(i, j) * SST] = fma(wsi, w[j], J[pidx<D>(i, j) * SST]);
+      eta[i * SST] = fma(wsi, r, eta[i * SST]);
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      b[i] = fma(K[i], r, bm[i]);
+#pragma unroll
+      for (int j = i; j < D; ++j) { C[i][j] = fma(-K[i], Pm[0][j], Pm[i][j]); C[j][i] = C[i][j]; }
+    }
+    // A' = (F A) - K w, row by row (row 0 of F A is w)
+#pragma unroll
+    for (int j = 0; j < D; ++j) Aout[(0 * D + j) * SST] = fma(-K[0], w[j], w[j]);
+#pragma unroll
+    for (int i = 1; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        double s = F[i][0] * Ain[(0 * D + j) * SST];
+#pragma unroll
+        for (int k = 1; k < D; ++k) s = fma(F[i][k], Ain[(k * D + j) * SST], s);
+        Aout[(i * D + j) * SST] = fma(-K[i], w[j], s);
+      }
+  } else {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      b[i] = bm[i];
+#pragma unroll
+      for (int j = 0; j < D; ++j) C[i][j] = Pm[i][j];
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) Aout[(0 * D + j) * SST] = w[j];
+#pragma unroll
+    for (int i = 1; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        double s = F[i][0] * Ain[(0 * D + j) * SST];
+#pragma unroll
+        for (int k = 1; k < D; ++k) s = fma(F[i][k], Ain[(k * D + j) * SST], s);
+        Aout[(i * D + j) * SST] = s;
+      }
+  }
+}
+
 // General filtering operator of Sec. 3, o = a (earlier) x b (later):
 //   M = I + C_a J_b,  X_A = M^{-1} A_a,  x_b = M^{-1}(b_a + C_a eta_b),
 //   X_C = M^{-1} C_a,  v = eta_b - J_b b_a,  x_v = M^{-1} C_a v,
