@@ -350,7 +350,8 @@ def run_ours(args, wl_params):
     d = m.d
     obs = N / n
     alg = {
-        "filter_reduce": n * (flops_discretize(d, kf, kq, bool(m.raw.companion)) + flops_filter_fold(d, obs)),
+        "discretize": n * flops_discretize(d, kf, kq, bool(m.raw.companion)),
+        "filter_reduce": n * flops_filter_fold(d, obs),
         "filter_propagate": n * (flops_kf_step(d, obs) + flops_smoother_element(d) + flops_smoother_fold(d)),
         "smoother_propagate": n * flops_rts_step(d),
     }

@@ -239,6 +239,31 @@ __device__ __forceinline__ void load_egl(const double* rec, int64_t k, SAgg<D>& 
 // ---------------------------------------------------------------------------
 // filter levels 0 + 1: discretise, fold the chunk's elements, warp scan
 // ---------------------------------------------------------------------------
+// discretisation into the per-step records, one thread per step; a series'
+// first step (k = 0) gets F = 0, Q = P_inf.  Also checks the times.
+constexpr int DISC_BLOCK = 256;
+template <int D>
+__global__ void __launch_bounds__(DISC_BLOCK) k_discretize_rec(const DevModel<D> m, const double* t, int64_t n,
+                                                             double* rec, int* status) {
+  const int64_t k = (int64_t)blockIdx.x * DISC_BLOCK + threadIdx.x;
+  const bool act = k < n;
+  const bool first = (k == 0);
+  double h = 0.0;
+  int bits = 0;
+  if (act) {
+    const double t1 = t[k];
+    if (nonfinite(t1)) bits |= PSSGP_ENAN;
+    if (!first) {
+      h = t1 - t[k - 1];
+      if (negative_nonzero(h)) bits |= PSSGP_EUNSORTED;
+    }
+  }
+  Mat<D> F, Q;
+  discretize<D>(m, h, first, act, F, Q);
+  if (act) store_fq<D>(rec, k, F, Q);
+  flag(status, bits);
+}
+
 // shared memory of k_filter_reduce: A (two buffers), J (packed) and eta per
 // thread, entry-major with stride BLOCK
 template <int D> constexpr int reduce_smem_doubles() { return (2 * D * D + Sym<D>::N + D) * BLOCK; }
@@ -270,33 +295,19 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
   for (int e = 0; e < Sym<D>::N; ++e) sJ[e * BLOCK] = 0.0;
   double* Ain = sA0;
   double* Aout = sA1;
-  double tprev = (k0 > 0 && k0 < a.n) ? a.t[k0 - 1] : 0.0;
   const double R0 = a.R ? a.R[0] : a.R_scalar;
 #pragma unroll 1
-  for (int64_t j = 0; j < a.L; ++j) {          // trip count uniform across the warp
-    const int64_t k = k0 + j;
-    const bool act = k < k1;
-    const double tk = act ? a.t[k] : tprev;
-    const double h = tk - tprev;
-    tprev = tk;
-    const bool first = (k == 0);
-    if (act) {
-      if (nonfinite(tk)) bits |= PSSGP_ENAN;
-      if (!first && negative_nonzero(h)) bits |= PSSGP_EUNSORTED;
-    }
+  for (int64_t k = k0; k < k1; ++k) {
     Mat<D> F, Q;
-    discretize<D>(m, h, first, act, F, Q);
-    if (act) {
-      store_fq<D>(a.rec_fq, k, F, Q);
-      const bool obs = a.mask[k] != 0;
-      const double yk = a.y[k];
-      const double Rk = a.R_per_step ? a.R[k] : R0;
-      if (obs && nonfinite(yk)) bits |= PSSGP_ENAN;
-      fagg_fold_step_smem<D, BLOCK>(b, C, Ain, Aout, sJ, seta, F, Q, obs, yk, Rk, bad);
-      double* tsw = Ain;
-      Ain = Aout;
-      Aout = tsw;
-    }
+    load_fq<D>(a.rec_fq, k, F, Q);
+    const bool obs = a.mask[k] != 0;
+    const double yk = a.y[k];
+    const double Rk = a.R_per_step ? a.R[k] : R0;
+    if (obs && nonfinite(yk)) bits |= PSSGP_ENAN;
+    fagg_fold_step_smem<D, BLOCK>(b, C, Ain, Aout, sJ, seta, F, Q, obs, yk, Rk, bad);
+    double* tsw = Ain;
+    Ain = Aout;
+    Aout = tsw;
   }
   FAgg<D> ag;
 #pragma unroll
@@ -851,6 +862,11 @@ const double* run_smoother_level2(const Plan& p, double* buf0, cudaStream_t s) {
 template <int D>
 void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s) {
   const int grid = (int)(p.P0 / BLOCK);
+  {
+    Timed tm(s, T_DISC);
+    k_discretize_rec<D><<<(unsigned)((p.n + DISC_BLOCK - 1) / DISC_BLOCK), DISC_BLOCK, 0, s>>>(m, a.t, p.n, a.rec_fq,
+                                                                                               a.status);
+  }
   {
     constexpr int smem = reduce_smem_doubles<D>() * 8;
     static bool attr_set = false;     // per instantiation (and per process)
