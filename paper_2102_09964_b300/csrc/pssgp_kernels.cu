@@ -240,12 +240,18 @@ __device__ __forceinline__ void load_egl(const double* rec, int64_t k, SAgg<D>& 
 // filter levels 0 + 1: discretise, fold the chunk's elements, warp scan
 // ---------------------------------------------------------------------------
 // discretisation into the per-step records, one thread per step; a series'
-// first step (k = 0) gets F = 0, Q = P_inf.  Also checks the times.
-constexpr int DISC_BLOCK = 256;
+// first step (k = 0) gets F = 0, Q = P_inf.  Also checks the times.  The
+// block's records (consecutive steps, contiguous in memory) are staged in
+// shared memory and written out with consecutive threads on consecutive
+// addresses.
+constexpr int DISC_BLOCK = 128;
 template <int D>
 __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_rec(const DevModel<D> m, const double* t, int64_t n,
                                                              double* rec, int* status) {
-  const int64_t k = (int64_t)blockIdx.x * DISC_BLOCK + threadIdx.x;
+  constexpr int FQS = fqs_of<D>();
+  extern __shared__ double stage[];           // DISC_BLOCK * FQS doubles
+  const int64_t k0 = (int64_t)blockIdx.x * DISC_BLOCK;
+  const int64_t k = k0 + threadIdx.x;
   const bool act = k < n;
   const bool first = (k == 0);
   double h = 0.0;
@@ -260,7 +266,11 @@ __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_rec(const DevModel<D>
   }
   Mat<D> F, Q;
   discretize<D>(m, h, first, act, F, Q);
-  if (act) store_fq<D>(rec, k, F, Q);
+  store_fq<D>(stage, threadIdx.x, F, Q);     // record threadIdx.x of the block
+  __syncthreads();
+  const int64_t nrec = min((int64_t)DISC_BLOCK, n - k0);
+  double* dst = rec + k0 * FQS;
+  for (int64_t e = threadIdx.x; e < nrec * FQS; e += DISC_BLOCK) dst[e] = stage[e];
   flag(status, bits);
 }
 
@@ -864,8 +874,8 @@ void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s
   const int grid = (int)(p.P0 / BLOCK);
   {
     Timed tm(s, T_DISC);
-    k_discretize_rec<D><<<(unsigned)((p.n + DISC_BLOCK - 1) / DISC_BLOCK), DISC_BLOCK, 0, s>>>(m, a.t, p.n, a.rec_fq,
-                                                                                               a.status);
+    k_discretize_rec<D><<<(unsigned)((p.n + DISC_BLOCK - 1) / DISC_BLOCK), DISC_BLOCK,
+                          DISC_BLOCK * fqs_of<D>() * 8, s>>>(m, a.t, p.n, a.rec_fq, a.status);
   }
   {
     constexpr int smem = reduce_smem_doubles<D>() * 8;

@@ -48,6 +48,22 @@ struct DevModel {
 // first = true gives the prior at a series' first time: F = 0, Q = P_inf.
 // Must be called by all 32 lanes of a warp (warp reductions inside).
 // ---------------------------------------------------------------------------
+// s doublings F <- F F, Q <- F Q F^T + Q (kept out of line: rare path)
+template <int D>
+__device__ __noinline__ void double_steps(Mat<D>& F, Mat<D>& Q, int s, int smax) {
+#pragma unroll 1
+  for (int r = 0; r < smax; ++r) {
+    if (r < s) {
+      Mat<D> T, Q2, F2;
+      mul<D>(F, Q, T);
+      mul_Bt_sym_add<D>(T, F, Q, Q2);
+      mul<D>(F, F, F2);
+      copy<D>(Q2, Q);
+      copy<D>(F2, F);
+    }
+  }
+}
+
 template <int D>
 __device__ __forceinline__ void discretize(const DevModel<D>& m, double h, bool first, bool active,
                                            Mat<D>& F, Mat<D>& Q) {
@@ -114,17 +130,7 @@ __device__ __forceinline__ void discretize(const DevModel<D>& m, double h, bool 
 #pragma unroll
     for (int j = i; j < D; ++j) { Q[i][j] *= hs; Q[j][i] = Q[i][j]; }
   // doubling for long steps (rare; each lane applies its own count)
-#pragma unroll 1
-  for (int r = 0; r < smax; ++r) {
-    if (r < s) {
-      Mat<D> T, Q2, F2;
-      mul<D>(F, Q, T);
-      mul_Bt_sym_add<D>(T, F, Q, Q2);
-      mul<D>(F, F, F2);
-      copy<D>(Q2, Q);
-      copy<D>(F2, F);
-    }
-  }
+  if (smax > 0) double_steps<D>(F, Q, s, smax);
   if (first) {
 #pragma unroll
     for (int i = 0; i < D; ++i)
