@@ -92,6 +92,20 @@ struct Timed {
   }
 };
 
+// first CUDA error seen since the start of the current entry-point call (host
+// thread): every launch is followed by after_launch(), so an error cannot be
+// masked by later runtime calls
+thread_local cudaError_t t_first_err = cudaSuccess;
+inline void begin_call() { t_first_err = cudaSuccess; (void)cudaGetLastError(); }
+inline void after_launch() {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess && t_first_err == cudaSuccess) t_first_err = e;
+}
+inline int end_call() {
+  after_launch();
+  return t_first_err == cudaSuccess ? PSSGP_OK : PSSGP_ECUDA;
+}
+
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 int64_t align256(int64_t b) { return round_up(b, 256); }
 
@@ -852,6 +866,7 @@ const double* run_filter_level2(const Plan& p, double* buf0, int* status, cudaSt
   for (int64_t off = 1; off < p.P2; off <<= 1) {
     Timed tm(s, T_FL2);
     k_filter_ks<D><<<grid, BLOCK, 0, s>>>(in, out, p.P2, off, status);
+    after_launch();
     std::swap(in, out);
   }
   return in;
@@ -864,6 +879,7 @@ const double* run_smoother_level2(const Plan& p, double* buf0, cudaStream_t s) {
   for (int64_t off = 1; off < p.P2; off <<= 1) {
     Timed tm(s, T_SL2);
     k_smoother_ks<D><<<grid, BLOCK, 0, s>>>(in, out, p.P2, off);
+    after_launch();
     std::swap(in, out);
   }
   return in;
@@ -874,23 +890,25 @@ void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s
   const int grid = (int)(p.P0 / BLOCK);
   {
     Timed tm(s, T_DISC);
-    k_discretize_rec<D><<<(unsigned)((p.n + DISC_BLOCK - 1) / DISC_BLOCK), DISC_BLOCK,
-                          DISC_BLOCK * fqs_of<D>() * 8, s>>>(m, a.t, p.n, a.rec_fq, a.status);
+    constexpr int dsmem = DISC_BLOCK * fqs_of<D>() * 8;
+    // opt in to > 48 KB of dynamic shared memory (per device; cheap host call)
+    cudaFuncSetAttribute(k_discretize_rec<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem);
+    k_discretize_rec<D><<<(unsigned)((p.n + DISC_BLOCK - 1) / DISC_BLOCK), DISC_BLOCK, dsmem, s>>>(
+        m, a.t, p.n, a.rec_fq, a.status);
+    after_launch();
   }
   {
     constexpr int smem = reduce_smem_doubles<D>() * 8;
-    static bool attr_set = false;     // per instantiation (and per process)
-    if (!attr_set) {
-      cudaFuncSetAttribute(k_filter_reduce<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      attr_set = true;
-    }
+    cudaFuncSetAttribute(k_filter_reduce<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     Timed tm(s, T_FRED);
     k_filter_reduce<D><<<grid, BLOCK, smem, s>>>(m, a);
+    after_launch();
   }
   a.wfin_f = run_filter_level2<D>(p, a.wagg_f, a.status, s);
   {
     Timed tm(s, T_FPROP);
     k_filter_propagate<D><<<grid, BLOCK, 0, s>>>(m, a);
+    after_launch();
   }
 }
 template <int D>
@@ -899,6 +917,7 @@ void run_smoother_tail(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStr
   a.wfin_s = run_smoother_level2<D>(p, a.wagg_s, s);
   Timed tm(s, T_SPROP);
   k_smoother_propagate<D><<<grid, BLOCK, 0, s>>>(m, a);
+  after_launch();
 }
 
 int check_ws(const Plan& p, void* ws, size_t ws_bytes) {
@@ -929,6 +948,7 @@ int check_small_ws(void* ws, size_t ws_bytes) {
 int filter_common(const pssgp_model* model, const double* t, const double* y, const uint8_t* mask, const double* R,
                   int32_t R_per_step, int64_t n, double* xf, double* Pf, int64_t ld, double* loglik, void* ws,
                   size_t ws_bytes, void* stream, int64_t lanes, double* dbg) {
+  begin_call();
   if (!model_ok(model) || !t || !y || !mask || !R || n < 1) return PSSGP_EINVAL;
   if ((xf || Pf) && ld < n) return PSSGP_EINVAL;
   const Plan p = make_plan(model->d, n, lanes);
@@ -948,8 +968,9 @@ int filter_common(const pssgp_model* model, const double* t, const double* y, co
   if (loglik) {
     Timed tm(s, T_LL);
     k_loglik_reduce<<<1, 256, 0, s>>>(a.llp, p.P0, loglik);
+    after_launch();
   }
-  return cuda_rc(cudaGetLastError());
+  return end_call();
 }
 
 }  // namespace
@@ -975,6 +996,7 @@ extern "C" int pssgp_get_status(void* ws, void* stream, int32_t* status) {
 extern "C" int pssgp_merge(const double* t_train, const double* y_train, int64_t N, const double* t_test, int64_t M,
                            double* t, double* y, uint8_t* mask, int64_t* test_pos, void* ws, size_t ws_bytes,
                            void* stream) {
+  begin_call();
   if (!t_train || !y_train || !t || !y || !mask || N < 0 || M < 0 || N + M < 1) return PSSGP_EINVAL;
   if (M > 0 && (!t_test || !test_pos)) return PSSGP_EINVAL;
   int rc = check_small_ws(ws, ws_bytes);
@@ -985,11 +1007,13 @@ extern "C" int pssgp_merge(const double* t_train, const double* y_train, int64_t
   const int64_t threads = (N + M + MERGE_ITEMS - 1) / MERGE_ITEMS;
   k_merge<<<(unsigned)((threads + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(t_train, y_train, N, t_test, M, t, y, mask,
                                                                        test_pos, status);
-  return cuda_rc(cudaGetLastError());
+  after_launch();
+  return end_call();
 }
 
 extern "C" int pssgp_discretize(const pssgp_model* model, const double* t, int64_t n, double* F, double* Q,
                                 int64_t ld, void* ws, size_t ws_bytes, void* stream) {
+  begin_call();
   if (!model_ok(model) || !t || !F || !Q || n < 1 || ld < n) return PSSGP_EINVAL;
   int rc = check_small_ws(ws, ws_bytes);
   if (rc) return rc;
@@ -997,8 +1021,8 @@ extern "C" int pssgp_discretize(const pssgp_model* model, const double* t, int64
   int* status = static_cast<int*>(ws);
   if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return PSSGP_ECUDA;
   const unsigned grid = (unsigned)((n + BLOCK - 1) / BLOCK);
-  PSSGP_DISPATCH(model->d, k_discretize<D><<<grid, BLOCK, 0, s>>>(dev_model<D>(model), t, n, F, Q, ld, status));
-  return cuda_rc(cudaGetLastError());
+  PSSGP_DISPATCH(model->d, k_discretize<D><<<grid, BLOCK, 0, s>>>(dev_model<D>(model), t, n, F, Q, ld, status); after_launch());
+  return end_call();
 }
 
 extern "C" int pssgp_filter(const pssgp_model* model, const double* t, const double* y, const uint8_t* mask,
@@ -1018,6 +1042,7 @@ extern "C" int pssgp_loglik(const pssgp_model* model, const double* t, const dou
 extern "C" int pssgp_smooth(const pssgp_model* model, const double* t, const double* xf, const double* Pf, int64_t n,
                             int64_t ld, double* f_mean, double* f_var, double* xs, double* Ps, void* ws,
                             size_t ws_bytes, void* stream) {
+  begin_call();
   if (!model_ok(model) || !t || !xf || !Pf || n < 1 || ld < n) return PSSGP_EINVAL;
   const Plan p = make_plan(model->d, n, 0);
   const int rc = check_ws(p, ws, ws_bytes);
@@ -1034,15 +1059,17 @@ extern "C" int pssgp_smooth(const pssgp_model* model, const double* t, const dou
     {
       Timed tm(s, T_SELEM);
       k_smoother_elements<D><<<grid, BLOCK, 0, s>>>(m, a, xf, Pf);
+      after_launch();
     }
     run_smoother_tail<D>(m, p, a, s);
   });
-  return cuda_rc(cudaGetLastError());
+  return end_call();
 }
 
 extern "C" int pssgp_predict(const pssgp_model* model, const double* t_train, const double* y_train, int64_t N,
                              const double* t_test, int64_t M, double R, double* mean_test, double* var_test,
                              double* loglik, void* ws, size_t ws_bytes, void* stream) {
+  begin_call();
   if (!model_ok(model) || !t_train || !y_train || N < 1 || M < 0) return PSSGP_EINVAL;
   if (M > 0 && (!t_test || !mean_test || !var_test)) return PSSGP_EINVAL;
   if (!(R > 0.0) || !std::isfinite(R)) return PSSGP_EINVAL;
@@ -1064,6 +1091,7 @@ extern "C" int pssgp_predict(const pssgp_model* model, const double* t_train, co
     Timed tm(s, T_MERGE);
     k_merge<<<(unsigned)((threads + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(t_train, y_train, N, t_test, M, t, y, mask,
                                                                          tpos, a.status);
+    after_launch();
   }
   a.t = t; a.y = y; a.mask = mask; a.R = nullptr; a.R_scalar = R; a.R_per_step = 0;
   a.fuse_smoother = 1;
@@ -1077,12 +1105,14 @@ extern "C" int pssgp_predict(const pssgp_model* model, const double* t_train, co
   if (M > 0) {
     Timed tm(s, T_GATHER);
     k_gather<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(fmean, fvar, tpos, M, mean_test, var_test);
+    after_launch();
   }
   if (loglik) {
     Timed tm(s, T_LL);
     k_loglik_reduce<<<1, 256, 0, s>>>(a.llp, p.P0, loglik);
+    after_launch();
   }
-  return cuda_rc(cudaGetLastError());
+  return end_call();
 }
 
 extern "C" int pssgp_debug_filter_aggregates(const pssgp_model* model, const double* t, const double* y,
