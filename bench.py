@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--workload", default="rbf6", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--timing-steps", type=int, default=3)
+    ap.add_argument("--warps-per-sm", type=int, default=0, help="scan lanes per SM / 32 (0 = library default)")
     ap.add_argument("--n-train", type=int, default=0,
                     help="profile a prefix of the workload with this many training points (0 = full 2^20)")
     return ap.parse_args()
@@ -114,8 +115,8 @@ def taylor_terms(model, t, lanes, L):
     return float(kf.mean()), float(kq.mean())
 
 
-def lane_plan(n, sms=148):
-    lanes_max = sms * 4 * 32
+def lane_plan(n, sms=148, warps_per_sm=4):
+    lanes_max = sms * warps_per_sm * 32
     want = (n + 7) // 8
     P0 = min(lanes_max, max(want, 1))
     P0 = (P0 + 127) // 128 * 128
@@ -242,6 +243,8 @@ def run_ours(args, wl_params):
         torch.cuda.set_device(0)
     B.build()
     P.lib()
+    if args.warps_per_sm:
+        P.set_warps_per_sm(args.warps_per_sm)
     dev = torch.device("cuda", torch.cuda.current_device())
     s = wl.sinusoid_large(seed=2 + rank)
     if args.n_train:
@@ -345,7 +348,7 @@ def run_ours(args, wl_params):
 
     t_merged = np.sort(np.concatenate([s.t_train, s.t_test]), kind="stable")
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    lanes, L = lane_plan(n, sms)
+    lanes, L = lane_plan(n, sms, args.warps_per_sm or 4)
     kf, kq = taylor_terms(m, t_merged, lanes, L)
     d = m.d
     obs = N / n

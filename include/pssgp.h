@@ -248,6 +248,12 @@ int pssgp_timing(int32_t mode, double* ms, int64_t* counts, int32_t nslots);
 /* Name of timing slot `slot` ("" if unused). */
 const char* pssgp_timing_name(int32_t slot);
 
+/* Scan tuning: the number of chunks ("lanes") of the scans is
+ * SMs x warps_per_sm x 32 (4 or 8; default 4).  More lanes give each SM more
+ * warps to hide latency but shorter chunks and more scan overhead.  Affects
+ * calls planned afterwards, including pssgp_workspace_size (query it again). */
+int pssgp_set_warps_per_sm(int32_t warps_per_sm);
+
 /* sizeof(pssgp_model) as compiled into the library, for bindings that mirror
  * the struct (ABI check). */
 size_t pssgp_model_bytes(void);

@@ -82,6 +82,7 @@ def lib():
                                                     vp, vp, ctypes.POINTER(i32), vp, sz, vp]
         L.pssgp_fp64_fma_rate.argtypes = [ctypes.POINTER(dp)]
         L.pssgp_timing.argtypes = [i32, vp, vp, i32]
+        L.pssgp_set_warps_per_sm.argtypes = [i32]
         L.pssgp_loglik_noalloc.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, vp, vp]
         L.pssgp_timing_name.argtypes = [i32]
         L.pssgp_timing_name.restype = ctypes.c_char_p
@@ -302,3 +303,8 @@ def timing(mode: int):
         if name and cnt[i] > 0:
             out[name] = (float(ms[i]), int(cnt[i]))
     return out
+
+
+def set_warps_per_sm(w: int):
+    """Scan tuning knob (4 or 8 warps per SM); re-create workspaces afterwards."""
+    _check(lib().pssgp_set_warps_per_sm(int(w)), "pssgp_set_warps_per_sm")

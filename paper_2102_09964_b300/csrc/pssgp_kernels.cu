@@ -37,7 +37,7 @@ using namespace pssgp;
 namespace {
 
 constexpr int BLOCK = 128;           // 4 warps: one per SM sub-partition
-constexpr int WARPS_PER_SM = 4;
+int g_warps_per_sm = 4;              // lanes per SM / 32 (pssgp_set_warps_per_sm)
 constexpr int MIN_CHUNK = 8;         // steps per lane below which fewer lanes are used
 
 // ---------------------------------------------------------------------------
@@ -126,7 +126,7 @@ Plan make_plan(int d, int64_t n, int64_t lanes_req) {
   Plan p{};
   p.d = d;
   p.n = n;
-  const int64_t lanes_max = (int64_t)num_sms() * WARPS_PER_SM * 32;
+  const int64_t lanes_max = (int64_t)num_sms() * g_warps_per_sm * 32;
   const int64_t want = (n + MIN_CHUNK - 1) / MIN_CHUNK;
   int64_t P0 = std::min(lanes_max, std::max<int64_t>(want, 1));
   if (lanes_req > 0) P0 = lanes_req;
@@ -1278,5 +1278,12 @@ extern "C" int pssgp_loglik_noalloc(const pssgp_model* model, const double* t, c
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemcpyAsync(status, ws, sizeof(int32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess) return PSSGP_ECUDA;
   }
+  return PSSGP_OK;
+}
+
+extern "C" int pssgp_set_warps_per_sm(int32_t warps_per_sm) {
+  if (warps_per_sm < 4 || warps_per_sm > 8 || warps_per_sm % 4) return PSSGP_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_warps_per_sm = warps_per_sm;
   return PSSGP_OK;
 }
