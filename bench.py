@@ -93,6 +93,11 @@ def flops_smoother_fold(d):
     return (2 * d ** 3 - d * d) * 2 + 2 * d * d + 2 * s * d                # E_a E, E_a L, E_a g + g_a, (.)E_a^T + L_a
 
 
+def flops_fixed_point(d, observed_frac):
+    s = d * (d + 1) // 2
+    return (2 * d ** 3 - d * d) + observed_frac * (4 * d + 2 * s + 2 * d * d)   # Sig F^T, rank-one updates
+
+
 def flops_rts_step(d):
     s = d * (d + 1) // 2
     return 2 * d * d + (2 * d ** 3 - d * d) + 2 * s * d
@@ -355,7 +360,7 @@ def run_ours(args, wl_params):
     alg = {
         "discretize": n * flops_discretize(d, kf, kq, bool(m.raw.companion)),
         "filter_reduce": n * flops_filter_fold(d, obs),
-        "filter_propagate": n * (flops_kf_step(d, obs) + flops_smoother_element(d) + flops_smoother_fold(d)),
+        "filter_propagate": n * (flops_kf_step(d, obs) + flops_smoother_element(d) + flops_fixed_point(d, obs)),
         "smoother_propagate": n * flops_rts_step(d),
     }
     ts = max(args.timing_steps, 1)

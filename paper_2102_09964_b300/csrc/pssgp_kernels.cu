@@ -435,8 +435,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
   }
   const double R0 = a.R ? a.R[0] : a.R_scalar;
   const int fuse = a.fuse_smoother;
-  SAgg<D> sa;
-  sagg_identity<D>(sa);
+  FixedPoint<D> fp;                 // smoother chunk aggregate by forward recursion
   double qsum = 0.0;
   LogProd lp;
   int nobs = 0;
@@ -449,18 +448,18 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
     mul<D>(F, P, T);
     mul_Bt_sym_add<D>(T, F, Q, Pm);
     if (fuse && k > k0) {
-      SAgg<D> e, r;
+      SAgg<D> e;
       if (!smoother_element<D>(x, P, T, xm, Pm, e)) bad = true;
       store_egl<D>(a.rec_egl, k - 1, e);
-      sagg_combine<D>(sa, e, r);
-      sa = r;
     }
-    if (a.mask[k]) {
+    const bool obs = a.mask[k] != 0;
+    double Si = 0.0, v = 0.0;
+    if (obs) {
       const double Rk = a.R_per_step ? a.R[k] : R0;
       const double S = Pm[0][0] + Rk;
       if (bad_pos(S)) bad = true;
-      const double Si = __drcp_rn(S);
-      const double v = a.y[k] - xm[0];
+      Si = __drcp_rn(S);
+      v = a.y[k] - xm[0];
       Vec<D> K;
 #pragma unroll
       for (int i = 0; i < D; ++i) K[i] = Pm[i][0] * Si;
@@ -478,6 +477,10 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
       for (int i = 0; i < D; ++i) x[i] = xm[i];
       copy<D>(Pm, P);
     }
+    if (fuse) {
+      if (k == k0) fixed_point_start<D>(fp, x, P);
+      else fixed_point_step<D>(fp, F, obs, Pm, Si, v);
+    }
     if (a.xf) {
 #pragma unroll
       for (int i = 0; i < D; ++i) a.xf[i * a.ld + k] = x[i] * m.Dsc[i];
@@ -491,27 +494,35 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
   }
   a.llp[g] = (nobs > 0) ? -0.5 * ((double)nobs * 1.8378770664093454836 + lp.ln() + qsum) : 0.0;
   if (fuse) {
+    SAgg<D> sa;
     if (k1 > k0) {
-      // element of the chunk's last step: the transition into the next step
-      // (or E = 0, g = x, L = P at the end of the series)
-      SAgg<D> e, r;
+      // element of the chunk's last step (the transition into the next step,
+      // or E = 0, g = x, L = P at the end of the series) and the chunk aggregate
+      SAgg<D> e;
       if (k1 < a.n) {
-        Mat<D> F, Q, T, Pm;
+        Mat<D> F, Q, T, Pm, Lc;
         Vec<D> xm;
+        double invd[D];
         load_fq<D>(a.rec_fq, k1, F, Q);
         mulv<D>(F, x, xm);
         mul<D>(F, P, T);
         mul_Bt_sym_add<D>(T, F, Q, Pm);
         if (!smoother_element<D>(x, P, T, xm, Pm, e)) bad = true;
+        if (!cholesky<D>(Pm, Lc, invd)) bad = true;
+        fixed_point_finish<D>(fp, F, xm, Lc, invd, sa);
       } else {
         set_zero<D>(e.E);
 #pragma unroll
         for (int i = 0; i < D; ++i) e.g[i] = x[i];
         copy<D>(P, e.L);
+        set_zero<D>(sa.E);
+#pragma unroll
+        for (int i = 0; i < D; ++i) sa.g[i] = fp.mu[i];
+        copy<D>(fp.V, sa.L);
       }
       store_egl<D>(a.rec_egl, k1 - 1, e);
-      sagg_combine<D>(sa, e, r);
-      sa = r;
+    } else {
+      sagg_identity<D>(sa);
     }
     // smoother level 1: inclusive suffix scan over the warp's lanes
 #pragma unroll 1

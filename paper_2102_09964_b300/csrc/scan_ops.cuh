@@ -521,6 +521,121 @@ __device__ __forceinline__ bool smoother_element(const Vec<D>& x, const Mat<D>& 
   return ok;
 }
 
+// Chunk aggregate of the smoothing operator by forward recursion.
+// The product of the smoothing elements of steps s..e-1 is the conditional
+// p(x_s | x_e, y_{1:e-1}) = N(E x_e + g, L) (each element is
+// p(x_k | x_{k+1}, y_{1:k}), supplement Prop. 2, and the chain is Markov).
+// It follows from the joint of (x_s, x_k) given y_{1:k}, carried forward with
+// the Kalman filter as in fixed-point smoothing:
+//   mu = E[x_s | y_1:k], V = Cov(x_s | y_1:k), Sig = Cov(x_s, x_k | y_1:k),
+//   predict  Sig <- Sig F^T;
+//   update   c = Sig[:,0] (Cov(x_s, y)), mu += c v / S, V -= c c^T / S,
+//            Sig -= c K^T   (K = P^-[:,0] / S, the filter gain);
+// and at the chunk end, with the prediction (x^-, P^-) of step e,
+//   E = Sig F_e^T (P^-)^{-1}, g = mu - E x^-, L = V - E (Sig F_e^T)^T.
+// Cost per step: one d x d product and rank-one updates, instead of the two
+// products of an explicit fold of the operator.
+template <int D>
+struct FixedPoint {
+  Vec<D> mu;
+  Mat<D> V;     // symmetric
+  Mat<D> Sig;
+};
+
+template <int D>
+__device__ __forceinline__ void fixed_point_start(FixedPoint<D>& f, const Vec<D>& x, const Mat<D>& P) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    f.mu[i] = x[i];
+#pragma unroll
+    for (int j = 0; j < D; ++j) { f.V[i][j] = P[i][j]; f.Sig[i][j] = P[i][j]; }
+  }
+}
+
+// Sig <- Sig F^T ; then, if observed, the rank-one update with gain K = Pm[:,0]/S
+template <int D>
+__device__ __forceinline__ void fixed_point_step(FixedPoint<D>& f, const Mat<D>& F, bool observed, const Mat<D>& Pm,
+                                                 double Si, double v) {
+  Mat<D> Sm;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double s = f.Sig[i][0] * F[j][0];
+#pragma unroll
+      for (int k = 1; k < D; ++k) s = fma(f.Sig[i][k], F[j][k], s);
+      Sm[i][j] = s;
+    }
+  if (observed) {
+    Vec<D> c, cs, K;
+#pragma unroll
+    for (int i = 0; i < D; ++i) { c[i] = Sm[i][0]; cs[i] = c[i] * Si; K[i] = Pm[i][0] * Si; }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      f.mu[i] = fma(cs[i], v, f.mu[i]);
+#pragma unroll
+      for (int j = i; j < D; ++j) { f.V[i][j] = fma(-cs[i], c[j], f.V[i][j]); f.V[j][i] = f.V[i][j]; }
+#pragma unroll
+      for (int j = 0; j < D; ++j) f.Sig[i][j] = fma(-c[i], K[j], Sm[i][j]);
+    }
+  } else {
+    copy<D>(Sm, f.Sig);
+  }
+}
+
+// chunk end: aggregate (E, g, L) from the fixed-point state and the
+// prediction (xm, Pm) of the step after the chunk, Pm = Lc Lc^T given.
+template <int D>
+__device__ __forceinline__ void fixed_point_finish(const FixedPoint<D>& f, const Mat<D>& F, const Vec<D>& xm,
+                                                   const Mat<D>& Lc, const double (&invd)[D], SAgg<D>& a) {
+  // Z = (Sig F^T)^T = F Sig^T ; W = Lc^{-1} Z ; E^T = Lc^{-T} W ; L = V - W^T W
+  Mat<D> Wm;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double z = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) z = fma(F[i][k], f.Sig[j][k], z);
+      Wm[i][j] = z;
+    }
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double s = Wm[i][j];
+#pragma unroll
+      for (int k = 0; k < i; ++k) s = fma(-Lc[i][k], Wm[k][j], s);
+      Wm[i][j] = s * invd[i];
+    }
+#pragma unroll
+  for (int i = D - 1; i >= 0; --i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double s = Wm[i][j];
+#pragma unroll
+      for (int k = i + 1; k < D; ++k) s = fma(-Lc[k][i], a.E[j][k], s);
+      a.E[j][i] = s * invd[i];
+    }
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double s = f.mu[i];
+#pragma unroll
+    for (int k = 0; k < D; ++k) s = fma(-a.E[i][k], xm[k], s);
+    a.g[i] = s;
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) {
+      double s = f.V[i][j];
+#pragma unroll
+      for (int k = 0; k < D; ++k) s = fma(-Wm[k][i], Wm[k][j], s);
+      a.L[i][j] = s;
+      a.L[j][i] = s;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // (De)serialisation of aggregates: entry-major with a stride, so that the
 // lanes of a warp touch consecutive addresses.
