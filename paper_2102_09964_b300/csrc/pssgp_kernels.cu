@@ -401,8 +401,16 @@ struct LogProd {
 };
 
 // filter level 3 (+ smoother levels 0/1 when fused)
+// shared memory of k_filter_propagate: the fixed-point state Sig, V (packed),
+// mu per thread, entry-major with stride BLOCK
+template <int D> constexpr int propagate_smem_doubles() { return (D * D + Sym<D>::N + D) * BLOCK; }
+
 template <int D>
 __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D> m, const ScanArgs a) {
+  extern __shared__ double psm[];
+  double* sSig = psm + threadIdx.x;
+  double* sV = sSig + D * D * BLOCK;
+  double* smu = sV + Sym<D>::N * BLOCK;
   const int64_t g = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int64_t w = g >> 5;
@@ -435,7 +443,6 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
   }
   const double R0 = a.R ? a.R[0] : a.R_scalar;
   const int fuse = a.fuse_smoother;
-  FixedPoint<D> fp;                 // smoother chunk aggregate by forward recursion
   double qsum = 0.0;
   LogProd lp;
   int nobs = 0;
@@ -477,9 +484,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
       for (int i = 0; i < D; ++i) x[i] = xm[i];
       copy<D>(Pm, P);
     }
-    if (fuse) {
-      if (k == k0) fixed_point_start<D>(fp, x, P);
-      else fixed_point_step<D>(fp, F, obs, Pm, Si, v);
+    if (fuse) {   // smoother chunk aggregate by forward recursion (state in shared memory)
+      if (k == k0) fixed_point_start_smem<D, BLOCK>(sSig, sV, smu, x, P);
+      else fixed_point_step_smem<D, BLOCK>(sSig, sV, smu, F, obs, Pm, Si, v);
     }
     if (a.xf) {
 #pragma unroll
@@ -509,8 +516,12 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
         mul_Bt_sym_add<D>(T, F, Q, Pm);
         if (!smoother_element<D>(x, P, T, xm, Pm, e)) bad = true;
         if (!cholesky<D>(Pm, Lc, invd)) bad = true;
+        FixedPoint<D> fp;
+        fixed_point_load<D, BLOCK>(sSig, sV, smu, fp);
         fixed_point_finish<D>(fp, F, xm, Lc, invd, sa);
       } else {
+        FixedPoint<D> fp;
+        fixed_point_load<D, BLOCK>(sSig, sV, smu, fp);
         set_zero<D>(e.E);
 #pragma unroll
         for (int i = 0; i < D; ++i) e.g[i] = x[i];
@@ -917,8 +928,10 @@ void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s
   }
   a.wfin_f = run_filter_level2<D>(p, a.wagg_f, a.status, s);
   {
+    constexpr int psmem = propagate_smem_doubles<D>() * 8;
+    cudaFuncSetAttribute(k_filter_propagate<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);
     Timed tm(s, T_FPROP);
-    k_filter_propagate<D><<<grid, BLOCK, 0, s>>>(m, a);
+    k_filter_propagate<D><<<grid, BLOCK, psmem, s>>>(m, a);
     after_launch();
   }
 }

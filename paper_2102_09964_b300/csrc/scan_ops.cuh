@@ -636,6 +636,73 @@ __device__ __forceinline__ void fixed_point_finish(const FixedPoint<D>& f, const
     }
 }
 
+// The same recursion with its state in shared memory (element e of a
+// thread's Sig / V(packed) / mu at ptr[e * SST]); each row of Sig is updated
+// in place (row i of Sig F^T needs only row i of Sig), so only a row and the
+// vector c = Sig[:,0] are held in registers.
+template <int D, int SST>
+__device__ __forceinline__ void fixed_point_start_smem(double* Sig, double* V, double* mu, const Vec<D>& x,
+                                                       const Mat<D>& P) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    mu[i * SST] = x[i];
+#pragma unroll
+    for (int j = 0; j < D; ++j) Sig[(i * D + j) * SST] = P[i][j];
+#pragma unroll
+    for (int j = i; j < D; ++j) V[pidx<D>(i, j) * SST] = P[i][j];
+  }
+}
+
+template <int D, int SST>
+__device__ __forceinline__ void fixed_point_step_smem(double* Sig, double* V, double* mu, const Mat<D>& F,
+                                                      bool observed, const Mat<D>& Pm, double Si, double v) {
+  Vec<D> c;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double row[D], sm[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) row[k] = Sig[(i * D + k) * SST];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double s = row[0] * F[j][0];
+#pragma unroll
+      for (int k = 1; k < D; ++k) s = fma(row[k], F[j][k], s);
+      sm[j] = s;
+    }
+    c[i] = sm[0];
+    if (observed) {
+      const double ci = sm[0];
+#pragma unroll
+      for (int j = 0; j < D; ++j) Sig[(i * D + j) * SST] = fma(-ci, Pm[j][0] * Si, sm[j]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < D; ++j) Sig[(i * D + j) * SST] = sm[j];
+    }
+  }
+  if (observed) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const double cs = c[i] * Si;
+      mu[i * SST] = fma(cs, v, mu[i * SST]);
+#pragma unroll
+      for (int j = i; j < D; ++j) V[pidx<D>(i, j) * SST] = fma(-cs, c[j], V[pidx<D>(i, j) * SST]);
+    }
+  }
+}
+
+template <int D, int SST>
+__device__ __forceinline__ void fixed_point_load(const double* Sig, const double* V, const double* mu,
+                                                 FixedPoint<D>& f) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    f.mu[i] = mu[i * SST];
+#pragma unroll
+    for (int j = 0; j < D; ++j) f.Sig[i][j] = Sig[(i * D + j) * SST];
+#pragma unroll
+    for (int j = i; j < D; ++j) { f.V[i][j] = V[pidx<D>(i, j) * SST]; f.V[j][i] = f.V[i][j]; }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // (De)serialisation of aggregates: entry-major with a stride, so that the
 // lanes of a warp touch consecutive addresses.
