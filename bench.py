@@ -33,6 +33,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "filter+smoother time steps/s at N=2^20,d=6 FP64"
+# DRAM bytes per merged step of each kernel from one ncu capture of the
+# current kernels on a 2^18-step case (profiles/fp64_instruction_counts_rbf6_n264k.md);
+# traffic grows in proportion to the steps, so a launch's traffic is this x n.
+# Reset an entry to None whenever its kernel changes.
+PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1390.0, "filter_reduce": 1390.0, "discretize": 372.0,
+                                "smoother_propagate": 560.0}
 UNIT = "steps/s"
 WORKLOADS = {
     "rbf6": dict(kind="rbf", order=6, lengthscale=1.0, variance=1.0, noise=0.01),
@@ -373,8 +379,9 @@ def run_ours(args, wl_params):
         v["share"] = round(v["ms_per_step"] / tot_all, 4)
     dom = max((k for k in alg if k in kernels), key=lambda k: kernels[k]["ms_per_step"])
     achieved = alg[dom] / (kernels[dom]["ms_per_launch"] * 1e-3) / 1e12
+    tb = PROFILED_DRAM_BYTES_PER_STEP.get(dom) if args.workload == "rbf6" else None
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_tflops, 4), "unit": "TFLOP/s",
-                "frac": round(achieved / peak_tflops, 4), "traffic": None, "kernel": dom,
+                "frac": round(achieved / peak_tflops, 4), "traffic": (tb * n if tb else None), "kernel": dom,
                 "peak_source": "measured FP64 FMA rate of this GPU (pssgp_fp64_fma_rate, x2 flops)",
                 "algorithmic_flops_per_launch": alg[dom], "taylor_terms": {"F": round(kf, 2), "Q": round(kq, 2)}}
     whole = sum(alg.values()) / (ms * 1e-3) / 1e12
