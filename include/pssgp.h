@@ -58,6 +58,7 @@ extern "C" {
 #define PSSGP_ENAN 1           /* non-finite time or observed y                 */
 #define PSSGP_EUNSORTED 2      /* times decrease somewhere                      */
 #define PSSGP_ENOTPD 4         /* innovation variance or a pivot <= 0 / singular */
+#define PSSGP_EBATCH 8         /* batched: bad offsets or a non-positive parameter */
 
 /* ---- model ------------------------------------------------------------- */
 #define PSSGP_MATERN12 1
@@ -187,6 +188,34 @@ int pssgp_smooth(const pssgp_model* model, const double* t,
 int pssgp_loglik(const pssgp_model* model, const double* t, const double* y,
                  const uint8_t* mask, const double* R, int32_t R_per_step,
                  int64_t n, double* loglik, void* ws, size_t ws_bytes, void* stream);
+
+/* Log marginal likelihoods of a batch of B independent series in one pass
+ * (the hyperparameter search of Sec. 2 and Sec. 5 evaluates many
+ * (lengthscale, variance, noise) candidates or many series at once).
+ *  - Series s occupies steps offsets[s] .. offsets[s+1]-1 of t, y, mask
+ *    (device arrays of length n; t sorted within each series).  offsets:
+ *    device int64[B + 1], offsets[0] = 0, non-decreasing, offsets[B] = n;
+ *    empty series are allowed and get loglik 0.
+ *  - params: device double[3 B], per series (lengthscale, variance, noise
+ *    variance R), all > 0.
+ *  - model: any pssgp_model_build result of the kernel family; its
+ *    lengthscale and variance fields say where it was built.  Series s uses
+ *    the same family at (lengthscale_s, variance_s): for a stationary kernel
+ *    whose covariance is variance * k(tau / lengthscale) the state-space
+ *    model rescales exactly (F(h) -> F(h l0 / l), Q -> Q v / v0 in the
+ *    time-scaled state coordinates, which leave H x unchanged).  Returns
+ *    PSSGP_EMODEL if those fields are not positive and finite (a model from
+ *    pssgp_model_from_sde carries none).
+ *  - Each series starts from the stationary prior (F = 0, Q = P_inf), so
+ *    the concatenation filters every series independently.
+ *  - loglik: device double[B].  ws: pssgp_workspace_size(d, n) bytes.
+ *  - Device status (pssgp_get_status): PSSGP_EBATCH for bad offsets or a
+ *    non-positive parameter, plus the bits of pssgp_filter. */
+int pssgp_loglik_batched(const pssgp_model* model, const int64_t* offsets,
+                         int32_t B, const double* params, const double* t,
+                         const double* y, const uint8_t* mask, int64_t n,
+                         double* loglik, void* ws, size_t ws_bytes,
+                         void* stream);
 
 /* Allocation-free variant of pssgp_loglik for callers that cannot allocate
  * device memory themselves -- for instance a plugin inside a host program

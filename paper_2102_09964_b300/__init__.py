@@ -29,7 +29,7 @@ KINDS = {"matern12": MATERN12, "matern32": MATERN32, "matern52": MATERN52, "rbf"
 
 OK = 0
 ERRORS = {-1: "EINVAL", -2: "EDIM", -3: "EKERNEL", -4: "EWORKSPACE", -5: "ECUDA", -6: "EMODEL", -7: "ESCRATCH"}
-ENAN, EUNSORTED, ENOTPD = 1, 2, 4
+ENAN, EUNSORTED, ENOTPD, EBATCH = 1, 2, 4, 8
 
 
 class PssgpKernel(ctypes.Structure):
@@ -77,6 +77,7 @@ def lib():
         L.pssgp_filter.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, vp, i64, vp, vp, sz, vp]
         L.pssgp_smooth.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, i64, i64, vp, vp, vp, vp, vp, sz, vp]
         L.pssgp_loglik.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, vp, sz, vp]
+        L.pssgp_loglik_batched.argtypes = [ctypes.POINTER(PssgpModel), vp, i32, vp, vp, vp, vp, i64, vp, vp, sz, vp]
         L.pssgp_predict.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, i64, vp, i64, dp, vp, vp, vp, vp, sz, vp]
         L.pssgp_debug_filter_aggregates.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i64, i32,
                                                     vp, vp, ctypes.POINTER(i32), vp, sz, vp]
@@ -234,6 +235,27 @@ def loglik(model: Model, t, y, mask, R, ws=None):
     rc = lib().pssgp_loglik(ctypes.byref(model.raw), _ptr(t), _ptr(y), _ptr(mask), _ptr(R), per, n, _ptr(ll),
                             _ptr(ws), ws.numel(), _stream())
     _check(rc, "pssgp_loglik")
+    return ll, ws
+
+
+def loglik_batched(model: Model, offsets, params, t, y, mask, ws=None, out=None):
+    """Log marginal likelihoods of B series in one pass.  offsets: int64[B+1]
+    (series s = steps offsets[s]..offsets[s+1]-1 of t, y, mask); params:
+    float64[B, 3] = (lengthscale, variance, noise variance) per series; model:
+    the kernel family, built at any hyperparameters.  Returns (loglik[B], ws)."""
+    d, n = model.d, t.numel()
+    dev = t.device
+    B = offsets.numel() - 1
+    if offsets.dtype != torch.int64 or not offsets.is_contiguous():
+        raise TypeError("offsets must be a contiguous int64 tensor")
+    params = _f64(params, dev).reshape(-1)
+    if params.numel() != 3 * B:
+        raise ValueError("params must hold 3 values per series")
+    ws = ws if ws is not None else workspace(d, n, dev)
+    ll = out if out is not None else torch.empty(B, dtype=torch.float64, device=dev)
+    rc = lib().pssgp_loglik_batched(ctypes.byref(model.raw), _ptr(offsets), B, _ptr(params), _ptr(t), _ptr(y),
+                                    _ptr(mask), n, _ptr(ll), _ptr(ws), ws.numel(), _stream())
+    _check(rc, "pssgp_loglik_batched")
     return ll, ws
 
 

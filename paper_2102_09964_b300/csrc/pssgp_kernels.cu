@@ -119,7 +119,7 @@ struct Plan {
   int fqs, egs;      // per-step record strides (doubles, even)
   // byte offsets into the workspace
   int64_t o_status, o_fq, o_egl, o_laggf, o_waggf, o_laggs, o_waggs, o_llp, o_fmean, o_fvar, o_t, o_y, o_mask,
-      o_tpos, total;
+      o_tpos, o_rstep, o_seg, o_llstep, total;
 };
 
 Plan make_plan(int d, int64_t n, int64_t lanes_req) {
@@ -154,6 +154,9 @@ Plan make_plan(int d, int64_t n, int64_t lanes_req) {
   p.o_y = o; o += align256(n * 8);
   p.o_mask = o; o += align256(n);
   p.o_tpos = o; o += align256(n * 8);
+  p.o_rstep = o; o += align256(n * 8);     // batched: noise variance per step
+  p.o_seg = o; o += align256(n);           // batched: 1 at each series' first step
+  p.o_llstep = o; o += align256(n * 8);    // batched: log-likelihood pieces per step
   p.total = o;
   return p;
 }
@@ -188,6 +191,8 @@ struct ScanArgs {
   int64_t ld;
   int fuse_smoother;     // 1: the filter pass also builds the smoother elements
   double* dbg_agg;       // optional: level-0 lane aggregates (tests)
+  const uint8_t* seg_start;  // batched: series starts (null for one series)
+  double* ll_step;           // batched: per-step log-likelihood pieces
 };
 
 __device__ __forceinline__ void flag(int* status, int bits) {
@@ -286,6 +291,78 @@ __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_rec(const DevModel<D>
   double* dst = rec + k0 * FQS;
   for (int64_t e = threadIdx.x; e < nrec * FQS; e += DISC_BLOCK) dst[e] = stage[e];
   flag(status, bits);
+}
+
+// batched series: the series of step k by binary search in offsets[0..B];
+// the model, built at (ell0, var0), rescaled per series (see discretize);
+// writes the F/Q record, the step's noise variance and whether it starts a
+// series.  params[3s..3s+2] = lengthscale, variance, noise variance.  The
+// grid covers max(n, B + 1) threads so that every offset is checked.
+template <int D>
+__global__ void __launch_bounds__(DISC_BLOCK) k_discretize_batched(const DevModel<D> m, double ell0, double var0,
+                                                                 const int64_t* offsets, int B, const double* params,
+                                                                 const double* t, int64_t n, double* rec,
+                                                                 double* Rstep, uint8_t* seg, int* status) {
+  constexpr int FQS = fqs_of<D>();
+  extern __shared__ double stage[];
+  const int64_t k0 = (int64_t)blockIdx.x * DISC_BLOCK;
+  const int64_t k = k0 + threadIdx.x;
+  const bool act = k < n;
+  int bits = 0;
+  if (k <= B) {   // offsets: 0 = o_0 <= o_1 <= ... <= o_B = n
+    const int64_t ok = offsets[k];
+    if ((k == 0 && ok != 0) || (k == B && ok != n) || (k < B && offsets[k + 1] < ok)) bits |= PSSGP_EBATCH;
+  }
+  int64_t sid = 0;
+  bool first = false;
+  double uscale = 1.0, qscale = 1.0, R = 1.0, h = 0.0;
+  if (act) {
+    int lo = 0, hi = B;                       // last s with offsets[s] <= k
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (offsets[mid] <= k) lo = mid; else hi = mid;
+    }
+    sid = lo;
+    first = (k == 0) || (k == offsets[sid]);
+    const double ell = params[3 * sid], s2 = params[3 * sid + 1];
+    R = params[3 * sid + 2];
+    if (bad_pos(ell) || bad_pos(s2) || bad_pos(R)) bits |= PSSGP_EBATCH;
+    uscale = ell0 / ell;
+    qscale = s2 / var0;
+    const double t1 = t[k];
+    if (nonfinite(t1)) bits |= PSSGP_ENAN;
+    if (!first) {
+      h = t1 - t[k - 1];
+      if (negative_nonzero(h)) bits |= PSSGP_EUNSORTED;
+    }
+  }
+  Mat<D> F, Q;
+  discretize<D>(m, h, first, act, F, Q, uscale, qscale);
+  store_fq<D>(stage, threadIdx.x, F, Q);
+  if (act) {
+    Rstep[k] = R;
+    seg[k] = first ? 1 : 0;
+  }
+  __syncthreads();
+  const int64_t nrec = min((int64_t)DISC_BLOCK, n - k0);
+  double* dst = rec + k0 * FQS;
+  for (int64_t e = threadIdx.x; e < nrec * FQS; e += DISC_BLOCK) dst[e] = stage[e];
+  flag(status, bits);
+}
+
+// one warp per series: fixed-order sum of the per-step log-likelihood pieces
+__global__ void __launch_bounds__(BLOCK) k_segment_sum(const double* v, int64_t n, const int64_t* offsets, int B,
+                                                           double* out) {
+  const int s = (int)((int64_t)blockIdx.x * (BLOCK / 32) + (threadIdx.x >> 5));
+  const int lane = threadIdx.x & 31;
+  if (s >= B) return;
+  const int64_t a = min(max(offsets[s], (int64_t)0), n);     // clamped: bad offsets are
+  const int64_t b = min(max(offsets[s + 1], a), n);           // flagged by k_discretize_batched
+  double acc = 0.0;
+  for (int64_t k = a + lane; k < b; k += 32) acc += v[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[s] = acc;
 }
 
 // shared memory of k_filter_reduce: A (two buffers), J (packed) and eta per
@@ -400,6 +477,11 @@ struct LogProd {
   __device__ __forceinline__ double ln() const { return ::log(mant) + (double)expo * 0.69314718055994530942; }
 };
 
+// log-likelihood of nobs observed steps from log prod S and sum v^2/S
+__device__ __forceinline__ double ll_piece(int nobs, const LogProd& lp, double qsum) {
+  return (nobs > 0) ? -0.5 * ((double)nobs * 1.8378770664093454836 + lp.ln() + qsum) : 0.0;
+}
+
 // filter level 3 (+ smoother levels 0/1 when fused)
 // shared memory of k_filter_propagate: the fixed-point state Sig, V (packed),
 // mu per thread, entry-major with stride BLOCK
@@ -446,8 +528,19 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
   double qsum = 0.0;
   LogProd lp;
   int nobs = 0;
+  int64_t lpos = k0;   // batched: where the current series piece is written
 #pragma unroll 1
   for (int64_t k = k0; k < k1; ++k) {
+    if (a.ll_step) {   // one log-likelihood piece per (lane chunk, series) pair
+      if (k > k0 && a.seg_start[k]) {
+        a.ll_step[lpos] = ll_piece(nobs, lp, qsum);
+        lpos = k;
+        nobs = 0;
+        qsum = 0.0;
+        lp = LogProd();
+      }
+      a.ll_step[k] = 0.0;
+    }
     Mat<D> F, Q, T, Pm;
     Vec<D> xm;
     load_fq<D>(a.rec_fq, k, F, Q);
@@ -499,7 +592,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
         for (int j = i; j < D; ++j) a.Pf[pidx<D>(i, j) * a.ld + k] = P[i][j] * (m.Dsc[i] * m.Dsc[j]);
     }
   }
-  a.llp[g] = (nobs > 0) ? -0.5 * ((double)nobs * 1.8378770664093454836 + lp.ln() + qsum) : 0.0;
+  a.llp[g] = ll_piece(nobs, lp, qsum);
+  if (a.ll_step && k1 > k0) a.ll_step[lpos] = a.llp[g];
   if (fuse) {
     SAgg<D> sa;
     if (k1 > k0) {
@@ -907,16 +1001,33 @@ const double* run_smoother_level2(const Plan& p, double* buf0, cudaStream_t s) {
   return in;
 }
 
+// a batch of series sharing one model (pssgp_loglik_batched)
+struct BatchArgs {
+  double ell0, var0;        // hyperparameters the model was built at
+  const int64_t* offsets;   // [B + 1]
+  int B;
+  const double* params;     // [B][3]
+  double* Rstep;
+  uint8_t* seg;
+};
+
 template <int D>
-void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s) {
+void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s, const BatchArgs* bt = nullptr) {
   const int grid = (int)(p.P0 / BLOCK);
   {
     Timed tm(s, T_DISC);
     constexpr int dsmem = DISC_BLOCK * fqs_of<D>() * 8;
     // opt in to > 48 KB of dynamic shared memory (per device; cheap host call)
-    cudaFuncSetAttribute(k_discretize_rec<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem);
-    k_discretize_rec<D><<<(unsigned)((p.n + DISC_BLOCK - 1) / DISC_BLOCK), DISC_BLOCK, dsmem, s>>>(
-        m, a.t, p.n, a.rec_fq, a.status);
+    if (!bt) {
+      cudaFuncSetAttribute(k_discretize_rec<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem);
+      k_discretize_rec<D><<<(unsigned)((p.n + DISC_BLOCK - 1) / DISC_BLOCK), DISC_BLOCK, dsmem, s>>>(
+          m, a.t, p.n, a.rec_fq, a.status);
+    } else {
+      cudaFuncSetAttribute(k_discretize_batched<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem);
+      const int64_t thr = std::max<int64_t>(p.n, (int64_t)bt->B + 1);
+      k_discretize_batched<D><<<(unsigned)((thr + DISC_BLOCK - 1) / DISC_BLOCK), DISC_BLOCK, dsmem, s>>>(
+          m, bt->ell0, bt->var0, bt->offsets, bt->B, bt->params, a.t, p.n, a.rec_fq, bt->Rstep, bt->seg, a.status);
+    }
     after_launch();
   }
   {
@@ -1061,6 +1172,40 @@ extern "C" int pssgp_loglik(const pssgp_model* model, const double* t, const dou
   if (!loglik) return PSSGP_EINVAL;
   return filter_common(model, t, y, mask, R, R_per_step, n, nullptr, nullptr, n, loglik, ws, ws_bytes, stream, 0,
                        nullptr);
+}
+
+extern "C" int pssgp_loglik_batched(const pssgp_model* model, const int64_t* offsets, int32_t B,
+                                    const double* params, const double* t, const double* y, const uint8_t* mask,
+                                    int64_t n, double* loglik, void* ws, size_t ws_bytes, void* stream) {
+  begin_call();
+  if (!model_ok(model) || !offsets || !params || !t || !y || !mask || !loglik || B < 1 || n < 1)
+    return PSSGP_EINVAL;
+  const double ell0 = model->lengthscale, var0 = model->variance;
+  if (!(ell0 > 0.0) || !(var0 > 0.0) || !std::isfinite(ell0) || !std::isfinite(var0)) return PSSGP_EMODEL;
+  const Plan p = make_plan(model->d, n, 0);
+  const int rc = check_ws(p, ws, ws_bytes);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScanArgs a = base_args(p, ws);
+  BatchArgs bt;
+  bt.ell0 = ell0; bt.var0 = var0; bt.offsets = offsets; bt.B = B; bt.params = params;
+  bt.Rstep = reinterpret_cast<double*>(ws_ptr(ws, p.o_rstep));
+  bt.seg = reinterpret_cast<uint8_t*>(ws_ptr(ws, p.o_seg));
+  a.t = t; a.y = y; a.mask = mask; a.R = bt.Rstep; a.R_per_step = 1;
+  a.fuse_smoother = 0;
+  a.seg_start = bt.seg;
+  a.ll_step = reinterpret_cast<double*>(ws_ptr(ws, p.o_llstep));
+  if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess) return PSSGP_ECUDA;
+  PSSGP_DISPATCH(model->d, {
+    const DevModel<D> m = dev_model<D>(model);
+    run_filter<D>(m, p, a, s, &bt);
+  });
+  {
+    Timed tm(s, T_LL);
+    k_segment_sum<<<(unsigned)((B + BLOCK / 32 - 1) / (BLOCK / 32)), BLOCK, 0, s>>>(a.ll_step, n, offsets, B, loglik);
+    after_launch();
+  }
+  return end_call();
 }
 
 extern "C" int pssgp_smooth(const pssgp_model* model, const double* t, const double* xf, const double* Pf, int64_t n,

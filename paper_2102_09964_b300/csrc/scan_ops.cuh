@@ -64,9 +64,15 @@ __device__ __noinline__ void double_steps(Mat<D>& F, Mat<D>& Q, int s, int smax)
   }
 }
 
+// uscale, qscale: for a kernel with a lengthscale and a variance, the model
+// at (l, s2) in l-scaled coordinates has F(h) = F1(h / l), Q(h) = s2 Q1(h / l),
+// P_inf = s2 P_inf1, with (F1, Q1, P_inf1) the model at l = 1, s2 = 1; so one
+// unit model serves a batch of series with uscale = 1/l and qscale = s2 each
+// (both 1 for a model built at its own hyperparameters).
 template <int D>
 __device__ __forceinline__ void discretize(const DevModel<D>& m, double h, bool first, bool active,
-                                           Mat<D>& F, Mat<D>& Q) {
+                                           Mat<D>& F, Mat<D>& Q, double uscale = 1.0, double qscale = 1.0) {
+  h *= uscale;
   float hf = (float)h;
   int s = 0;
   if (active && !first && hf > m.hmax) {
@@ -125,10 +131,11 @@ __device__ __forceinline__ void discretize(const DevModel<D>& m, double h, bool 
 #pragma unroll
       for (int j = i; j < D; ++j) Q[i][j] = fma(Q[i][j], hs, m.qc[pidx<D>(i, j)][t]);
   }
+  const double hq = hs * qscale;
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
-    for (int j = i; j < D; ++j) { Q[i][j] *= hs; Q[j][i] = Q[i][j]; }
+    for (int j = i; j < D; ++j) { Q[i][j] *= hq; Q[j][i] = Q[i][j]; }
   // doubling for long steps (rare; each lane applies its own count)
   if (smax > 0) double_steps<D>(F, Q, s, smax);
   if (first) {
@@ -137,7 +144,7 @@ __device__ __forceinline__ void discretize(const DevModel<D>& m, double h, bool 
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         F[i][j] = 0.0;
-        Q[i][j] = m.Pinf[i <= j ? pidx<D>(i, j) : pidx<D>(j, i)];
+        Q[i][j] = qscale * m.Pinf[i <= j ? pidx<D>(i, j) : pidx<D>(j, i)];
       }
   }
 }

@@ -1,0 +1,164 @@
+"""GPU parity of the batched log-likelihood (many independent series in one
+pass) against the sequential oracle, series by series.
+
+Each series s is filtered by the oracle with the model built directly at its
+own (lengthscale, variance) and its own noise variance; the CUDA path uses one
+model of the family, rescaled per series on the device.  Tolerance semantics
+as in test_gpu_parity: |dl| <= tol * max(|l|, n_obs).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2102_09964_b300 as P
+import workloads as wl
+from oracle import model as om
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"matern12": 1e-9, "matern32": 1e-9, "matern52": 1e-9, "rbf": 1e-6}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2102_09964_b300 import build
+    build.build()
+    P.lib()
+    oracle.build()
+
+
+def dev(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def oracle_loglik(kind, t, y, mask, ell, s2, R):
+    if t.size == 0:
+        return 0.0
+    return oracle.run(om.make_model(kind, ell, s2), t, y, mask, R).loglik
+
+
+def run_batched(kind, bt, mask=None, ell0=1.0, s20=1.0):
+    m = P.build_model(kind, ell0, s20)
+    n = bt.t.size
+    mask = np.ones(n, np.uint8) if mask is None else mask
+    ll, ws = P.loglik_batched(m, dev(bt.offsets, torch.int64), dev(bt.params()), dev(bt.t), dev(bt.y),
+                              dev(mask, torch.uint8))
+    return ll.cpu().numpy(), P.status(ws)
+
+
+def check_series(kind, bt, ll, mask=None, idx=None):
+    idx = range(bt.B) if idx is None else idx
+    worst = 0.0
+    for s in idx:
+        a, b = bt.offsets[s], bt.offsets[s + 1]
+        ms = np.ones(b - a, np.uint8) if mask is None else mask[a:b]
+        ref = oracle_loglik(kind, bt.t[a:b], bt.y[a:b], ms, bt.lengthscale[s], bt.variance[s], bt.noise[s])
+        nobs = int(ms.sum())
+        err = abs(ll[s] - ref) / max(abs(ref), nobs, 1)
+        assert err <= TOL[kind], (kind, s, b - a, ll[s], ref, err)
+        worst = max(worst, err)
+    return worst
+
+
+# lengths: empty, single-step, shorter than a warp, tile-ragged, long
+LENGTHS = [0, 1, 2, 7, 31, 33, 0, 257, 1000, 4099, 1, 12_345, 3, 65_536]
+
+
+@pytest.mark.parametrize("kind", ["matern32", "matern52", "rbf", "matern12"])
+def test_batched_matches_oracle_per_series(kind):
+    bt = wl.series_batch(seed=11, lengths=LENGTHS)
+    bt.variance[:] = np.exp(np.random.default_rng(5).uniform(np.log(0.3), np.log(3.0), bt.B))
+    ll, st = run_batched(kind, bt)
+    assert st == 0
+    check_series(kind, bt, ll)
+
+
+@pytest.mark.parametrize("kind", ["matern52", "rbf"])
+def test_batched_model_built_elsewhere(kind):
+    """The family's model may be built at any (lengthscale, variance): the
+    per-series rescaling is relative to where it was built."""
+    bt = wl.series_batch(seed=12, lengths=[500, 2000, 77, 9000])
+    ll, st = run_batched(kind, bt, ell0=0.37, s20=2.5)
+    assert st == 0
+    check_series(kind, bt, ll)
+
+
+def test_batched_missing_measurements():
+    bt = wl.series_batch(seed=13, lengths=[300, 5000, 1, 40, 2500])
+    rng = np.random.default_rng(14)
+    mask = (rng.uniform(size=bt.t.size) > 0.2).astype(np.uint8)
+    a, b = bt.offsets[3], bt.offsets[4]
+    mask[a:b] = 0                               # one series fully missing: loglik 0
+    ll, st = run_batched("matern52", bt, mask)
+    assert st == 0
+    assert ll[3] == 0.0
+    check_series("matern52", bt, ll, mask)
+
+
+def test_batched_equals_single_series_calls():
+    """Cross-check against the single-series entry point on the same device."""
+    bt = wl.series_batch(seed=15, lengths=[3000, 20_000, 150, 8000])
+    ll, st = run_batched("matern32", bt)
+    assert st == 0
+    for s in range(bt.B):
+        t, y = bt.series(s)
+        m = P.build_model("matern32", bt.lengthscale[s], bt.variance[s])
+        l1, ws = P.loglik(m, dev(t), dev(y), dev(np.ones(t.size, np.uint8), torch.uint8), bt.noise[s])
+        ref = float(l1.cpu().numpy()[0])
+        assert abs(ll[s] - ref) <= 1e-11 * max(abs(ref), t.size)
+
+
+def test_batched_more_series_than_steps():
+    """Many empty series: every offset is still checked, empty series get 0."""
+    bt = wl.series_batch(seed=16, lengths=[0, 0, 1, 0, 2, 0, 0, 0, 3, 0])
+    ll, st = run_batched("matern32", bt)
+    assert st == 0
+    check_series("matern32", bt, ll)
+    assert np.all(ll[[0, 1, 3, 5, 6, 7, 9]] == 0.0)
+
+
+def test_batched_status_flags():
+    bt = wl.series_batch(seed=17, lengths=[100, 200, 300])
+    m = P.build_model("matern32", 1.0, 1.0)
+    args = (dev(bt.t), dev(bt.y), dev(np.ones(bt.t.size, np.uint8), torch.uint8))
+    bad = bt.params().copy()
+    bad[1, 0] = -1.0                            # non-positive lengthscale
+    ll, ws = P.loglik_batched(m, dev(bt.offsets, torch.int64), dev(bad), *args)
+    assert P.status(ws) & P.EBATCH
+    off = bt.offsets.copy()
+    off[1], off[2] = off[2], off[1]             # decreasing offsets
+    ll, ws = P.loglik_batched(m, dev(off, torch.int64), dev(bt.params()), *args)
+    assert P.status(ws) & P.EBATCH
+    off = bt.offsets.copy()
+    off[-1] -= 1                                # offsets[B] != n
+    ll, ws = P.loglik_batched(m, dev(off, torch.int64), dev(bt.params()), *args)
+    assert P.status(ws) & P.EBATCH
+
+
+def test_batched_deterministic():
+    bt = wl.series_batch(seed=18, lengths=[40_000, 123, 7777, 31_000])
+    a, _ = run_batched("rbf", bt)
+    b, _ = run_batched("rbf", bt)
+    assert np.array_equal(a, b)
+
+
+def test_batched_full_size_sampled():
+    """The 4,096-series workload (about 63 M steps, Matern-3/2 and 5/2 mixed)
+    run as one call per family, in the launch configuration of the benchmark;
+    a sample of series (shortest, longest and random ones) against the oracle."""
+    bt = wl.series_batch(**wl.BATCH)
+    kinds = np.array(bt.kind)
+    lens = np.diff(bt.offsets)
+    rng = np.random.default_rng(19)
+    for kind in ("matern32", "matern52"):
+        idx = np.flatnonzero(kinds == kind)
+        sub = wl.subset(bt, idx)
+        ll, st = run_batched(kind, sub)
+        assert st == 0
+        assert np.all(np.isfinite(ll))
+        sl = lens[idx]
+        pick = sorted({int(np.argmin(sl)), int(np.argmax(sl)), *rng.choice(idx.size, 4, replace=False).tolist()})
+        check_series(kind, sub, ll, idx=pick)

@@ -151,6 +151,17 @@ def test_host_argument_errors(lib):
                             None, 0, None) == -1
     assert lib.pssgp_predict(ctypes.byref(mm.raw), None, None, 0, None, 0, 0.01, None, None, None,
                              None, 0, None) == -1
+    assert lib.pssgp_loglik_batched(ctypes.byref(mm.raw), None, 1, None, None, None, None, 10, None,
+                                    None, 0, None) == -1
+    # a model without a lengthscale / variance cannot be rescaled per series
+    # (checked before anything is dereferenced: the pointers here are dummies)
+    o = om.make_model("matern32", 1.0, 1.0)
+    sde = P.model_from_sde(o.G, o.L, o.q, o.H)
+    fake = ctypes.c_void_p(256)
+    assert lib.pssgp_loglik_batched(ctypes.byref(sde.raw), fake, 1, fake, fake, fake, fake, 10, fake,
+                                    fake, 1 << 30, None) == -6
+    assert lib.pssgp_loglik_batched(ctypes.byref(mm.raw), fake, 0, fake, fake, fake, fake, 10, fake,
+                                    fake, 1 << 30, None) == -1
 
 
 def test_workspace_size_grows_linearly(lib):

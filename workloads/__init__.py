@@ -75,3 +75,76 @@ def random_series(seed: int, N: int, M: int, T: float, noise: float = 0.1) -> Se
 SMALL = dict(kind="matern32", lengthscale=0.5, variance=1.0, noise=0.01)
 LARGE_RBF = dict(kind="rbf", order=6, lengthscale=1.0, variance=1.0, noise=0.01)
 LARGE_M52 = dict(kind="matern52", lengthscale=1.0, variance=1.0, noise=0.01)
+
+
+@dataclass
+class Batch:
+    """B independent series concatenated: series s is t[offsets[s]:offsets[s+1]]."""
+    t: np.ndarray
+    y: np.ndarray
+    offsets: np.ndarray      # int64[B + 1]
+    kind: list               # kernel family per series ("matern32" / "matern52")
+    lengthscale: np.ndarray
+    variance: np.ndarray
+    noise: np.ndarray        # noise variance R per series
+
+    @property
+    def B(self) -> int:
+        return self.offsets.size - 1
+
+    def params(self, idx=None) -> np.ndarray:
+        """(lengthscale, variance, noise) rows, float64[B, 3] (or the rows idx)."""
+        p = np.stack([self.lengthscale, self.variance, self.noise], axis=1)
+        return p if idx is None else p[idx]
+
+    def series(self, s: int):
+        a, b = self.offsets[s], self.offsets[s + 1]
+        return self.t[a:b], self.y[a:b]
+
+
+def series_batch(seed: int = 3, B: int = 4096, n_min: int = 1000, n_max: int = 65536, spacing: float = 0.01,
+                 kinds=("matern32", "matern52"), lengths=None) -> Batch:
+    """Many independent series of uneven length (the batched hyperparameter
+    search workload): lengths log-uniform on [n_min, n_max] (or given),
+    times sorted uniform on [0, spacing * n], kernel family drawn uniformly
+    from `kinds`, lengthscale log-uniform on [0.1, 10], variance 1, noise
+    variance log-uniform on [1e-3, 1e-1].  y is a random two-tone sinusoid at
+    frequencies set by the series' lengthscale, with N(0, R) noise."""
+    rng = np.random.default_rng(seed)
+    if lengths is None:
+        lengths = np.rint(np.exp(rng.uniform(np.log(n_min), np.log(n_max), B))).astype(np.int64)
+    lengths = np.asarray(lengths, dtype=np.int64)
+    B = lengths.size
+    offsets = np.zeros(B + 1, dtype=np.int64)
+    np.cumsum(lengths, out=offsets[1:])
+    kind = [kinds[i] for i in rng.integers(0, len(kinds), B)]
+    ell = np.exp(rng.uniform(np.log(0.1), np.log(10.0), B))
+    var = np.ones(B)
+    R = np.exp(rng.uniform(np.log(1e-3), np.log(1e-1), B))
+    n = int(offsets[-1])
+    t = np.empty(n)
+    y = np.empty(n)
+    for s in range(B):
+        a, b = offsets[s], offsets[s + 1]
+        m = b - a
+        ts = np.sort(rng.uniform(0.0, spacing * m, m))
+        w1, w2 = rng.uniform(0.5, 2.0, 2) / ell[s]
+        ph = rng.uniform(0.0, 2.0 * np.pi, 2)
+        t[a:b] = ts
+        y[a:b] = np.sin(w1 * ts + ph[0]) + 0.5 * np.sin(w2 * ts + ph[1]) + rng.normal(0.0, np.sqrt(R[s]), m)
+    return Batch(t, y, offsets, kind, ell, var, R)
+
+
+def subset(bt: Batch, idx) -> Batch:
+    """The series idx of a batch, re-concatenated in that order."""
+    idx = np.asarray(idx, dtype=np.int64)
+    lengths = bt.offsets[idx + 1] - bt.offsets[idx]
+    offsets = np.zeros(idx.size + 1, dtype=np.int64)
+    np.cumsum(lengths, out=offsets[1:])
+    t = np.concatenate([bt.t[bt.offsets[s]:bt.offsets[s + 1]] for s in idx]) if idx.size else np.empty(0)
+    y = np.concatenate([bt.y[bt.offsets[s]:bt.offsets[s + 1]] for s in idx]) if idx.size else np.empty(0)
+    return Batch(t, y, offsets, [bt.kind[s] for s in idx], bt.lengthscale[idx].copy(), bt.variance[idx].copy(),
+                 bt.noise[idx].copy())
+
+
+BATCH = dict(seed=3, B=4096, n_min=1000, n_max=65536, spacing=0.01)
