@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--timing-steps", type=int, default=3)
     ap.add_argument("--warps-per-sm", type=int, default=0, help="scan lanes per SM / 32 (0 = library default)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 4,096-series batched measurement")
     ap.add_argument("--n-train", type=int, default=0,
                     help="profile a prefix of the workload with this many training points (0 = full 2^20)")
     return ap.parse_args()
@@ -239,6 +240,77 @@ def run_reference(args, wl_params):
     return 0
 
 
+def batched_bench(args, P, wl, dev, barrier, world, rank):
+    """Log-likelihood of the 4,096-series batch (lengths log-uniform in
+    [1000, 65536], Matern-3/2 / 5/2 mixed, one pssgp_loglik_batched call per
+    family), autotuned lane counts, both families replayed as one CUDA graph
+    per evaluation; inputs resident in HBM."""
+    import torch
+    bt = wl.series_batch(**dict(wl.BATCH, seed=wl.BATCH["seed"] + rank))
+    kinds = np.array(bt.kind)
+    parts = []
+    for kind in ("matern32", "matern52"):
+        sub = wl.subset(bt, np.flatnonzero(kinds == kind))
+        m = P.build_model(kind, 1.0, 1.0)
+        d = dict(kind=kind, m=m, n=sub.t.size, B=sub.B,
+                 off=torch.as_tensor(sub.offsets, device=dev), par=torch.as_tensor(sub.params(), device=dev),
+                 t=torch.as_tensor(sub.t, device=dev), y=torch.as_tensor(sub.y, device=dev),
+                 mask=torch.ones(sub.t.size, dtype=torch.uint8, device=dev))
+        d["ws"] = P.workspace(m.d, d["n"], dev)
+        d["ll"] = torch.empty(sub.B, dtype=torch.float64, device=dev)
+        parts.append(d)
+    tuning = {}
+    for d in parts:
+        w, _ = P.autotune_loglik_batched(d["m"], d["off"], d["par"], d["t"], d["y"], d["mask"], ws=d["ws"],
+                                         out=d["ll"])
+        tuning[d["kind"]] = {"d": d["m"].d, "warps_per_sm": w}
+
+    def call(d):
+        P.loglik_batched(d["m"], d["off"], d["par"], d["t"], d["y"], d["mask"], ws=d["ws"], out=d["ll"])
+
+    for d in parts:
+        call(d)
+    torch.cuda.synchronize()
+    assert all(P.status(d["ws"]) == 0 for d in parts), "device status error (batched)"
+    g = P.Graph()
+    with g:
+        for d in parts:
+            call(d)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        g.launch()
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.launch()
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        tmax = torch.tensor([ms], device=dev)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        ms = float(tmax.item())
+    P.timing(1)
+    for d in parts:
+        call(d)
+    torch.cuda.synchronize()
+    per = P.timing(2)
+    P.timing(0)
+    n_all = sum(d["n"] for d in parts)
+    return {"workload": "4,096 series, lengths log-uniform [1000, 65536], times U[0, 0.01 n], Matern-3/2 / 5/2 "
+                        "mixed, l log-uniform [0.1, 10], s2 = 1, R log-uniform [1e-3, 1e-1]; log-likelihood of "
+                        "every series, one pssgp_loglik_batched per family, replayed as one CUDA graph",
+            "series": bt.B, "steps_total": int(n_all), "ms_per_eval": ms,
+            "series_per_s": bt.B * world / (ms * 1e-3), "steps_per_s": n_all * world / (ms * 1e-3),
+            "tuning": tuning, "gpu_launches_per_eval": int(sum(c for _, c in per.values())),
+            "kernels_ms": {k: round(v[0], 4) for k, v in per.items()},
+            "l2": "inputs and workspace ~17 GB per evaluation, far above the 126 MB L2"}
+
+
 def run_ours(args, wl_params):
     import torch
     import paper_2102_09964_b300 as P
@@ -396,6 +468,8 @@ def run_ours(args, wl_params):
                        "l2": "workspace traffic ~1 GB per step exceeds the 126 MB L2 (no explicit flush)"},
             "e2e": e2e, "gpu_launches": int(gpu_launches), "clocks": clocks, "roofline": roofline,
             "whole_path_tflops": round(whole, 4), "kernels": kernels}
+    if not args.no_batched:
+        line["batched"] = batched_bench(args, P, wl, dev, barrier, world, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl_params)
     if rank == 0:

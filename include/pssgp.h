@@ -131,7 +131,8 @@ int pssgp_model_from_sde(int32_t d, const double* G, const double* L, double q,
 
 /* ---- workspace --------------------------------------------------------- */
 /* Bytes of device workspace for a call on n merged steps with state
- * dimension d (valid for every entry point below with the same n, d). */
+ * dimension d (valid for every entry point below with the same n, d, and
+ * for every scan tuning: sized for the largest lane count). */
 size_t pssgp_workspace_size(int32_t d, int64_t n);
 
 /* Copies the device status word of the last call that used `ws` to *status,
@@ -226,7 +227,8 @@ int pssgp_loglik_batched(const pssgp_model* model, const int64_t* offsets,
  *  - Scratch: a fixed 32 MiB array inside the library's device image, held on
  *    every GPU that loads the library until the process exits.  That bounds
  *    the problem size: n up to about 28,000 merged steps at d = 6 and about
- *    160,000 at d = 2 (exactly: pssgp_workspace_size(d, n) <= 32 MiB).  Larger
+ *    160,000 at d = 2 (exactly: the workspace of the current scan tuning,
+ *    at most pssgp_workspace_size(d, n), must fit in 32 MiB).  Larger
  *    problems are rejected with PSSGP_ESCRATCH before anything is launched.
  *  - The first call on a device looks up the scratch's device address
  *    (cudaGetSymbolAddress, with that device current); make that first call
@@ -277,11 +279,46 @@ int pssgp_timing(int32_t mode, double* ms, int64_t* counts, int32_t nslots);
 /* Name of timing slot `slot` ("" if unused). */
 const char* pssgp_timing_name(int32_t slot);
 
-/* Scan tuning: the number of chunks ("lanes") of the scans is
- * SMs x warps_per_sm x 32 (4 or 8; default 4).  More lanes give each SM more
- * warps to hide latency but shorter chunks and more scan overhead.  Affects
- * calls planned afterwards, including pssgp_workspace_size (query it again). */
+/* Scan tuning: the number of chunks ("lanes", one per thread) of the scans
+ * is SMs x warps_per_sm x 32, i.e. n / (SMs x warps_per_sm x 32) steps per
+ * thread; warps_per_sm is 4, 8, 12 or 16 (default 4).  More lanes give each
+ * SM more warps to hide latency but shorter chunks and more scan overhead.
+ * Affects calls planned afterwards.  pssgp_set_warps_per_sm sets every state
+ * dimension; pssgp_tune_set one (PSSGP_EDIM for d outside 1..8);
+ * pssgp_tune_get returns the current value for d. */
 int pssgp_set_warps_per_sm(int32_t warps_per_sm);
+int pssgp_tune_set(int32_t d, int32_t warps_per_sm);
+int pssgp_tune_get(int32_t d);
+
+/* Autotuner: runs pssgp_loglik_batched (same arguments) once per candidate
+ * warps_per_sm (4, 8, 12, 16) to warm up and then `reps` times between two
+ * CUDA events on `stream`; keeps the fastest for model->d (pssgp_tune_set)
+ * and reports it in *best_warps and its mean milliseconds per call in
+ * *best_ms (nullable).  Synchronises `stream`.  On an error the previous
+ * tuning is restored and the error returned. */
+int pssgp_autotune_loglik_batched(const pssgp_model* model,
+                                  const int64_t* offsets, int32_t B,
+                                  const double* params, const double* t,
+                                  const double* y, const uint8_t* mask,
+                                  int64_t n, double* loglik, void* ws,
+                                  size_t ws_bytes, void* stream, int32_t reps,
+                                  int32_t* best_warps, float* best_ms);
+
+/* ---- CUDA graphs --------------------------------------------------------- */
+/* Record the launches of any sequence of library calls made on `stream`
+ * between pssgp_graph_begin and pssgp_graph_end (thread-local stream
+ * capture) into a graph, and replay the whole sequence with one
+ * pssgp_graph_launch.  The graph keeps the pointers and sizes of the
+ * recorded calls: device data they point to (inputs, per-series parameters)
+ * may change between launches, shapes may not.  `stream` must not be the
+ * legacy default stream (PSSGP_EINVAL).  While recording, calls only enqueue
+ * work: do not call pssgp_get_status, pssgp_timing(2) or the autotuner.
+ * pssgp_graph_end returns PSSGP_ECUDA if the capture was invalidated. */
+typedef struct pssgp_graph_s pssgp_graph;
+int pssgp_graph_begin(void* stream);
+int pssgp_graph_end(void* stream, pssgp_graph** out);
+int pssgp_graph_launch(pssgp_graph* graph, void* stream);
+int pssgp_graph_destroy(pssgp_graph* graph);
 
 /* sizeof(pssgp_model) as compiled into the library, for bindings that mirror
  * the struct (ABI check). */

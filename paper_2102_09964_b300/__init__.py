@@ -84,6 +84,15 @@ def lib():
         L.pssgp_fp64_fma_rate.argtypes = [ctypes.POINTER(dp)]
         L.pssgp_timing.argtypes = [i32, vp, vp, i32]
         L.pssgp_set_warps_per_sm.argtypes = [i32]
+        L.pssgp_tune_set.argtypes = [i32, i32]
+        L.pssgp_tune_get.argtypes = [i32]
+        L.pssgp_autotune_loglik_batched.argtypes = [ctypes.POINTER(PssgpModel), vp, i32, vp, vp, vp, vp, i64, vp,
+                                                    vp, sz, vp, i32, ctypes.POINTER(i32),
+                                                    ctypes.POINTER(ctypes.c_float)]
+        L.pssgp_graph_begin.argtypes = [vp]
+        L.pssgp_graph_end.argtypes = [vp, ctypes.POINTER(vp)]
+        L.pssgp_graph_launch.argtypes = [vp, vp]
+        L.pssgp_graph_destroy.argtypes = [vp]
         L.pssgp_loglik_noalloc.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, vp, vp]
         L.pssgp_timing_name.argtypes = [i32]
         L.pssgp_timing_name.restype = ctypes.c_char_p
@@ -328,5 +337,103 @@ def timing(mode: int):
 
 
 def set_warps_per_sm(w: int):
-    """Scan tuning knob (4 or 8 warps per SM); re-create workspaces afterwards."""
+    """Scan tuning knob for every state dimension (4, 8, 12 or 16 warps per SM)."""
     _check(lib().pssgp_set_warps_per_sm(int(w)), "pssgp_set_warps_per_sm")
+
+
+def tune_set(d: int, w: int):
+    """Scan tuning knob for state dimension d (4, 8, 12 or 16 warps per SM)."""
+    _check(lib().pssgp_tune_set(int(d), int(w)), "pssgp_tune_set")
+
+
+def tune_get(d: int) -> int:
+    w = lib().pssgp_tune_get(int(d))
+    _check(min(w, 0), "pssgp_tune_get")
+    return w
+
+
+def _tune_key(d: int, n: int, B: int) -> str:
+    import math
+    name = torch.cuda.get_device_name()
+    return f"{name}|loglik_batched|d={d}|n=2^{round(math.log2(max(n, 1)))}|B=2^{round(math.log2(max(B, 1)))}"
+
+
+def autotune_loglik_batched(model: Model, offsets, params, t, y, mask, ws=None, out=None, reps: int = 3,
+                            cache: str | None = None):
+    """Pick the scan lane count for this batch shape by timing every candidate
+    (native autotuner), and apply it for model.d.  With `cache` (a JSON file),
+    a stored choice for the same device, d and size class is applied without
+    timing, and new choices are stored.  Returns (warps_per_sm, ms or None)."""
+    import json
+    import os
+    d, n = model.d, t.numel()
+    B = offsets.numel() - 1
+    key = _tune_key(d, n, B)
+    table = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            table = json.load(f)
+        if key in table:
+            tune_set(d, int(table[key]["warps_per_sm"]))
+            return int(table[key]["warps_per_sm"]), None
+    ws = ws if ws is not None else workspace(d, n, t.device)
+    ll = out if out is not None else torch.empty(B, dtype=torch.float64, device=t.device)
+    params = _f64(params, t.device).reshape(-1)
+    w = ctypes.c_int32(0)
+    ms = ctypes.c_float(0.0)
+    rc = lib().pssgp_autotune_loglik_batched(ctypes.byref(model.raw), _ptr(offsets), B, _ptr(params), _ptr(t),
+                                             _ptr(y), _ptr(mask), n, _ptr(ll), _ptr(ws), ws.numel(), _stream(),
+                                             int(reps), ctypes.byref(w), ctypes.byref(ms))
+    _check(rc, "pssgp_autotune_loglik_batched")
+    if cache:
+        table[key] = {"warps_per_sm": int(w.value), "ms": float(ms.value)}
+        with open(cache, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+    return int(w.value), float(ms.value)
+
+
+class Graph:
+    """A sequence of library calls recorded once into a CUDA graph and replayed
+    with one launch (native stream capture).  Use on a non-default stream:
+
+        g = Graph(stream)
+        with g:
+            loglik_batched(..., ws=ws, out=ll)     # buffers allocated beforehand
+        g.launch()                                  # replays all recorded launches
+    """
+
+    def __init__(self, stream: torch.cuda.Stream | None = None):
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self._h = ctypes.c_void_p(None)
+        self._ctx = None
+
+    def __enter__(self):
+        self._ctx = torch.cuda.stream(self.stream)
+        self._ctx.__enter__()
+        _check(lib().pssgp_graph_begin(ctypes.c_void_p(self.stream.cuda_stream)), "pssgp_graph_begin")
+        return self
+
+    def __exit__(self, exc_type, exc, tb):
+        h = ctypes.c_void_p(None)
+        rc = lib().pssgp_graph_end(ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        self._ctx.__exit__(exc_type, exc, tb)
+        if exc_type is None:
+            _check(rc, "pssgp_graph_end")
+            self._h = h
+        return False
+
+    def launch(self):
+        """Enqueue the recorded work on the graph's stream and make the current
+        stream wait for it."""
+        cur = torch.cuda.current_stream()
+        self.stream.wait_stream(cur)
+        _check(lib().pssgp_graph_launch(self._h, ctypes.c_void_p(self.stream.cuda_stream)), "pssgp_graph_launch")
+        cur.wait_stream(self.stream)
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            try:
+                lib().pssgp_graph_destroy(self._h)
+            except Exception:
+                pass
+            self._h = ctypes.c_void_p(None)

@@ -37,7 +37,9 @@ using namespace pssgp;
 namespace {
 
 constexpr int BLOCK = 128;           // 4 warps: one per SM sub-partition
-int g_warps_per_sm = 4;              // lanes per SM / 32 (pssgp_set_warps_per_sm)
+// lanes per SM / 32, per state dimension (pssgp_set_warps_per_sm, pssgp_tune_set)
+constexpr int WARPS_MAX = 16;
+int g_warps_per_sm[PSSGP_DMAX + 1] = {4, 4, 4, 4, 4, 4, 4, 4, 4};
 constexpr int MIN_CHUNK = 8;         // steps per lane below which fewer lanes are used
 
 // ---------------------------------------------------------------------------
@@ -122,11 +124,17 @@ struct Plan {
       o_tpos, o_rstep, o_seg, o_llstep, total;
 };
 
-Plan make_plan(int d, int64_t n, int64_t lanes_req) {
+int warps_for(int d) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_warps_per_sm[d];
+}
+
+// warps: lanes per SM / 32 (0: the current tuning for d)
+Plan make_plan(int d, int64_t n, int64_t lanes_req, int warps = 0) {
   Plan p{};
   p.d = d;
   p.n = n;
-  const int64_t lanes_max = (int64_t)num_sms() * g_warps_per_sm * 32;
+  const int64_t lanes_max = (int64_t)num_sms() * (warps > 0 ? warps : warps_for(d)) * 32;
   const int64_t want = (n + MIN_CHUNK - 1) / MIN_CHUNK;
   int64_t P0 = std::min(lanes_max, std::max<int64_t>(want, 1));
   if (lanes_req > 0) P0 = lanes_req;
@@ -1115,7 +1123,7 @@ int filter_common(const pssgp_model* model, const double* t, const double* y, co
 // ===========================================================================
 extern "C" size_t pssgp_workspace_size(int32_t d, int64_t n) {
   if (d < 1 || d > PSSGP_DMAX || n < 1) return 0;
-  return (size_t)make_plan(d, n, 0).total;
+  return (size_t)make_plan(d, n, 0, WARPS_MAX).total;   // enough for every tuning
 }
 
 extern "C" int pssgp_get_status(void* ws, void* stream, int32_t* status) {
@@ -1451,8 +1459,112 @@ extern "C" int pssgp_loglik_noalloc(const pssgp_model* model, const double* t, c
 }
 
 extern "C" int pssgp_set_warps_per_sm(int32_t warps_per_sm) {
-  if (warps_per_sm < 4 || warps_per_sm > 8 || warps_per_sm % 4) return PSSGP_EINVAL;
+  if (warps_per_sm < 4 || warps_per_sm > WARPS_MAX || warps_per_sm % 4) return PSSGP_EINVAL;
   std::lock_guard<std::mutex> lk(g_mu);
-  g_warps_per_sm = warps_per_sm;
+  for (int d = 0; d <= PSSGP_DMAX; ++d) g_warps_per_sm[d] = warps_per_sm;
+  return PSSGP_OK;
+}
+
+extern "C" int pssgp_tune_set(int32_t d, int32_t warps_per_sm) {
+  if (d < 1 || d > PSSGP_DMAX) return PSSGP_EDIM;
+  if (warps_per_sm < 4 || warps_per_sm > WARPS_MAX || warps_per_sm % 4) return PSSGP_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_warps_per_sm[d] = warps_per_sm;
+  return PSSGP_OK;
+}
+
+extern "C" int pssgp_tune_get(int32_t d) {
+  if (d < 1 || d > PSSGP_DMAX) return PSSGP_EDIM;
+  return warps_for(d);
+}
+
+// ===========================================================================
+// Autotuner: times the candidate lane counts on the caller's own problem
+// ===========================================================================
+extern "C" int pssgp_autotune_loglik_batched(const pssgp_model* model, const int64_t* offsets, int32_t B,
+                                             const double* params, const double* t, const double* y,
+                                             const uint8_t* mask, int64_t n, double* loglik, void* ws,
+                                             size_t ws_bytes, void* stream, int32_t reps, int32_t* best_warps,
+                                             float* best_ms) {
+  if (!model_ok(model) || !best_warps || reps < 1) return PSSGP_EINVAL;
+  const int d = model->d;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int saved = warps_for(d);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return PSSGP_ECUDA;
+  }
+  int best = saved, rc = PSSGP_OK;
+  float best_t = 0.0f;
+  for (int w = 4; w <= WARPS_MAX && rc == PSSGP_OK; w += 4) {
+    pssgp_tune_set(d, w);
+    rc = pssgp_loglik_batched(model, offsets, B, params, t, y, mask, n, loglik, ws, ws_bytes, stream);  // warm-up
+    if (rc) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && rc == PSSGP_OK; ++r)
+      rc = pssgp_loglik_batched(model, offsets, B, params, t, y, mask, n, loglik, ws, ws_bytes, stream);
+    cudaEventRecord(e1, s);
+    float ms = 0.0f;
+    if (rc == PSSGP_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      rc = PSSGP_ECUDA;
+    ms /= (float)reps;
+    if (rc == PSSGP_OK && (best_t == 0.0f || ms < best_t)) { best_t = ms; best = w; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  pssgp_tune_set(d, rc == PSSGP_OK ? best : saved);
+  if (rc) return rc;
+  *best_warps = best;
+  if (best_ms) *best_ms = best_t;
+  return PSSGP_OK;
+}
+
+// ===========================================================================
+// CUDA graphs: record a sequence of library calls once, replay it with one
+// launch
+// ===========================================================================
+struct pssgp_graph_s {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" int pssgp_graph_begin(void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!s) return PSSGP_EINVAL;   // the legacy default stream cannot be captured
+  return cuda_rc(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+}
+
+extern "C" int pssgp_graph_end(void* stream, pssgp_graph_s** out) {
+  if (!out) return PSSGP_EINVAL;
+  *out = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(s, &g) != cudaSuccess || !g) {
+    (void)cudaGetLastError();
+    return PSSGP_ECUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return PSSGP_ECUDA;
+  }
+  pssgp_graph_s* h = new pssgp_graph_s;
+  h->graph = g;
+  h->exec = ex;
+  *out = h;
+  return PSSGP_OK;
+}
+
+extern "C" int pssgp_graph_launch(pssgp_graph_s* g, void* stream) {
+  if (!g || !g->exec) return PSSGP_EINVAL;
+  return cuda_rc(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+}
+
+extern "C" int pssgp_graph_destroy(pssgp_graph_s* g) {
+  if (!g) return PSSGP_EINVAL;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
   return PSSGP_OK;
 }

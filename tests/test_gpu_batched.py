@@ -162,3 +162,69 @@ def test_batched_full_size_sampled():
         sl = lens[idx]
         pick = sorted({int(np.argmin(sl)), int(np.argmax(sl)), *rng.choice(idx.size, 4, replace=False).tolist()})
         check_series(kind, sub, ll, idx=pick)
+
+
+@pytest.mark.parametrize("warps", [4, 8, 12, 16])
+def test_batched_every_tuning(warps):
+    """Every lane count the autotuner may pick gives the oracle's results."""
+    bt = wl.series_batch(seed=20, lengths=[70_000, 5, 33_333, 129, 100_000, 1])
+    saved = P.tune_get(3)
+    try:
+        P.tune_set(3, warps)
+        ll, st = run_batched("matern52", bt)
+    finally:
+        P.tune_set(3, saved)
+    assert st == 0
+    check_series("matern52", bt, ll)
+
+
+def test_autotune_keeps_results():
+    bt = wl.series_batch(seed=21, lengths=[50_000, 20_000, 90_000, 3])
+    m = P.build_model("matern32", 1.0, 1.0)
+    args = (dev(bt.offsets, torch.int64), dev(bt.params()), dev(bt.t), dev(bt.y),
+            dev(np.ones(bt.t.size, np.uint8), torch.uint8))
+    saved = P.tune_get(2)
+    try:
+        w, ms = P.autotune_loglik_batched(m, *args, reps=2)
+        assert w in (4, 8, 12, 16) and ms > 0.0
+        assert P.tune_get(2) == w
+        ll, ws = P.loglik_batched(m, *args)
+    finally:
+        P.tune_set(2, saved)
+    assert P.status(ws) == 0
+    check_series("matern32", bt, ll.cpu().numpy())
+
+
+def test_graph_replay_with_new_parameters():
+    """Both families of a mixed batch recorded into one CUDA graph; the
+    per-series parameters are device data, so a replay after updating them
+    in place gives the new log-likelihoods (bit-identical to direct calls)."""
+    bt = wl.series_batch(seed=22, B=24, n_min=1000, n_max=20_000)
+    kinds = np.array(bt.kind)
+    parts = []
+    for kind in ("matern32", "matern52"):
+        sub = wl.subset(bt, np.flatnonzero(kinds == kind))
+        m = P.build_model(kind, 1.0, 1.0)
+        d = dict(m=m, sub=sub, off=dev(sub.offsets, torch.int64), par=dev(sub.params()), t=dev(sub.t),
+                 y=dev(sub.y), mask=dev(np.ones(sub.t.size, np.uint8), torch.uint8))
+        d["ws"] = P.workspace(m.d, sub.t.size, torch.device("cuda"))
+        d["ll"] = torch.empty(sub.B, dtype=torch.float64, device="cuda")
+        P.loglik_batched(d["m"], d["off"], d["par"], d["t"], d["y"], d["mask"], ws=d["ws"], out=d["ll"])  # warm-up
+        parts.append((kind, d))
+    torch.cuda.synchronize()
+    g = P.Graph()
+    with g:
+        for _, d in parts:
+            P.loglik_batched(d["m"], d["off"], d["par"], d["t"], d["y"], d["mask"], ws=d["ws"], out=d["ll"])
+    for scale in (1.0, 1.7):
+        for _, d in parts:
+            d["par"][:, 0] = torch.as_tensor(d["sub"].lengthscale * scale, device="cuda")
+        g.launch()
+        torch.cuda.synchronize()
+        for kind, d in parts:
+            got = d["ll"].cpu().numpy().copy()
+            ref, _ = P.loglik_batched(d["m"], d["off"], d["par"], d["t"], d["y"], d["mask"])
+            assert np.array_equal(got, ref.cpu().numpy())
+            sub = wl.subset(d["sub"], np.arange(d["sub"].B))
+            sub.lengthscale = sub.lengthscale * scale
+            check_series(kind, sub, got, idx=[0, sub.B - 1])
