@@ -17,7 +17,11 @@ Logarithmic Time".  What the oracle computes (all in long double inside
 * sequential RTS smoother, supplement Eq. (smoother) with the sign of the
   covariance term taken from the proof of Prop. 2;
 * the parallel-filter elements and operator (Sec. 3) and the parallel-smoother
-  elements and operator (supplement, Prop. 2), for the Prop. 1/2 checks.
+  elements and operator (supplement, Prop. 2), for the Prop. 1/2 checks;
+* the gradient of the log-likelihood in (log lengthscale, log variance,
+  log noise) by forward mode: the Frechet derivative of the Van Loan
+  exponential and the differentiated sequential filter
+  (``loglik_grad_fwd``), plus central differences (``loglik_grad_fd``).
 
 Model formation (``model.py``), merge (``merge.py``) and the dense GP
 (``dense_gp.py``) are numpy.
@@ -29,6 +33,7 @@ brute-force bracketings); none is "parity unpinned".
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from dataclasses import dataclass
@@ -214,3 +219,82 @@ def predict(m, t_train, y_train, t_test, R):
     t, y, mask, test_pos = merge(t_train, y_train, t_test)
     res = run(m, t, y, mask, R)
     return res.f_mean[test_pos], res.f_var[test_pos], res, (t, y, mask, test_pos)
+
+
+# ---------------------------------------------------------------------------
+# Gradient of the log marginal likelihood with respect to
+# theta = (log lengthscale, log variance, log noise variance)
+# ---------------------------------------------------------------------------
+GRAD_PARAMS = ("log_lengthscale", "log_variance", "log_noise")
+
+
+def loglik_tangent(m, t, y, mask, R, param):
+    """(loglik, d loglik / d param) by forward mode through the discretisation
+    (Frechet derivative of the Van Loan exponential) and the sequential
+    Kalman filter, with the model's tangent from ``model.model_tangent``.
+    ``m`` must be the unbalanced model; R scalar or per step."""
+    from . import model as _model
+    lib = _load()
+    d = m.d
+    t = _c(t)
+    n = t.size
+    Ra, per = _R_arr(R, n)
+    if param == "log_noise":
+        dG = np.zeros((d, d)); dW = np.zeros((d, d)); dPinf = np.zeros((d, d))
+        dRa = Ra.copy()
+    else:
+        dG, dW, dPinf = _model.model_tangent(m, param)
+        dRa = np.zeros_like(Ra)
+    F = np.empty((n, d, d)); Q = np.empty((n, d, d)); dF = np.empty((n, d, d)); dQ = np.empty((n, d, d))
+    rc = lib.orc_discretize_tangent(d, _p(_c(m.G)), _p(_c(m.W)), _p(_c(m.Pinf)), _p(_c(dG)), _p(_c(dW)),
+                                    _p(_c(dPinf)), _p(t), ctypes.c_long(n), _p(F), _p(Q), _p(dF), _p(dQ))
+    _check(rc, "discretize_tangent")
+    y = _c(y)
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    ll = ctypes.c_double(0.0)
+    dll = ctypes.c_double(0.0)
+    rc = lib.orc_loglik_tangent(d, _p(_c(m.H).ravel()), _p(Ra), _p(dRa), per, _p(F), _p(Q), _p(dF), _p(dQ),
+                                _p(y), _u8(mask), ctypes.c_long(n), ctypes.byref(ll), ctypes.byref(dll))
+    _check(rc, "loglik_tangent")
+    return ll.value, dll.value
+
+
+def loglik_grad_fwd(kind, lengthscale, variance, t, y, mask, R, order=6):
+    """(loglik, gradient over GRAD_PARAMS) by forward mode, one direction at a
+    time (R scalar or per step; d/d log noise scales every R_k)."""
+    from . import model as _model
+    m = _model.make_model(kind, lengthscale, variance, order=order)
+    g = []
+    ll = None
+    for p in GRAD_PARAMS:
+        ll, dl = loglik_tangent(m, t, y, mask, R, p)
+        g.append(dl)
+    return ll, np.array(g)
+
+
+def loglik_at(kind, lengthscale, variance, t, y, mask, R, order=6):
+    """The oracle log-likelihood of the model built at these hyperparameters."""
+    from . import model as _model
+    m = _model.make_model(kind, lengthscale, variance, order=order)
+    F, Q = discretize(m, t)
+    return kalman_filter(m, F, Q, y, mask, R)[4]
+
+
+def loglik_grad_fd(kind, lengthscale, variance, t, y, mask, R, h=1e-6, order=6):
+    """Central finite differences of the oracle log-likelihood in
+    (log lengthscale, log variance, log noise), step h in each log parameter."""
+    base = np.log([lengthscale, variance])
+    R = np.asarray(R, dtype=np.float64)
+    g = []
+    for i in range(3):
+        vals = []
+        for sgn in (1.0, -1.0):
+            th = base.copy()
+            Rp = R
+            if i < 2:
+                th[i] += sgn * h
+            else:
+                Rp = R * math.exp(sgn * h)
+            vals.append(loglik_at(kind, math.exp(th[0]), math.exp(th[1]), t, y, mask, Rp, order=order))
+        g.append((vals[0] - vals[1]) / (2.0 * h))
+    return np.array(g)

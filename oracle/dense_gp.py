@@ -36,3 +36,24 @@ def posterior(kfun, t_all: np.ndarray, mask: np.ndarray, y_all: np.ndarray, R):
     logdet = 2.0 * np.sum(np.log(np.diag(cf[0])))
     loglik = -0.5 * float(yo @ alpha) - 0.5 * logdet - 0.5 * to.size * math.log(2.0 * math.pi)
     return mean, var, loglik
+
+
+def loglik_grad(kfun, dkfuns, t: np.ndarray, y: np.ndarray, R: float, dR: float):
+    """Gradient of log N(y; 0, K + R I) with respect to parameters theta_i,
+    given dK/dtheta_i as covariance functions dkfuns[i] (None for the noise
+    parameter, whose derivative is dR I):
+        d loglik / d theta = 1/2 alpha^T dK alpha - 1/2 tr(K^-1 dK),
+        alpha = (K + R I)^-1 y.
+    Returns (loglik, [gradients])."""
+    tau = t[:, None] - t[None, :]
+    Ky = kfun(tau) + R * np.eye(t.size)
+    cf = cho_factor(Ky, lower=True)
+    alpha = cho_solve(cf, y)
+    Kinv = cho_solve(cf, np.eye(t.size))
+    logdet = 2.0 * np.sum(np.log(np.diag(cf[0])))
+    ll = -0.5 * float(y @ alpha) - 0.5 * logdet - 0.5 * t.size * math.log(2.0 * math.pi)
+    out = []
+    for dk in dkfuns:
+        dK = dR * np.eye(t.size) if dk is None else dk(tau)
+        out.append(0.5 * float(alpha @ dK @ alpha) - 0.5 * float(np.sum(Kinv * dK)))
+    return ll, out

@@ -216,3 +216,58 @@ def ssm_kernel(m: SSModel):
             out += c * np.exp(l * a)
         return out.real
     return k
+
+
+# ---------------------------------------------------------------------------
+# Derivatives of the model with respect to the log hyperparameters, for the
+# forward-mode gradient of the log marginal likelihood (Sec. 2, parameter
+# estimation).  In the unbalanced companion form built above, both families
+# have drift coefficients a_k proportional to lengthscale^(k - d) (Matern:
+# a_k = binom(d, k) lam^(d - k) with lam = sqrt(2 nu) / lengthscale; RBF: the
+# roots of P(s), a polynomial in lengthscale * s, scale as 1 / lengthscale)
+# and a white-noise density q proportional to variance * lengthscale^(1 - 2d)
+# (Matern: lam^(2 nu) = lam^(2d - 1); RBF: lengthscale / lengthscale^(2n)).
+# Hence, with G[d-1, k] = -a_k and W = q L L^T,
+#   d G[d-1, k] / d log l = -(d - k) G[d-1, k],  dW / d log l = (1 - 2d) W,
+#   dG / d log s2 = 0,                           dW / d log s2 = W,
+# and dP_inf follows from differentiating G P + P G^T + W = 0:
+#   G dP + dP G^T + (dG P + P dG^T + dW) = 0.
+# ---------------------------------------------------------------------------
+
+def model_tangent(m: SSModel, param: str):
+    """(dG, dW, dP_inf) of an unbalanced model for param in
+    {'log_lengthscale', 'log_variance'}."""
+    d = m.d
+    if not np.all(m.D == 1.0):
+        raise ValueError("model_tangent needs the unbalanced model")
+    W = m.W
+    if param == "log_lengthscale":
+        dG = np.zeros((d, d))
+        for k in range(d):
+            dG[d - 1, k] = -(d - k) * m.G[d - 1, k]
+        dW = (1.0 - 2.0 * d) * W
+    elif param == "log_variance":
+        dG = np.zeros((d, d))
+        dW = W.copy()
+    else:
+        raise ValueError(param)
+    dPinf = lyapunov(m.G, dG @ m.Pinf + m.Pinf @ dG.T + dW)
+    return dG, dW, dPinf
+
+
+def matern_kernel_dlogl(nu: float, lengthscale: float, variance: float):
+    """d k / d log(lengthscale) of the textbook Matern covariance, written out
+    from k(tau) = variance f(r), r = sqrt(2 nu) |tau| / lengthscale:
+    d k / d log l = -r variance f'(r)."""
+    def dk(tau):
+        r = np.abs(tau) / lengthscale
+        if nu == 0.5:
+            return variance * r * np.exp(-r)
+        if nu == 1.5:
+            s = math.sqrt(3.0) * r
+            return variance * s * s * np.exp(-s)
+        if nu == 2.5:
+            s = math.sqrt(5.0) * r
+            return variance * s * s * (1.0 + s) / 3.0 * np.exp(-s)
+        raise ValueError(nu)
+    return dk

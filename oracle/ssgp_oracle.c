@@ -551,3 +551,240 @@ int orc_smoother_combine(int d,
 
 /* Library self-identification for the ctypes loader. */
 int orc_version(void) { return 1; }
+
+/* ----------------------------------------------------------------------- */
+/* Forward-mode (tangent) derivative of the log marginal likelihood        */
+/* (Sec. 2, parameter estimation by maximising the marginal likelihood).   */
+/*                                                                         */
+/* Discretisation tangents: the Frechet derivative of the matrix           */
+/* exponential in direction B is the upper-right block of                  */
+/*   exp([[A, B], [0, A]]),                                                */
+/* applied to Van Loan's block A = [[-G, W], [0, G^T]] h with the tangent  */
+/* B = [[-dG, dW], [0, dG^T]] h; then F = E22^T, Q = F E12 give            */
+/* dF = dE22^T, dQ = dF E12 + F dE12.  Long steps are halved as in         */
+/* discretize_one and doubled back with the differentiated identities      */
+/*   F(2h) = F F,  Q(2h) = F Q F^T + Q.                                    */
+/* ----------------------------------------------------------------------- */
+#define BMAX (4 * DMAX)
+
+/* C = A B, all n x n (n <= BMAX), C may alias A or B */
+static void mm_big(int n, const real *A, const real *B, real *C) {
+  static __thread real T[BMAX * BMAX];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      real s = 0.0L;
+      for (int k = 0; k < n; ++k) s += A[i * n + k] * B[k * n + j];
+      T[i * n + j] = s;
+    }
+  memcpy(C, T, sizeof(real) * n * n);
+}
+
+/* exp(A) for n <= BMAX: the same scaling, Taylor sum and squaring as expm */
+static void expm_big(int n, const real *A, real *E) {
+  real nrm = 0.0L;
+  for (int j = 0; j < n; ++j) {
+    real c = 0.0L;
+    for (int i = 0; i < n; ++i) c += fabsl(A[i * n + j]);
+    if (c > nrm) nrm = c;
+  }
+  int s = 0;
+  while (nrm > 0.5L) { nrm *= 0.5L; ++s; }
+  static __thread real As[BMAX * BMAX], T[BMAX * BMAX];
+  real sc = ldexpl(1.0L, -s);
+  for (int i = 0; i < n * n; ++i) As[i] = A[i] * sc;
+  memset(E, 0, sizeof(real) * n * n);
+  memset(T, 0, sizeof(real) * n * n);
+  for (int i = 0; i < n; ++i) { E[i * n + i] = 1.0L; T[i * n + i] = 1.0L; }
+  for (int k = 1; k <= 80; ++k) {
+    mm_big(n, T, As, T);
+    real tmax = 0.0L, emax = 0.0L;
+    for (int i = 0; i < n * n; ++i) {
+      T[i] /= (real)k;
+      E[i] += T[i];
+      if (fabsl(T[i]) > tmax) tmax = fabsl(T[i]);
+      if (fabsl(E[i]) > emax) emax = fabsl(E[i]);
+    }
+    if (k > 2 && tmax <= 1e-30L * emax) break;
+  }
+  for (int i = 0; i < s; ++i) mm_big(n, E, E, E);
+}
+
+static void vanloan_tangent(int d, const real *G, const real *W, const real *dG, const real *dW, real h,
+                            real *F, real *Q, real *dF, real *dQ) {
+  int n = 2 * d, N = 4 * d;
+  real X[BMAX * BMAX], E[BMAX * BMAX];
+  memset(X, 0, sizeof(X));
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      /* diagonal blocks: Van Loan's matrix C */
+      for (int b = 0; b < 2; ++b) {
+        int o = b * n;
+        X[(o + i) * N + o + j] = -G[i * d + j] * h;
+        X[(o + i) * N + o + d + j] = W[i * d + j] * h;
+        X[(o + d + i) * N + o + d + j] = G[j * d + i] * h;
+      }
+      /* upper-right block: its tangent */
+      X[i * N + n + j] = -dG[i * d + j] * h;
+      X[i * N + n + d + j] = dW[i * d + j] * h;
+      X[(d + i) * N + n + d + j] = dG[j * d + i] * h;
+    }
+  expm_big(N, X, E);
+  real E12[DMAX * DMAX], dE12[DMAX * DMAX], T1[DMAX * DMAX], T2[DMAX * DMAX];
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      F[i * d + j] = E[(d + j) * N + d + i];            /* F  = E22^T  */
+      E12[i * d + j] = E[i * N + d + j];
+      dF[i * d + j] = E[(d + j) * N + n + d + i];       /* dF = dE22^T */
+      dE12[i * d + j] = E[i * N + n + d + j];
+    }
+  mm(d, d, d, F, E12, Q);                               /* Q  = F E12  */
+  mm(d, d, d, dF, E12, T1);
+  mm(d, d, d, F, dE12, T2);
+  for (int i = 0; i < d * d; ++i) dQ[i] = T1[i] + T2[i];  /* dQ = dF E12 + F dE12 */
+  symmetrize(d, Q);
+  symmetrize(d, dQ);
+}
+
+static void discretize_tangent_one(int d, const real *G, const real *W, const real *dG, const real *dW, real h,
+                                   real *F, real *Q, real *dF, real *dQ) {
+  real gn = 0.0L;
+  for (int j = 0; j < d; ++j) {
+    real c = 0.0L;
+    for (int i = 0; i < d; ++i) c += fabsl(G[i * d + j]);
+    if (c > gn) gn = c;
+  }
+  int s = 0;
+  while (gn * ldexpl(h, -s) > 0.5L) ++s;
+  vanloan_tangent(d, G, W, dG, dW, ldexpl(h, -s), F, Q, dF, dQ);
+  for (int r = 0; r < s; ++r) {
+    real Ft[DMAX * DMAX], dFt[DMAX * DMAX], T[DMAX * DMAX], A1[DMAX * DMAX], A2[DMAX * DMAX],
+        A3[DMAX * DMAX], A4[DMAX * DMAX];
+    tr(d, d, F, Ft);
+    tr(d, d, dF, dFt);
+    /* dQ' = dF Q F^T + F dQ F^T + F Q dF^T + dQ */
+    mm(d, d, d, dF, Q, T);  mm(d, d, d, T, Ft, A1);
+    mm(d, d, d, F, dQ, T);  mm(d, d, d, T, Ft, A2);
+    mm(d, d, d, F, Q, T);   mm(d, d, d, T, dFt, A3);
+    /* Q' = F Q F^T + Q */
+    mm(d, d, d, T, Ft, A4);
+    for (int i = 0; i < d * d; ++i) {
+      dQ[i] += A1[i] + A2[i] + A3[i];
+      Q[i] += A4[i];
+    }
+    symmetrize(d, Q);
+    symmetrize(d, dQ);
+    /* dF' = dF F + F dF,  F' = F F */
+    mm(d, d, d, dF, F, A1);
+    mm(d, d, d, F, dF, A2);
+    for (int i = 0; i < d * d; ++i) dF[i] = A1[i] + A2[i];
+    mm(d, d, d, F, F, F);
+  }
+}
+
+/* Per-step F, Q (as orc_discretize) and their tangents for one direction
+ * (dG, dW, dPinf: derivatives of the model's G, W = L q L^T and P_inf). */
+int orc_discretize_tangent(int d, const double *G_, const double *W_, const double *Pinf_, const double *dG_,
+                           const double *dW_, const double *dPinf_, const double *t, long n, double *F_,
+                           double *Q_, double *dF_, double *dQ_) {
+  if (d < 1 || d > DMAX || n < 1) return 3;
+  for (long k = 1; k < n; ++k)
+    if (!(t[k] >= t[k - 1])) return 2;
+  real G[DMAX * DMAX], W[DMAX * DMAX], dG[DMAX * DMAX], dW[DMAX * DMAX];
+  load(d, d, G_, G); load(d, d, W_, W); load(d, d, dG_, dG); load(d, d, dW_, dW);
+  int dd = d * d;
+  for (int i = 0; i < dd; ++i) { F_[i] = 0.0; Q_[i] = Pinf_[i]; dF_[i] = 0.0; dQ_[i] = dPinf_[i]; }
+#pragma omp parallel for schedule(static)
+  for (long k = 1; k < n; ++k) {
+    real F[DMAX * DMAX], Q[DMAX * DMAX], dF[DMAX * DMAX], dQ[DMAX * DMAX];
+    discretize_tangent_one(d, G, W, dG, dW, (real)t[k] - (real)t[k - 1], F, Q, dF, dQ);
+    store(d, d, F, F_ + k * dd); store(d, d, Q, Q_ + k * dd);
+    store(d, d, dF, dF_ + k * dd); store(d, d, dQ, dQ_ + k * dd);
+  }
+  return 0;
+}
+
+/* The sequential Kalman filter of orc_kalman_filter carried with one
+ * tangent direction: given per-step F, Q and their tangents dF, dQ (step 0:
+ * F = 0, Q = P_inf, dQ = dP_inf) and the noise tangent dR (scalar, or per
+ * step with R_per_step), returns the log-likelihood and its directional
+ * derivative.  Differentiating each line of the filter:
+ *   m^- = F m                 dm^- = dF m + F dm
+ *   P^- = F P F^T + Q         dP^- = dF P F^T + F dP F^T + F P dF^T + dQ
+ *   S = H P^- H^T + R         dS = H dP^- H^T + dR
+ *   v = y - H m^-             dv = -H dm^-
+ *   K = P^- H^T / S           dK = (dP^- H^T - K dS) / S
+ *   m = m^- + K v             dm = dm^- + dK v + K dv
+ *   P = P^- - K S K^T         dP = dP^- - dK S K^T - K dS K^T - K S dK^T
+ *   l += -1/2 [log(2 pi S) + v^2 / S]
+ *                             dl += -1/2 [dS / S + 2 v dv / S - v^2 dS / S^2] */
+int orc_loglik_tangent(int d, const double *H_, const double *R, const double *dR, int R_per_step,
+                       const double *F_, const double *Q_, const double *dF_, const double *dQ_,
+                       const double *y, const unsigned char *mask, long n, double *loglik, double *dloglik) {
+  if (d < 1 || d > DMAX || n < 1) return 3;
+  const real twopi = 6.283185307179586476925286766559L;
+  int dd = d * d;
+  real H[DMAX];
+  load(1, d, H_, H);
+  real m[DMAX] = {0}, P[DMAX * DMAX] = {0}, dm[DMAX] = {0}, dP[DMAX * DMAX] = {0};
+  real ll = 0.0L, dll = 0.0L;
+  for (long k = 0; k < n; ++k) {
+    real F[DMAX * DMAX], Q[DMAX * DMAX], dF[DMAX * DMAX], dQ[DMAX * DMAX], Ft[DMAX * DMAX], dFt[DMAX * DMAX];
+    load(d, d, F_ + k * dd, F); load(d, d, Q_ + k * dd, Q);
+    load(d, d, dF_ + k * dd, dF); load(d, d, dQ_ + k * dd, dQ);
+    tr(d, d, F, Ft);
+    tr(d, d, dF, dFt);
+    real mp[DMAX], dmp[DMAX], Pp[DMAX * DMAX], dPp[DMAX * DMAX], T[DMAX * DMAX], A[DMAX * DMAX];
+    real t1[DMAX], t2[DMAX];
+    mm(d, d, 1, F, m, mp);
+    mm(d, d, 1, dF, m, t1);
+    mm(d, d, 1, F, dm, t2);
+    for (int i = 0; i < d; ++i) dmp[i] = t1[i] + t2[i];
+    mm(d, d, d, F, P, T); mm(d, d, d, T, Ft, Pp);
+    for (int i = 0; i < dd; ++i) Pp[i] += Q[i];
+    for (int i = 0; i < dd; ++i) dPp[i] = dQ[i];
+    mm(d, d, d, dF, P, T); mm(d, d, d, T, Ft, A);
+    for (int i = 0; i < dd; ++i) dPp[i] += A[i];
+    mm(d, d, d, F, dP, T); mm(d, d, d, T, Ft, A);
+    for (int i = 0; i < dd; ++i) dPp[i] += A[i];
+    mm(d, d, d, F, P, T); mm(d, d, d, T, dFt, A);
+    for (int i = 0; i < dd; ++i) dPp[i] += A[i];
+    symmetrize(d, Pp);
+    symmetrize(d, dPp);
+    if (mask[k]) {
+      real Rk = (real)(R_per_step ? R[k] : R[0]);
+      real dRk = (real)(R_per_step ? dR[k] : dR[0]);
+      real PH[DMAX], dPH[DMAX];
+      for (int i = 0; i < d; ++i) {
+        real s = 0.0L, ds = 0.0L;
+        for (int j = 0; j < d; ++j) { s += Pp[i * d + j] * H[j]; ds += dPp[i * d + j] * H[j]; }
+        PH[i] = s; dPH[i] = ds;
+      }
+      real S = Rk, dS = dRk;
+      for (int i = 0; i < d; ++i) { S += H[i] * PH[i]; dS += H[i] * dPH[i]; }
+      if (!(S > 0.0L)) return 1;
+      real v = (real)y[k], dv = 0.0L;
+      for (int i = 0; i < d; ++i) { v -= H[i] * mp[i]; dv -= H[i] * dmp[i]; }
+      real K[DMAX], dK[DMAX];
+      for (int i = 0; i < d; ++i) { K[i] = PH[i] / S; dK[i] = (dPH[i] - K[i] * dS) / S; }
+      for (int i = 0; i < d; ++i) {
+        m[i] = mp[i] + K[i] * v;
+        dm[i] = dmp[i] + dK[i] * v + K[i] * dv;
+      }
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+          P[i * d + j] = Pp[i * d + j] - K[i] * S * K[j];
+          dP[i * d + j] = dPp[i * d + j] - dK[i] * S * K[j] - K[i] * dS * K[j] - K[i] * S * dK[j];
+        }
+      symmetrize(d, P);
+      symmetrize(d, dP);
+      ll += -0.5L * (logl(twopi * S) + v * v / S);
+      dll += -0.5L * (dS / S + 2.0L * v * dv / S - v * v * dS / (S * S));
+    } else {
+      memcpy(m, mp, sizeof(real) * d); memcpy(dm, dmp, sizeof(real) * d);
+      memcpy(P, Pp, sizeof(real) * dd); memcpy(dP, dPp, sizeof(real) * dd);
+    }
+  }
+  if (loglik) *loglik = (double)ll;
+  if (dloglik) *dloglik = (double)dll;
+  return 0;
+}
