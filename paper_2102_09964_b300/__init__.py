@@ -78,6 +78,11 @@ def lib():
         L.pssgp_smooth.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, i64, i64, vp, vp, vp, vp, vp, sz, vp]
         L.pssgp_loglik.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, vp, sz, vp]
         L.pssgp_loglik_batched.argtypes = [ctypes.POINTER(PssgpModel), vp, i32, vp, vp, vp, vp, i64, vp, vp, sz, vp]
+        L.pssgp_workspace_size_grad.restype = sz
+        L.pssgp_workspace_size_grad.argtypes = [i32, i64]
+        L.pssgp_loglik_grad.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, vp, vp, sz, vp]
+        L.pssgp_loglik_grad_batched.argtypes = [ctypes.POINTER(PssgpModel), vp, i32, vp, vp, vp, vp, i64, vp, vp,
+                                                vp, sz, vp]
         L.pssgp_predict.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, i64, vp, i64, dp, vp, vp, vp, vp, sz, vp]
         L.pssgp_debug_filter_aggregates.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i64, i32,
                                                     vp, vp, ctypes.POINTER(i32), vp, sz, vp]
@@ -163,6 +168,11 @@ def workspace(d: int, n: int, device="cuda", extra: int = 0) -> torch.Tensor:
     """A device workspace of the size the library asks for (torch allocations
     are 256-byte aligned)."""
     return torch.empty(workspace_size(d, n) + int(extra), dtype=torch.uint8, device=device)
+
+
+def workspace_grad(d: int, n: int, device="cuda") -> torch.Tensor:
+    """A device workspace for the gradient entry points."""
+    return torch.empty(int(lib().pssgp_workspace_size_grad(int(d), int(n))), dtype=torch.uint8, device=device)
 
 
 def status(ws: torch.Tensor) -> int:
@@ -266,6 +276,72 @@ def loglik_batched(model: Model, offsets, params, t, y, mask, ws=None, out=None)
                                     _ptr(mask), n, _ptr(ll), _ptr(ws), ws.numel(), _stream())
     _check(rc, "pssgp_loglik_batched")
     return ll, ws
+
+
+def loglik_grad(model: Model, t, y, mask, R, ws=None):
+    """Log-likelihood of one series and its gradient with respect to
+    (log lengthscale, log variance, log noise variance) by the adjoint scans.
+    R: scalar or per step (the noise derivative scales every R_k).
+    Returns (loglik[1], grad[3], ws)."""
+    d, n = model.d, t.numel()
+    dev = t.device
+    R = _f64(R, dev).reshape(-1)
+    per = 1 if R.numel() == n and n > 1 else 0
+    ws = ws if ws is not None else workspace_grad(d, n, dev)
+    ll = torch.empty(1, dtype=torch.float64, device=dev)
+    g = torch.empty(3, dtype=torch.float64, device=dev)
+    rc = lib().pssgp_loglik_grad(ctypes.byref(model.raw), _ptr(t), _ptr(y), _ptr(mask), _ptr(R), per, n, _ptr(ll),
+                                 _ptr(g), _ptr(ws), ws.numel(), _stream())
+    _check(rc, "pssgp_loglik_grad")
+    return ll, g, ws
+
+
+def loglik_grad_batched(model: Model, offsets, params, t, y, mask, ws=None, out=None):
+    """Log-likelihoods of B series and their gradients with respect to each
+    series' (log lengthscale, log variance, log noise variance).  Arguments
+    as loglik_batched.  Returns (loglik[B], grad[B, 3], ws)."""
+    d, n = model.d, t.numel()
+    dev = t.device
+    B = offsets.numel() - 1
+    if offsets.dtype != torch.int64 or not offsets.is_contiguous():
+        raise TypeError("offsets must be a contiguous int64 tensor")
+    params = _f64(params, dev).reshape(-1)
+    if params.numel() != 3 * B:
+        raise ValueError("params must hold 3 values per series")
+    ws = ws if ws is not None else workspace_grad(d, n, dev)
+    if out is None:
+        out = (torch.empty(B, dtype=torch.float64, device=dev), torch.empty(B, 3, dtype=torch.float64, device=dev))
+    ll, g = out
+    rc = lib().pssgp_loglik_grad_batched(ctypes.byref(model.raw), _ptr(offsets), B, _ptr(params), _ptr(t), _ptr(y),
+                                         _ptr(mask), n, _ptr(ll), _ptr(g), _ptr(ws), ws.numel(), _stream())
+    _check(rc, "pssgp_loglik_grad_batched")
+    return ll, g, ws
+
+
+class BatchedLogLik(torch.autograd.Function):
+    """ll[B] = log marginal likelihoods of B series as a function of their
+    log hyperparameters theta[B, 3] = (log lengthscale, log variance,
+    log noise variance); the backward pass is the adjoint scans' gradient
+    (computed together with the forward values in one library call)."""
+
+    @staticmethod
+    def forward(ctx, theta, model, offsets, t, y, mask, ws):
+        params = torch.exp(theta.detach()).contiguous()
+        ll, g, _ = loglik_grad_batched(model, offsets, params, t, y, mask, ws=ws)
+        ctx.save_for_backward(g)
+        return ll
+
+    @staticmethod
+    def backward(ctx, gout):
+        (g,) = ctx.saved_tensors
+        return gout[:, None] * g, None, None, None, None, None, None
+
+
+def batched_loglik(theta, model: Model, offsets, t, y, mask, ws=None):
+    """Differentiable batched log-likelihood (see BatchedLogLik)."""
+    if ws is None:
+        ws = workspace_grad(model.d, t.numel(), t.device)
+    return BatchedLogLik.apply(theta, model, offsets, t, y, mask, ws)
 
 
 def predict(model: Model, t_train, y_train, t_test, R: float, ws=None, out=None, with_loglik=True):

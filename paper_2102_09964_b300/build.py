@@ -11,8 +11,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SOURCES = [os.path.join(HERE, "csrc", "pssgp_kernels.cu"), os.path.join(HERE, "csrc", "pssgp_model.cpp")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("linalg.cuh", "scan_ops.cuh", "warp_ops.cuh")] + \
-    [os.path.join(ROOT, "include", "pssgp.h")]
+DEPS = SOURCES + sorted(os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc"))
+                        if f.endswith(".cuh")) + [os.path.join(ROOT, "include", "pssgp.h")]
 LIB = os.path.join(HERE, "libpssgp.so")
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "../../include/pssgp.h"
+#include "adjoint_ops.cuh"
 #include "scan_ops.cuh"
 #include "warp_ops.cuh"
 
@@ -66,8 +67,10 @@ int num_sms() {
 constexpr int TIMING_SLOTS = 16;
 const char* const kTimingNames[TIMING_SLOTS] = {
     "merge", "filter_reduce", "filter_level2", "filter_propagate", "smoother_level2", "smoother_propagate",
-    "smoother_elements", "gather", "loglik_reduce", "discretize", "", "", "", "", "", ""};
-enum { T_MERGE = 0, T_FRED, T_FL2, T_FPROP, T_SL2, T_SPROP, T_SELEM, T_GATHER, T_LL, T_DISC };
+    "smoother_elements", "gather", "loglik_reduce", "discretize", "adjoint_level2", "adjoint_mean",
+    "adjoint_cov", "", "", ""};
+enum { T_MERGE = 0, T_FRED, T_FL2, T_FPROP, T_SL2, T_SPROP, T_SELEM, T_GATHER, T_LL, T_DISC, T_AL2, T_AMEAN,
+       T_ACOV };
 bool g_timing = false;
 struct TimingRec { cudaEvent_t a, b; int slot; };
 std::vector<TimingRec> g_pending;
@@ -121,7 +124,7 @@ struct Plan {
   int fqs, egs;      // per-step record strides (doubles, even)
   // byte offsets into the workspace
   int64_t o_status, o_fq, o_egl, o_laggf, o_waggf, o_laggs, o_waggs, o_llp, o_fmean, o_fvar, o_t, o_y, o_mask,
-      o_tpos, o_rstep, o_seg, o_llstep, total;
+      o_tpos, o_rstep, o_seg, o_llstep, o_adj, o_tauq, o_lpi, o_lmbar, o_gpart, o_gstep, total;
 };
 
 int warps_for(int d) {
@@ -130,7 +133,7 @@ int warps_for(int d) {
 }
 
 // warps: lanes per SM / 32 (0: the current tuning for d)
-Plan make_plan(int d, int64_t n, int64_t lanes_req, int warps = 0) {
+Plan make_plan(int d, int64_t n, int64_t lanes_req, int warps = 0, bool grad = false) {
   Plan p{};
   p.d = d;
   p.n = n;
@@ -165,6 +168,16 @@ Plan make_plan(int d, int64_t n, int64_t lanes_req, int warps = 0) {
   p.o_rstep = o; o += align256(n * 8);     // batched: noise variance per step
   p.o_seg = o; o += align256(n);           // batched: 1 at each series' first step
   p.o_llstep = o; o += align256(n * 8);    // batched: log-likelihood pieces per step
+  p.o_adj = p.o_tauq = p.o_lpi = p.o_lmbar = p.o_gpart = p.o_gstep = -1;
+  if (grad) {                                // gradient: forward moments, scan state
+    const int adjs = (d + sym + 2 + 1) / 2 * 2;
+    p.o_adj = o; o += align256(n * adjs * 8);
+    p.o_tauq = o; o += align256(n * 16);       // (tau, q) per step
+    p.o_lpi = o; o += align256(P0 * d * d * 8);
+    p.o_lmbar = o; o += align256(P0 * d * 8);
+    p.o_gpart = o; o += align256(3 * P0 * 8);
+    p.o_gstep = o; o += align256(3 * n * 8);
+  }
   p.total = o;
   return p;
 }
@@ -201,6 +214,17 @@ struct ScanArgs {
   double* dbg_agg;       // optional: level-0 lane aggregates (tests)
   const uint8_t* seg_start;  // batched: series starts (null for one series)
   double* ll_step;           // batched: per-step log-likelihood pieces
+  // gradient (adjoint) mode
+  int adj;                   // 1: the filter pass stores rec_adj and folds the mean-adjoint aggregate
+  double* rec_adj;           // [n][adjs] predicted moments, v, 1/S
+  double* tauq;              // [n][2] scaled step tau and variance ratio q
+  double* lane_pi;           // [D*D][P0] raw chunk product of the mean-adjoint factors
+  double* lane_mbar;         // [D][P0] mean adjoint at the chunk end
+  double* gpart;             // [3][P0] gradient partials per lane
+  double* g_step;            // batched: [3][n] gradient pieces per step
+  double* lagg_a;            // [ns][P0] covariance-adjoint lane aggregates
+  double* wagg_a;            // [2][ns][P2] and their warp aggregates
+  const double* wfin_a;
 };
 
 __device__ __forceinline__ void flag(int* status, int bits) {
@@ -274,7 +298,7 @@ __device__ __forceinline__ void load_egl(const double* rec, int64_t k, SAgg<D>& 
 constexpr int DISC_BLOCK = 128;
 template <int D>
 __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_rec(const DevModel<D> m, const double* t, int64_t n,
-                                                             double* rec, int* status) {
+                                                             double* rec, double* tauq, int* status) {
   constexpr int FQS = fqs_of<D>();
   extern __shared__ double stage[];           // DISC_BLOCK * FQS doubles
   const int64_t k0 = (int64_t)blockIdx.x * DISC_BLOCK;
@@ -294,6 +318,7 @@ __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_rec(const DevModel<D>
   Mat<D> F, Q;
   discretize<D>(m, h, first, act, F, Q);
   store_fq<D>(stage, threadIdx.x, F, Q);     // record threadIdx.x of the block
+  if (tauq && act) { tauq[2 * k] = h; tauq[2 * k + 1] = 1.0; }
   __syncthreads();
   const int64_t nrec = min((int64_t)DISC_BLOCK, n - k0);
   double* dst = rec + k0 * FQS;
@@ -310,7 +335,8 @@ template <int D>
 __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_batched(const DevModel<D> m, double ell0, double var0,
                                                                  const int64_t* offsets, int B, const double* params,
                                                                  const double* t, int64_t n, double* rec,
-                                                                 double* Rstep, uint8_t* seg, int* status) {
+                                                                 double* Rstep, uint8_t* seg, double* tauq,
+                                                                 int* status) {
   constexpr int FQS = fqs_of<D>();
   extern __shared__ double stage[];
   const int64_t k0 = (int64_t)blockIdx.x * DISC_BLOCK;
@@ -350,6 +376,7 @@ __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_batched(const DevMode
   if (act) {
     Rstep[k] = R;
     seg[k] = first ? 1 : 0;
+    if (tauq) { tauq[2 * k] = first ? 0.0 : h * uscale; tauq[2 * k + 1] = qscale; }
   }
   __syncthreads();
   const int64_t nrec = min((int64_t)DISC_BLOCK, n - k0);
@@ -360,7 +387,7 @@ __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_batched(const DevMode
 
 // one warp per series: fixed-order sum of the per-step log-likelihood pieces
 __global__ void __launch_bounds__(BLOCK) k_segment_sum(const double* v, int64_t n, const int64_t* offsets, int B,
-                                                           double* out) {
+                                                           double* out, int ostride) {
   const int s = (int)((int64_t)blockIdx.x * (BLOCK / 32) + (threadIdx.x >> 5));
   const int lane = threadIdx.x & 31;
   if (s >= B) return;
@@ -370,7 +397,7 @@ __global__ void __launch_bounds__(BLOCK) k_segment_sum(const double* v, int64_t 
   for (int64_t k = a + lane; k < b; k += 32) acc += v[k];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) out[s] = acc;
+  if (lane == 0) out[(int64_t)s * ostride] = acc;
 }
 
 // shared memory of k_filter_reduce: A (two buffers), J (packed) and eta per
@@ -589,6 +616,14 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
       if (k == k0) fixed_point_start_smem<D, BLOCK>(sSig, sV, smu, x, P);
       else fixed_point_step_smem<D, BLOCK>(sSig, sV, smu, F, obs, Pm, Si, v);
     }
+    if (a.adj) {  // gradient: forward moments and the mean-adjoint chunk product
+      store_adj<D>(a.rec_adj, k, xm, Pm, v, Si);
+      Vec<D> Kv;
+#pragma unroll
+      for (int i = 0; i < D; ++i) Kv[i] = Pm[i][0] * Si;     // 0 on missing steps
+      if (k == k0) adj_fold_start<D, BLOCK>(sSig, smu);
+      adj_fold_step<D, BLOCK>(sSig, smu, F, k > k0, Kv, v * Si);
+    }
     if (a.xf) {
 #pragma unroll
       for (int i = 0; i < D; ++i) a.xf[i * a.ld + k] = x[i] * m.Dsc[i];
@@ -602,7 +637,44 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
   }
   a.llp[g] = ll_piece(nobs, lp, qsum);
   if (a.ll_step && k1 > k0) a.ll_step[lpos] = a.llp[g];
-  if (fuse) {
+  if (a.adj) {
+    SAgg<D> sa;
+    if (k1 > k0) {
+      // last factor: the transition into the next chunk's first step (none
+      // after the last step)
+      Mat<D> F1;
+      if (k1 < a.n) load_F<D>(a.rec_fq, k1, fqs_of<D>(), F1);
+      else set_zero<D>(F1);
+      adj_fold_finish<D, BLOCK>(sSig, F1);
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        sa.g[i] = smu[i * BLOCK];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          sa.E[i][j] = sSig[(i * D + j) * BLOCK];
+          a.lane_pi[(i * D + j) * a.P0 + g] = sa.E[i][j];
+          sa.L[i][j] = 0.0;
+        }
+      }
+    } else {
+      sagg_identity<D>(sa);
+#pragma unroll
+      for (int e = 0; e < D * D; ++e) a.lane_pi[e * a.P0 + g] = (e % (D + 1) == 0) ? 1.0 : 0.0;
+    }
+    // level 1 of the mean-adjoint scan: inclusive suffix scan over the warp
+#pragma unroll 1
+    for (int off = 1; off < 32; off <<= 1) {
+      SAgg<D> o = sa;
+      shfl_down_sagg<D>(o, off);
+      if (lane + off < 32) {
+        SAgg<D> r;
+        sagg_combine<D>(sa, o, r);
+        sa = r;
+      }
+    }
+    store_sagg<D>(a.lagg_s + g, a.P0, sa);
+    if (lane == 0) store_sagg<D>(a.wagg_s + w, a.P2, sa);
+  } else if (fuse) {
     SAgg<D> sa;
     if (k1 > k0) {
       // element of the chunk's last step (the transition into the next step,
@@ -814,6 +886,230 @@ __global__ void __launch_bounds__(BLOCK, 1) k_smoother_elements(const DevModel<D
 }
 
 // deterministic sum of the per-lane log-likelihood partials (fixed order)
+// ---------------------------------------------------------------------------
+// gradient (adjoint) levels 3 and 0/1, see adjoint_ops.cuh
+// ---------------------------------------------------------------------------
+template <int D> constexpr int adjoint_smem_doubles() { return Sym<D>::N * BLOCK; }
+
+// mean-adjoint level 3 (backward through the chunk from the exclusive suffix)
+// fused with the covariance-adjoint levels 0/1 (backward Horner of
+// Mb <- E_k Mb E_k^T + B_k from zero, then a warp suffix scan)
+template <int D>
+__global__ void __launch_bounds__(BLOCK, 1) k_adjoint_mean(const DevModel<D> m, const ScanArgs a) {
+  extern __shared__ double adsm[];
+  double* sL = adsm + threadIdx.x;
+  const int64_t g = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t w = g >> 5;
+  const int64_t k0 = g * a.L;
+  const int64_t k1 = min(k0 + a.L, a.n);
+  Vec<D> mb;
+#pragma unroll
+  for (int i = 0; i < D; ++i) mb[i] = 0.0;
+  if (w + 1 < a.P2) {
+    SAgg<D> V;
+    load_sagg<D>(a.wfin_s + (w + 1), a.P2, V);
+#pragma unroll
+    for (int i = 0; i < D; ++i) mb[i] = V.g[i];
+  }
+  if (lane < 31) {
+    SAgg<D> S;
+    load_sagg<D>(a.lagg_s + (g + 1), a.P0, S);
+    Vec<D> t2;
+    mulv_add<D>(S.E, mb, S.g, t2);
+#pragma unroll
+    for (int i = 0; i < D; ++i) mb[i] = t2[i];
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) a.lane_mbar[i * a.P0 + g] = mb[i];
+#pragma unroll
+  for (int e = 0; e < Sym<D>::N; ++e) sL[e * BLOCK] = 0.0;
+#pragma unroll 1
+  for (int64_t k = k1 - 1; k >= k0; --k) {
+    Mat<D> F1;
+    if (k + 1 < a.n) load_F<D>(a.rec_fq, k + 1, fqs_of<D>(), F1);
+    else set_zero<D>(F1);
+    Vec<D> xb, xm, c0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) s = fma(F1[j][i], mb[j], s);
+      xb[i] = s;
+    }
+    double v, Si;
+    load_adj_col0<D>(a.rec_adj, k, xm, c0, v, Si);
+    Vec<D> K;
+    double kx = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) { K[i] = c0[i] * Si; kx = fma(K[i], xb[i], kx); }
+    const double vSi = v * Si;
+    const double c = -0.5 * fma(-vSi, vSi, Si);
+    adj_cov_step<D, BLOCK>(sL, F1, K, vSi, c, xb, kx);
+#pragma unroll
+    for (int i = 0; i < D; ++i) mb[i] = xb[i];
+    mb[0] += vSi - kx;
+  }
+  SAgg<D> sa;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    sa.g[i] = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) sa.E[i][j] = a.lane_pi[(i * D + j) * a.P0 + g];
+#pragma unroll
+    for (int j = i; j < D; ++j) { sa.L[i][j] = sL[pidx<D>(i, j) * BLOCK]; sa.L[j][i] = sa.L[i][j]; }
+  }
+#pragma unroll 1
+  for (int off = 1; off < 32; off <<= 1) {
+    SAgg<D> o = sa;
+    shfl_down_sagg<D>(o, off);
+    if (lane + off < 32) {
+      SAgg<D> r;
+      sagg_combine<D>(sa, o, r);
+      sa = r;
+    }
+  }
+  store_sagg<D>(a.lagg_a + g, a.P0, sa);
+  if (lane == 0) store_sagg<D>(a.wagg_a + w, a.P2, sa);
+}
+
+// covariance-adjoint level 3 with the gradient accumulation; per lane (or,
+// batched, per series piece) partial sums of the three derivatives
+template <int D>
+__global__ void __launch_bounds__(BLOCK, 1) k_adjoint_cov(const DevModel<D> m, const ScanArgs a) {
+  extern __shared__ double adsm[];
+  double* sM = adsm + threadIdx.x;
+  const int64_t g = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t w = g >> 5;
+  const int64_t k0 = g * a.L;
+  const int64_t k1 = min(k0 + a.L, a.n);
+  {
+    Mat<D> Mb;
+    set_zero<D>(Mb);
+    if (w + 1 < a.P2) {
+      SAgg<D> V;
+      load_sagg<D>(a.wfin_a + (w + 1), a.P2, V);
+      copy<D>(V.L, Mb);
+    }
+    if (lane < 31) {
+      SAgg<D> S;
+      load_sagg<D>(a.lagg_a + (g + 1), a.P0, S);
+      Mat<D> T, M2;
+      mul<D>(S.E, Mb, T);
+      mul_Bt_sym_add<D>(T, S.E, S.L, M2);
+      copy<D>(M2, Mb);
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = i; j < D; ++j) sM[pidx<D>(i, j) * BLOCK] = Mb[i][j];
+  }
+  Vec<D> mb;
+#pragma unroll
+  for (int i = 0; i < D; ++i) mb[i] = a.lane_mbar[i * a.P0 + g];
+  const double R0 = a.R[0];
+  double gl = 0.0, gs = 0.0, gr = 0.0;
+#pragma unroll 1
+  for (int64_t k = k1 - 1; k >= k0; --k) {
+    Vec<D> xb, xm, c0, K;
+    double v, Si, kx = 0.0, kPk;
+    {
+      Mat<D> F1;
+      if (k + 1 < a.n) load_F<D>(a.rec_fq, k + 1, fqs_of<D>(), F1);
+      else set_zero<D>(F1);
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) s = fma(F1[j][i], mb[j], s);
+        xb[i] = s;
+      }
+      load_adj_col0<D>(a.rec_adj, k, xm, c0, v, Si);
+#pragma unroll
+      for (int i = 0; i < D; ++i) { K[i] = c0[i] * Si; kx = fma(K[i], xb[i], kx); }
+      const double vSi0 = v * Si;
+      kPk = adj_cov_step<D, BLOCK>(sM, F1, K, vSi0, -0.5 * fma(-vSi0, vSi0, Si), xb, kx);
+    }
+    const double vSi = v * Si;
+    const double c = -0.5 * fma(-vSi, vSi, Si);
+#pragma unroll
+    for (int i = 0; i < D; ++i) mb[i] = xb[i];
+    mb[0] += vSi - kx;
+    // sM = Mb_k, mb = mb_k: the step's contributions
+    gs += adj_trace_smem_rec<D, BLOCK>(sM, a.rec_fq + k * fqs_of<D>() + D * D);
+    if (Si != 0.0) gr = fma(kPk - vSi * kx + c, a.R_per_step ? a.R[k] : R0, gr);
+    const double tau = a.tauq[2 * k];
+    if (tau != 0.0) {
+      const double q = a.tauq[2 * k + 1];
+      Mat<D> Mk, Mbk;
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = i; j < D; ++j) {
+          Mk[i][j] = load_adj_M<D>(a.rec_adj, k, i, j);
+          Mk[j][i] = Mk[i][j];
+          Mbk[i][j] = sM[pidx<D>(i, j) * BLOCK];
+          Mbk[j][i] = Mbk[i][j];
+        }
+      // t1 = mb^T G m, t2 = tr(Mb G M) = sum_il G_il (M Mb)_li, t3 = tr(Mb W)
+      double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+      if (m.companion) {
+#pragma unroll
+        for (int i = 0; i + 1 < D; ++i) {
+          const double gi = m.fc[i * D + i + 1][1];
+          t1 = fma(mb[i] * gi, xm[i + 1], t1);
+          double s = 0.0;
+#pragma unroll
+          for (int c2 = 0; c2 < D; ++c2) s = fma(Mk[i + 1][c2], Mbk[c2][i], s);
+          t2 = fma(gi, s, t2);
+        }
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+          const double gl_ = m.fc[(D - 1) * D + l][1];
+          t1 = fma(mb[D - 1] * gl_, xm[l], t1);
+          double s = 0.0;
+#pragma unroll
+          for (int c2 = 0; c2 < D; ++c2) s = fma(Mk[l][c2], Mbk[c2][D - 1], s);
+          t2 = fma(gl_, s, t2);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+          for (int l = 0; l < D; ++l) {
+            const double gil = m.fc[i * D + l][1];
+            t1 = fma(mb[i] * gil, xm[l], t1);
+            double s = 0.0;
+#pragma unroll
+            for (int c2 = 0; c2 < D; ++c2) s = fma(Mk[l][c2], Mbk[c2][i], s);
+            t2 = fma(gil, s, t2);
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = i; j < D; ++j) {
+          const double p = Mbk[i][j] * m.qc[pidx<D>(i, j)][0];
+          t3 = (i == j) ? t3 + p : fma(2.0, p, t3);
+        }
+      gl = fma(-tau, fma(2.0, t2, fma(q, t3, t1)), gl);
+    }
+    if (a.g_step) {   // batched: one piece per (chunk, series), at its first step in the chunk
+      const bool flush = (k == k0) || a.seg_start[k];
+      a.g_step[k] = flush ? gl : 0.0;
+      a.g_step[a.n + k] = flush ? gs : 0.0;
+      a.g_step[2 * a.n + k] = flush ? gr : 0.0;
+      if (flush) { gl = 0.0; gs = 0.0; gr = 0.0; }
+    }
+  }
+  if (!a.g_step) {
+    a.gpart[g] = gl;
+    a.gpart[a.P0 + g] = gs;
+    a.gpart[2 * a.P0 + g] = gr;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_loglik_reduce(const double* llp, int64_t P0, double* out) {
   __shared__ double sm[256];
   double s = 0.0;
@@ -978,6 +1274,15 @@ ScanArgs base_args(const Plan& p, void* ws) {
   a.wagg_s = reinterpret_cast<double*>(ws_ptr(ws, p.o_waggs));
   a.llp = reinterpret_cast<double*>(ws_ptr(ws, p.o_llp));
   a.status = reinterpret_cast<int*>(ws_ptr(ws, p.o_status));
+  if (p.o_adj >= 0) {
+    a.rec_adj = reinterpret_cast<double*>(ws_ptr(ws, p.o_adj));
+    a.tauq = reinterpret_cast<double*>(ws_ptr(ws, p.o_tauq));
+    a.lane_pi = reinterpret_cast<double*>(ws_ptr(ws, p.o_lpi));
+    a.lane_mbar = reinterpret_cast<double*>(ws_ptr(ws, p.o_lmbar));
+    a.gpart = reinterpret_cast<double*>(ws_ptr(ws, p.o_gpart));
+    a.lagg_a = a.lagg_f;     // the filter aggregates are dead once the filter pass is done
+    a.wagg_a = a.wagg_f;
+  }
   return a;
 }
 
@@ -1029,12 +1334,13 @@ void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s
     if (!bt) {
       cudaFuncSetAttribute(k_discretize_rec<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem);
       k_discretize_rec<D><<<(unsigned)((p.n + DISC_BLOCK - 1) / DISC_BLOCK), DISC_BLOCK, dsmem, s>>>(
-          m, a.t, p.n, a.rec_fq, a.status);
+          m, a.t, p.n, a.rec_fq, a.tauq, a.status);
     } else {
       cudaFuncSetAttribute(k_discretize_batched<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem);
       const int64_t thr = std::max<int64_t>(p.n, (int64_t)bt->B + 1);
       k_discretize_batched<D><<<(unsigned)((thr + DISC_BLOCK - 1) / DISC_BLOCK), DISC_BLOCK, dsmem, s>>>(
-          m, bt->ell0, bt->var0, bt->offsets, bt->B, bt->params, a.t, p.n, a.rec_fq, bt->Rstep, bt->seg, a.status);
+          m, bt->ell0, bt->var0, bt->offsets, bt->B, bt->params, a.t, p.n, a.rec_fq, bt->Rstep, bt->seg, a.tauq,
+          a.status);
     }
     after_launch();
   }
@@ -1061,6 +1367,52 @@ void run_smoother_tail(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStr
   Timed tm(s, T_SPROP);
   k_smoother_propagate<D><<<grid, BLOCK, 0, s>>>(m, a);
   after_launch();
+}
+
+// gradient: filter pass in adjoint mode, then the two backward scans
+template <int D>
+void run_grad(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s, const BatchArgs* bt) {
+  const int grid = (int)(p.P0 / BLOCK);
+  a.adj = 1;
+  a.fuse_smoother = 0;
+  run_filter<D>(m, p, a, s, bt);
+  {
+    double* in = a.wagg_s;
+    double* out = a.wagg_s + p.P2 * p.ns;
+    const int g2 = (int)((p.P2 + BLOCK / 32 - 1) / (BLOCK / 32));
+    for (int64_t off = 1; off < p.P2; off <<= 1) {
+      Timed tm(s, T_AL2);
+      k_smoother_ks<D><<<g2, BLOCK, 0, s>>>(in, out, p.P2, off);
+      after_launch();
+      std::swap(in, out);
+    }
+    a.wfin_s = in;
+  }
+  constexpr int asmem = adjoint_smem_doubles<D>() * 8;
+  {
+    cudaFuncSetAttribute(k_adjoint_mean<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, asmem);
+    Timed tm(s, T_AMEAN);
+    k_adjoint_mean<D><<<grid, BLOCK, asmem, s>>>(m, a);
+    after_launch();
+  }
+  {
+    double* in = a.wagg_a;
+    double* out = a.wagg_a + p.P2 * p.ns;
+    const int g2 = (int)((p.P2 + BLOCK / 32 - 1) / (BLOCK / 32));
+    for (int64_t off = 1; off < p.P2; off <<= 1) {
+      Timed tm(s, T_AL2);
+      k_smoother_ks<D><<<g2, BLOCK, 0, s>>>(in, out, p.P2, off);
+      after_launch();
+      std::swap(in, out);
+    }
+    a.wfin_a = in;
+  }
+  {
+    cudaFuncSetAttribute(k_adjoint_cov<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, asmem);
+    Timed tm(s, T_ACOV);
+    k_adjoint_cov<D><<<grid, BLOCK, asmem, s>>>(m, a);
+    after_launch();
+  }
 }
 
 int check_ws(const Plan& p, void* ws, size_t ws_bytes) {
@@ -1210,8 +1562,85 @@ extern "C" int pssgp_loglik_batched(const pssgp_model* model, const int64_t* off
   });
   {
     Timed tm(s, T_LL);
-    k_segment_sum<<<(unsigned)((B + BLOCK / 32 - 1) / (BLOCK / 32)), BLOCK, 0, s>>>(a.ll_step, n, offsets, B, loglik);
+    k_segment_sum<<<(unsigned)((B + BLOCK / 32 - 1) / (BLOCK / 32)), BLOCK, 0, s>>>(a.ll_step, n, offsets, B, loglik, 1);
     after_launch();
+  }
+  return end_call();
+}
+
+extern "C" size_t pssgp_workspace_size_grad(int32_t d, int64_t n) {
+  if (d < 1 || d > PSSGP_DMAX || n < 1) return 0;
+  return (size_t)make_plan(d, n, 0, WARPS_MAX, true).total;
+}
+
+extern "C" int pssgp_loglik_grad(const pssgp_model* model, const double* t, const double* y, const uint8_t* mask,
+                                 const double* R, int32_t R_per_step, int64_t n, double* loglik, double* grad,
+                                 void* ws, size_t ws_bytes, void* stream) {
+  begin_call();
+  if (!model_ok(model) || !t || !y || !mask || !R || !grad || n < 1) return PSSGP_EINVAL;
+  const Plan p = make_plan(model->d, n, 0, 0, true);
+  const int rc = check_ws(p, ws, ws_bytes);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScanArgs a = base_args(p, ws);
+  a.t = t; a.y = y; a.mask = mask; a.R = R; a.R_per_step = R_per_step;
+  if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess) return PSSGP_ECUDA;
+  PSSGP_DISPATCH(model->d, {
+    const DevModel<D> m = dev_model<D>(model);
+    run_grad<D>(m, p, a, s, nullptr);
+  });
+  {
+    Timed tm(s, T_LL);
+    if (loglik) {
+      k_loglik_reduce<<<1, 256, 0, s>>>(a.llp, p.P0, loglik);
+      after_launch();
+    }
+    for (int i = 0; i < 3; ++i) {
+      k_loglik_reduce<<<1, 256, 0, s>>>(a.gpart + i * p.P0, p.P0, grad + i);
+      after_launch();
+    }
+  }
+  return end_call();
+}
+
+extern "C" int pssgp_loglik_grad_batched(const pssgp_model* model, const int64_t* offsets, int32_t B,
+                                         const double* params, const double* t, const double* y,
+                                         const uint8_t* mask, int64_t n, double* loglik, double* grad, void* ws,
+                                         size_t ws_bytes, void* stream) {
+  begin_call();
+  if (!model_ok(model) || !offsets || !params || !t || !y || !mask || !grad || B < 1 || n < 1)
+    return PSSGP_EINVAL;
+  const double ell0 = model->lengthscale, var0 = model->variance;
+  if (!(ell0 > 0.0) || !(var0 > 0.0) || !std::isfinite(ell0) || !std::isfinite(var0)) return PSSGP_EMODEL;
+  const Plan p = make_plan(model->d, n, 0, 0, true);
+  const int rc = check_ws(p, ws, ws_bytes);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScanArgs a = base_args(p, ws);
+  BatchArgs bt;
+  bt.ell0 = ell0; bt.var0 = var0; bt.offsets = offsets; bt.B = B; bt.params = params;
+  bt.Rstep = reinterpret_cast<double*>(ws_ptr(ws, p.o_rstep));
+  bt.seg = reinterpret_cast<uint8_t*>(ws_ptr(ws, p.o_seg));
+  a.t = t; a.y = y; a.mask = mask; a.R = bt.Rstep; a.R_per_step = 1;
+  a.seg_start = bt.seg;
+  a.ll_step = reinterpret_cast<double*>(ws_ptr(ws, p.o_llstep));
+  a.g_step = reinterpret_cast<double*>(ws_ptr(ws, p.o_gstep));
+  if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess) return PSSGP_ECUDA;
+  PSSGP_DISPATCH(model->d, {
+    const DevModel<D> m = dev_model<D>(model);
+    run_grad<D>(m, p, a, s, &bt);
+  });
+  {
+    Timed tm(s, T_LL);
+    const unsigned sg = (unsigned)((B + BLOCK / 32 - 1) / (BLOCK / 32));
+    if (loglik) {
+      k_segment_sum<<<sg, BLOCK, 0, s>>>(a.ll_step, n, offsets, B, loglik, 1);
+      after_launch();
+    }
+    for (int i = 0; i < 3; ++i) {
+      k_segment_sum<<<sg, BLOCK, 0, s>>>(a.g_step + i * n, n, offsets, B, grad + i, 3);
+      after_launch();
+    }
   }
   return end_call();
 }

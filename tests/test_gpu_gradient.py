@@ -1,0 +1,180 @@
+"""GPU parity of the adjoint gradient of the log marginal likelihood with
+respect to (log lengthscale, log variance, log noise variance) against the
+oracle's forward-mode gradient (and, at the full 2^20-step size, against
+central differences of the oracle's log-likelihood).
+
+Tolerance semantics: |dg| <= tol * max(|g|, n_obs) per component, tol 1e-9
+for Matern kernels and 1e-6 for the order-6 RBF Taylor model (the same
+scale as the log-likelihood's own tolerance: both are sums of n_obs terms).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2102_09964_b300 as P
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"matern12": 1e-9, "matern32": 1e-9, "matern52": 1e-9, "rbf": 1e-6}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2102_09964_b300 import build
+    build.build()
+    P.lib()
+    oracle.build()
+
+
+def dev(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def check_grad(g, ref, nobs, tol, what=""):
+    err = np.max(np.abs(np.asarray(g) - ref) / np.maximum(np.abs(ref), max(nobs, 1)))
+    assert err <= tol, (what, g, ref, err)
+    return err
+
+
+def gpu_grad(kind, ell, s2, t, y, mask, R):
+    m = P.build_model(kind, ell, s2)
+    ll, g, ws = P.loglik_grad(m, dev(t), dev(y), dev(mask, torch.uint8), R)
+    return float(ll.item()), g.cpu().numpy(), P.status(ws)
+
+
+@pytest.mark.parametrize("kind", ["matern12", "matern32", "matern52", "rbf"])
+@pytest.mark.parametrize("n", [1, 2, 37, 3000, 40_001])
+def test_grad_matches_forward_mode(kind, n):
+    s = wl.random_series(31, max(n, 1), 0, T=n * 0.01 + 0.01)
+    t, y = s.t_train, s.y_train
+    rng = np.random.default_rng(32)
+    mask = (rng.uniform(size=n) > 0.1).astype(np.uint8)
+    ll, g, st = gpu_grad(kind, 0.7, 1.3, t, y, mask, 0.02)
+    assert st == 0
+    rll, rg = oracle.loglik_grad_fwd(kind, 0.7, 1.3, t, y, mask, 0.02)
+    nobs = int(mask.sum())
+    assert abs(ll - rll) <= TOL[kind] * max(abs(rll), nobs, 1)
+    check_grad(g, rg, nobs, TOL[kind], f"{kind}/{n}")
+
+
+@pytest.mark.parametrize("kind", ["matern32", "matern52", "rbf"])
+def test_grad_long_gaps_ties_missing_runs(kind):
+    s = wl.random_series(33, 6000, 0, T=60.0)
+    t, y = s.t_train.copy(), s.y_train
+    t[1000:] += 50.0                        # long step: halving/doubling path
+    t[2000:2010] = t[2000]                  # ties (zero-length steps)
+    t = np.maximum.accumulate(t)
+    mask = np.ones(t.size, np.uint8)
+    mask[3000:3500] = 0                     # a run of missing steps
+    ll, g, st = gpu_grad(kind, 1.1, 0.9, t, y, mask, 0.05)
+    assert st == 0
+    rll, rg = oracle.loglik_grad_fwd(kind, 1.1, 0.9, t, y, mask, 0.05)
+    check_grad(g, rg, int(mask.sum()), TOL[kind], kind)
+
+
+def test_grad_per_step_noise():
+    s = wl.random_series(34, 5000, 0, T=50.0)
+    R = np.exp(np.random.default_rng(35).uniform(np.log(1e-3), np.log(1e-1), 5000))
+    mask = np.ones(5000, np.uint8)
+    m = P.build_model("matern52", 0.8, 1.0)
+    ll, g, ws = P.loglik_grad(m, dev(s.t_train), dev(s.y_train), dev(mask, torch.uint8), dev(R))
+    assert P.status(ws) == 0
+    rll, rg = oracle.loglik_grad_fwd("matern52", 0.8, 1.0, s.t_train, s.y_train, mask, R)
+    check_grad(g.cpu().numpy(), rg, 5000, 1e-9)
+
+
+def test_grad_all_missing_is_zero():
+    t = np.linspace(0.0, 10.0, 3000)
+    ll, g, st = gpu_grad("matern32", 1.0, 1.0, t, np.zeros(3000), np.zeros(3000, np.uint8), 0.01)
+    assert st == 0 and ll == 0.0 and np.all(np.abs(g) <= 1e-12)
+
+
+@pytest.mark.parametrize("kind", ["matern32", "matern52", "rbf"])
+def test_batched_grad_matches_forward_mode(kind):
+    bt = wl.series_batch(seed=36, lengths=[0, 1, 2, 31, 33, 500, 4099, 0, 12_345, 3, 20_000])
+    m = P.build_model(kind, 1.0, 1.0)
+    mask = np.ones(bt.t.size, np.uint8)
+    ll, g, ws = P.loglik_grad_batched(m, dev(bt.offsets, torch.int64), dev(bt.params()), dev(bt.t), dev(bt.y),
+                                      dev(mask, torch.uint8))
+    assert P.status(ws) == 0
+    ll, g = ll.cpu().numpy(), g.cpu().numpy()
+    for s in range(bt.B):
+        a, b = bt.offsets[s], bt.offsets[s + 1]
+        if b == a:
+            assert ll[s] == 0.0 and np.all(g[s] == 0.0)
+            continue
+        rll, rg = oracle.loglik_grad_fwd(kind, bt.lengthscale[s], bt.variance[s], bt.t[a:b], bt.y[a:b],
+                                         mask[a:b], bt.noise[s])
+        assert abs(ll[s] - rll) <= TOL[kind] * max(abs(rll), b - a)
+        check_grad(g[s], rg, b - a, TOL[kind], (kind, s))
+
+
+def test_batched_grad_full_size_sampled():
+    """The 4,096-series workload, one call per family; sampled series against
+    the oracle's forward-mode gradient."""
+    bt = wl.series_batch(**wl.BATCH)
+    kinds = np.array(bt.kind)
+    lens = np.diff(bt.offsets)
+    rng = np.random.default_rng(37)
+    for kind in ("matern32", "matern52"):
+        idx = np.flatnonzero(kinds == kind)
+        sub = wl.subset(bt, idx)
+        m = P.build_model(kind, 1.0, 1.0)
+        ll, g, ws = P.loglik_grad_batched(m, dev(sub.offsets, torch.int64), dev(sub.params()), dev(sub.t),
+                                          dev(sub.y), torch.ones(sub.t.size, dtype=torch.uint8, device="cuda"))
+        assert P.status(ws) == 0
+        ll, g = ll.cpu().numpy(), g.cpu().numpy()
+        assert np.all(np.isfinite(g))
+        sl = lens[idx]
+        pick = sorted({int(np.argmin(sl)), int(np.argmax(sl)), *rng.choice(idx.size, 2, replace=False).tolist()})
+        for s in pick:
+            a, b = sub.offsets[s], sub.offsets[s + 1]
+            rll, rg = oracle.loglik_grad_fwd(kind, sub.lengthscale[s], 1.0, sub.t[a:b], sub.y[a:b],
+                                             np.ones(b - a, np.uint8), sub.noise[s])
+            check_grad(g[s], rg, b - a, TOL[kind], (kind, s))
+
+
+def test_grad_full_size_rbf_vs_central_differences():
+    """RBF-6 on the 2^20 training points, in the launch configuration of the
+    benchmark, against central differences (h = 1e-6) of the oracle."""
+    s = wl.sinusoid_large()
+    t, y = s.t_train, s.y_train
+    mask = np.ones(t.size, np.uint8)
+    ll, g, st = gpu_grad("rbf", 1.0, 1.0, t, y, mask, 0.01)
+    assert st == 0
+    gfd = oracle.loglik_grad_fd("rbf", 1.0, 1.0, t, y, mask, 0.01)
+    check_grad(g, gfd, t.size, 1e-6, "rbf 2^20")
+
+
+def test_autograd_function_and_a_descent_step():
+    bt = wl.series_batch(seed=38, lengths=[3000, 800, 15_000])
+    m = P.build_model("matern52", 1.0, 1.0)
+    off, t, y = dev(bt.offsets, torch.int64), dev(bt.t), dev(bt.y)
+    mask = torch.ones(bt.t.size, dtype=torch.uint8, device="cuda")
+    theta = torch.log(dev(bt.params())).requires_grad_(True)
+    ll = P.batched_loglik(theta, m, off, t, y, mask)
+    ll.sum().backward()
+    _, g, _ = P.loglik_grad_batched(m, off, torch.exp(theta.detach()), t, y, mask)
+    assert torch.equal(theta.grad, g)
+    # a few Adam steps on the negative log-likelihood decrease it
+    opt = torch.optim.Adam([theta], lr=0.05)
+    first = None
+    for _ in range(20):
+        opt.zero_grad()
+        loss = -P.batched_loglik(theta, m, off, t, y, mask).sum()
+        loss.backward()
+        opt.step()
+        first = loss.item() if first is None else first
+    assert loss.item() < first
+
+
+def test_grad_deterministic():
+    s = wl.random_series(39, 30_000, 0, T=300.0)
+    mask = np.ones(30_000, np.uint8)
+    a = gpu_grad("rbf", 1.0, 1.0, s.t_train, s.y_train, mask, 0.01)[1]
+    b = gpu_grad("rbf", 1.0, 1.0, s.t_train, s.y_train, mask, 0.01)[1]
+    assert np.array_equal(a, b)
