@@ -218,6 +218,36 @@ int pssgp_loglik_batched(const pssgp_model* model, const int64_t* offsets,
                          double* loglik, void* ws, size_t ws_bytes,
                          void* stream);
 
+/* ---- gradient of the log marginal likelihood ------------------------------ */
+/* d loglik / d(log lengthscale, log variance, log noise variance) by adjoint
+ * (reverse-mode) scans: the filter pass stores the predicted moments, then
+ * two backward scans of the smoothing operator's form (supplement Prop. 2)
+ * give the adjoints of the predicted mean and covariance at every step, from
+ * which the three derivatives are summed (dF/dlog l = -tau G F,
+ * dQ/dlog l = -tau (G Q + Q G^T + W), dQ/dlog s2 = Q).  The model must come
+ * from pssgp_model_build (its lengthscale and variance are the point of
+ * differentiation; a model from pssgp_model_from_sde has none: the result is
+ * then the derivative for the rescaled family of that SDE).  d/dlog R scales
+ * every R_k together.
+ * Workspace: pssgp_workspace_size_grad(d, n) bytes (larger than
+ * pssgp_workspace_size: it holds the forward moments of every step). */
+size_t pssgp_workspace_size_grad(int32_t d, int64_t n);
+
+/* One series.  loglik: one device double (nullable); grad: device double[3]. */
+int pssgp_loglik_grad(const pssgp_model* model, const double* t,
+                      const double* y, const uint8_t* mask, const double* R,
+                      int32_t R_per_step, int64_t n, double* loglik,
+                      double* grad, void* ws, size_t ws_bytes, void* stream);
+
+/* B series as in pssgp_loglik_batched.  loglik: device double[B] (nullable);
+ * grad: device double[B][3], per series d/d(log l, log s2, log R) at its own
+ * parameters. */
+int pssgp_loglik_grad_batched(const pssgp_model* model, const int64_t* offsets,
+                              int32_t B, const double* params, const double* t,
+                              const double* y, const uint8_t* mask, int64_t n,
+                              double* loglik, double* grad, void* ws,
+                              size_t ws_bytes, void* stream);
+
 /* Allocation-free variant of pssgp_loglik for callers that cannot allocate
  * device memory themselves -- for instance a plugin inside a host program
  * that owns every device allocation and does not let third-party code call
@@ -303,6 +333,43 @@ int pssgp_autotune_loglik_batched(const pssgp_model* model,
                                   int64_t n, double* loglik, void* ws,
                                   size_t ws_bytes, void* stream, int32_t reps,
                                   int32_t* best_warps, float* best_ms);
+
+/* ---- batched fit (Sec. 2: hyperparameters by maximising the marginal
+ * likelihood) -------------------------------------------------------------- */
+typedef struct pssgp_fit_options {
+  int32_t max_iter;      /* iterations at most (e.g. 2000)                      */
+  int32_t patience;      /* converged after this many iterations in a row with  */
+  double tol;            /*   |l_t - l_{t-1}| / n_s < tol (e.g. 10, 1e-7)        */
+  double lr;             /* Adam step on the log hyperparameters (e.g. 0.05)     */
+  double beta1, beta2, eps;  /* Adam constants (0.9, 0.999, 1e-8)               */
+  int32_t check_every;   /* read the converged flags and drop converged series  */
+  int32_t reserved;      /*   from the scans every this many iterations         */
+} pssgp_fit_options;
+
+/* Bytes of device workspace for pssgp_fit_batched. */
+size_t pssgp_fit_workspace_size(int32_t d, int64_t n, int32_t B);
+
+/* Fits (log lengthscale, log variance, log noise variance) of B series by
+ * Adam ascent on each series' exact log marginal likelihood, with the
+ * gradient of pssgp_loglik_grad_batched, all series in every call.
+ *  - offsets_host: HOST int64[B + 1] (as pssgp_loglik_batched's offsets);
+ *    t, y, mask: device arrays of length n.
+ *  - theta: device double[B][3], the starting point in, the fitted log
+ *    hyperparameters out (a converged series keeps the theta at which its
+ *    convergence test passed).
+ *  - loglik: device double[B], the log-likelihood at the returned theta;
+ *    iters: device int32[B], the iterations each series used (0 for empty
+ *    series).  *iterations_run (host, nullable): iterations of the loop.
+ *  - A series whose log-likelihood or gradient becomes non-finite stops.
+ *  - Synchronises `stream` every check_every iterations (the converged flags
+ *    are read on the host to re-pack the remaining series) and at the end.
+ * Not capturable in a CUDA graph (it synchronises). */
+int pssgp_fit_batched(const pssgp_model* model, const int64_t* offsets_host,
+                      int32_t B, const double* t, const double* y,
+                      const uint8_t* mask, int64_t n, double* theta,
+                      double* loglik, int32_t* iters,
+                      const pssgp_fit_options* opt, void* ws, size_t ws_bytes,
+                      void* stream, int32_t* iterations_run);
 
 /* ---- CUDA graphs --------------------------------------------------------- */
 /* Record the launches of any sequence of library calls made on `stream`

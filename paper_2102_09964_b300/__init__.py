@@ -78,6 +78,10 @@ def lib():
         L.pssgp_smooth.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, i64, i64, vp, vp, vp, vp, vp, sz, vp]
         L.pssgp_loglik.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, vp, sz, vp]
         L.pssgp_loglik_batched.argtypes = [ctypes.POINTER(PssgpModel), vp, i32, vp, vp, vp, vp, i64, vp, vp, sz, vp]
+        L.pssgp_fit_workspace_size.restype = sz
+        L.pssgp_fit_workspace_size.argtypes = [i32, i64, i32]
+        L.pssgp_fit_batched.argtypes = [ctypes.POINTER(PssgpModel), vp, i32, vp, vp, vp, i64, vp, vp, vp,
+                                        ctypes.POINTER(FitOptions), vp, sz, vp, ctypes.POINTER(i32)]
         L.pssgp_workspace_size_grad.restype = sz
         L.pssgp_workspace_size_grad.argtypes = [i32, i64]
         L.pssgp_loglik_grad.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, vp, vp, sz, vp]
@@ -316,6 +320,39 @@ def loglik_grad_batched(model: Model, offsets, params, t, y, mask, ws=None, out=
                                          _ptr(mask), n, _ptr(ll), _ptr(g), _ptr(ws), ws.numel(), _stream())
     _check(rc, "pssgp_loglik_grad_batched")
     return ll, g, ws
+
+
+class FitOptions(ctypes.Structure):
+    """pssgp_fit_options."""
+    _fields_ = [("max_iter", ctypes.c_int32), ("patience", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def fit_batched(model: Model, offsets, t, y, mask, theta0, max_iter=2000, patience=10, tol=1e-7, lr=0.05,
+                beta1=0.9, beta2=0.999, eps=1e-8, check_every=25, ws=None):
+    """Adam fit of every series' (log l, log s2, log R) on its exact log
+    marginal likelihood (native driver).  offsets: host int64 array [B+1];
+    t, y, mask: device arrays; theta0: [B, 3] start (log values).
+    Returns (theta[B, 3], loglik[B], iters[B], iterations_run)."""
+    import numpy as np
+    offs = np.ascontiguousarray(offsets, dtype=np.int64)
+    B = offs.size - 1
+    n = t.numel()
+    dev = t.device
+    theta = _f64(theta0, dev).reshape(B, 3).clone()
+    ll = torch.empty(B, dtype=torch.float64, device=dev)
+    it = torch.empty(B, dtype=torch.int32, device=dev)
+    if ws is None:
+        ws = torch.empty(int(lib().pssgp_fit_workspace_size(model.d, n, B)), dtype=torch.uint8, device=dev)
+    o = FitOptions(int(max_iter), int(patience), float(tol), float(lr), float(beta1), float(beta2), float(eps),
+                   int(check_every), 0)
+    nrun = ctypes.c_int32(0)
+    rc = lib().pssgp_fit_batched(ctypes.byref(model.raw), offs.ctypes.data_as(ctypes.c_void_p), B, _ptr(t), _ptr(y),
+                                 _ptr(mask), n, _ptr(theta), _ptr(ll), _ptr(it), ctypes.byref(o), _ptr(ws),
+                                 ws.numel(), _stream(), ctypes.byref(nrun))
+    _check(rc, "pssgp_fit_batched")
+    return theta, ll, it, int(nrun.value)
 
 
 class BatchedLogLik(torch.autograd.Function):
