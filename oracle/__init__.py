@@ -298,3 +298,38 @@ def loglik_grad_fd(kind, lengthscale, variance, t, y, mask, R, h=1e-6, order=6):
             vals.append(loglik_at(kind, math.exp(th[0]), math.exp(th[1]), t, y, mask, Rp, order=order))
         g.append((vals[0] - vals[1]) / (2.0 * h))
     return np.array(g)
+
+
+# ---------------------------------------------------------------------------
+# Simulation from the state-space prior (training data of the learned
+# initialisation), with the Philox4x32-10 counter-based generator
+# ---------------------------------------------------------------------------
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of a 4-word counter and 2-word key (list of 4 ints)."""
+    lib = _load()
+    c = (ctypes.c_uint32 * 4)(*ctr)
+    k = (ctypes.c_uint32 * 2)(*key)
+    o = (ctypes.c_uint32 * 4)()
+    lib.orc_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def normals(seed: int, sid: int, k: int, count: int) -> np.ndarray:
+    """The `count` standard normals of series `sid` at step k."""
+    lib = _load()
+    z = np.empty(count + 1)
+    lib.orc_normals(ctypes.c_uint64(seed), ctypes.c_uint32(sid), ctypes.c_uint32(k), count, _p(z))
+    return z[:count]
+
+
+def simulate_series(m, R: float, n: int, seed: int, sid: int, spacing: float = 0.01):
+    """(t, y) of series `sid` drawn from the prior of model m (its own
+    coordinates) with noise variance R, n steps of a Poisson time grid."""
+    lib = _load()
+    t = np.empty(n)
+    y = np.empty(n)
+    rc = lib.orc_simulate_series(m.d, _p(_c(m.G)), _p(_c(m.W)), _p(_c(m.Pinf)), _p(_c(m.H).ravel()),
+                                 ctypes.c_double(R), ctypes.c_long(n), ctypes.c_uint64(seed), ctypes.c_uint32(sid),
+                                 ctypes.c_double(spacing), _p(t), _p(y))
+    _check(rc, "simulate_series")
+    return t, y

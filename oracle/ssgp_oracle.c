@@ -788,3 +788,132 @@ int orc_loglik_tangent(int d, const double *H_, const double *R, const double *d
   if (dloglik) *dloglik = (double)dll;
   return 0;
 }
+
+/* ----------------------------------------------------------------------- */
+/* Simulation from the state-space prior (the training data of the learned */
+/* initialisation): random numbers from the counter-based generator        */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as */
+/* easy as 1, 2, 3", SC 2011), written from its definition: ten rounds of  */
+/*   (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2),                  */
+/*                        hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))                  */
+/* with the key advanced by the Weyl constants (W0, W1) between rounds.    */
+/* ----------------------------------------------------------------------- */
+#include <stdint.h>
+
+static void philox_round(uint32_t c[4], const uint32_t k[2]) {
+  const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+  const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+  const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k[0];
+  const uint32_t n1 = (uint32_t)p1;
+  const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k[1];
+  const uint32_t n3 = (uint32_t)p0;
+  c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+}
+
+static void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+  uint32_t k[2] = {key[0], key[1]};
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k[0] += 0x9E3779B9u; k[1] += 0xBB67AE85u; }
+    philox_round(c, k);
+  }
+  out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+void orc_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out) { philox4x32_10(ctr, key, out); }
+
+/* a uniform in (0, 1) from two 32-bit words: the 53-bit integer
+ * m = a * 2^21 + floor(b / 2^11), u = (m + 1/2) 2^-53 */
+static real u53(uint32_t a, uint32_t b) {
+  const uint64_t m = ((uint64_t)a << 21) | (uint64_t)(b >> 11);
+  return ((real)m + 0.5L) * ldexpl(1.0L, -53);
+}
+
+/* Draws of series `sid` at step k: call j of the generator has counter
+ * (k, sid, j, 0) and key (seed_lo, seed_hi).  Call 0 gives the time
+ * increment (its first uniform); call j >= 1 gives two standard normals by
+ * Box-Muller: r = sqrt(-2 log u1), (r cos 2 pi u2, r sin 2 pi u2). */
+static void draw_call(uint32_t k, uint32_t sid, uint32_t j, uint64_t seed, uint32_t w[4]) {
+  const uint32_t ctr[4] = {k, sid, j, 0u};
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  philox4x32_10(ctr, key, w);
+}
+
+void orc_normals(uint64_t seed, uint32_t sid, uint32_t k, int count, double *z) {
+  const real twopi = 6.283185307179586476925286766559L;
+  for (int j = 0; j < (count + 1) / 2; ++j) {
+    uint32_t w[4];
+    draw_call(k, sid, (uint32_t)(j + 1), seed, w);
+    const real u1 = u53(w[0], w[1]), u2 = u53(w[2], w[3]);
+    const real r = sqrtl(-2.0L * logl(u1));
+    z[2 * j] = (double)(r * cosl(twopi * u2));
+    if (2 * j + 1 < count) z[2 * j + 1] = (double)(r * sinl(twopi * u2));
+  }
+}
+
+/* lower Cholesky factor of a symmetric positive semi-definite matrix; a
+ * pivot at most 1e-10 times its diagonal entry (a direction with no
+ * variance, e.g. a zero-length step) gives a zero column */
+static void chol_psd(int d, const real *A, real *L) {
+  memset(L, 0, sizeof(real) * d * d);
+  for (int j = 0; j < d; ++j) {
+    real p = A[j * d + j];
+    for (int k = 0; k < j; ++k) p -= L[j * d + k] * L[j * d + k];
+    if (!(p > 1e-10L * A[j * d + j])) continue;
+    const real ljj = sqrtl(p);
+    L[j * d + j] = ljj;
+    for (int i = j + 1; i < d; ++i) {
+      real s = A[i * d + j];
+      for (int k = 0; k < j; ++k) s -= L[i * d + k] * L[j * d + k];
+      L[i * d + j] = s / ljj;
+    }
+  }
+}
+
+/* One series of n steps from the prior of the model (G, W, P_inf, H) with
+ * noise variance R: t_0 = 0, t_k = t_{k-1} - spacing log u_k (a Poisson
+ * process of mean spacing `spacing`); x_0 = chol(P_inf) z_0,
+ * x_k = F_k x_{k-1} + chol(Q_k) z_k (F_k, Q_k of the step, Van Loan as in
+ * orc_discretize); y_k = H x_k + sqrt(R) z'_k, with (z_k, z'_k) the d + 1
+ * normals of step k. */
+int orc_simulate_series(int d, const double *G_, const double *W_, const double *Pinf_, const double *H_,
+                        double R, long n, uint64_t seed, uint32_t sid, double spacing, double *t_out,
+                        double *y_out) {
+  if (d < 1 || d > DMAX || n < 0) return 3;
+  real G[DMAX * DMAX], W[DMAX * DMAX], Pinf[DMAX * DMAX], H[DMAX], L[DMAX * DMAX];
+  load(d, d, G_, G); load(d, d, W_, W); load(d, d, Pinf_, Pinf); load(1, d, H_, H);
+  real x[DMAX];
+  real t = 0.0L;
+  for (long k = 0; k < n; ++k) {
+    double z[DMAX + 2];
+    orc_normals(seed, sid, (uint32_t)k, d + 1, z);
+    if (k == 0) {
+      chol_psd(d, Pinf, L);
+      for (int i = 0; i < d; ++i) {
+        real s = 0.0L;
+        for (int j = 0; j <= i; ++j) s += L[i * d + j] * (real)z[j];
+        x[i] = s;
+      }
+    } else {
+      uint32_t w[4];
+      draw_call((uint32_t)k, sid, 0u, seed, w);
+      const real h = -(real)spacing * logl(u53(w[0], w[1]));
+      t += h;
+      real F[DMAX * DMAX], Q[DMAX * DMAX], xn[DMAX];
+      discretize_one(d, G, W, h, F, Q);
+      chol_psd(d, Q, L);
+      for (int i = 0; i < d; ++i) {
+        real s = 0.0L;
+        for (int j = 0; j < d; ++j) s += F[i * d + j] * x[j];
+        for (int j = 0; j <= i; ++j) s += L[i * d + j] * (real)z[j];
+        xn[i] = s;
+      }
+      memcpy(x, xn, sizeof(real) * d);
+    }
+    real f = 0.0L;
+    for (int i = 0; i < d; ++i) f += H[i] * x[i];
+    t_out[k] = (double)t;
+    y_out[k] = (double)(f + sqrtl((real)R) * (real)z[d]);
+  }
+  return 0;
+}
