@@ -371,6 +371,76 @@ int pssgp_fit_batched(const pssgp_model* model, const int64_t* offsets_host,
                       const pssgp_fit_options* opt, void* ws, size_t ws_bytes,
                       void* stream, int32_t* iterations_run);
 
+/* ---- learned initialisation of the fit --------------------------------------
+ * A small network proposes initial log hyperparameters for the marginal-
+ * likelihood fit from a log periodogram of each series; it is trained on
+ * series simulated from the state-space prior itself. */
+
+/* Simulates B series from the prior of the model's kernel family at
+ * per-series (lengthscale, variance, noise variance) = params[3 s .. 3 s + 2]
+ * (device double[3 B]); series s has offsets[s + 1] - offsets[s] steps
+ * (device int64[B + 1]).  Times: t_0 = 0, t_k = t_{k-1} - spacing log u_k (a
+ * Poisson process of mean spacing `spacing`); state: x_0 ~ N(0, P_inf),
+ * x_k = F_k x_{k-1} + chol(Q_k) z_k; y_k = f(t_k) + sqrt(R) z'_k.  Random
+ * numbers: Philox4x32-10 with key (seed mod 2^32, seed / 2^32); step k of
+ * series s uses counter (k, s, 0, 0) for the time increment (first 53-bit
+ * uniform (a 2^21 + b / 2^11 + 1/2) 2^-53 of words a, b) and counters
+ * (k, s, j, 0), j >= 1, for Box-Muller pairs of normals: the d state
+ * normals, then the measurement normal.  chol(.) is the lower Cholesky
+ * factor with a zero column where a pivot is at most 1e-10 of its diagonal
+ * entry.  Outputs t, y: device double[n].  status: device int32, set to
+ * PSSGP_ENAN if a value is not finite.  The model must come from
+ * pssgp_model_build (PSSGP_EMODEL otherwise). */
+int pssgp_simulate_prior(const pssgp_model* model, const int64_t* offsets,
+                         int32_t B, const double* params, uint64_t seed,
+                         double spacing, double* t, double* y, int32_t* status,
+                         void* stream);
+
+/* 65 features per series (device float[B][65]): log(P_j + 1e-8), j < 64, and
+ * log s2, where s2 is the series' variance, dbar its mean spacing
+ * (t_{n-1} - t_0) / (n - 1), A(w) = |sum_k (y_k - ybar) exp(-i w k dbar)|^2
+ * / (n s2) the periodogram on the regular grid k dbar, and P_j the mean of
+ * A at w_lo r^(j + (q - 3/2) / 4), q < 4, r = (w_hi / w_lo)^(1/63),
+ * w_lo = 2 pi / 40.96, w_hi = 0.9 pi / 0.01; zeros for a series with fewer
+ * than 2 steps or s2 = 0.  Computed in FP32 (phase re-anchored from FP64
+ * every 32 steps). */
+int pssgp_features(const int64_t* offsets, int32_t B, const double* t,
+                   const double* y, float* feat, void* stream);
+
+/* The network 65 -> 256 -> 256 -> 3 (ReLU), standardised inputs and outputs,
+ * BF16 GEMMs on the tensor cores with FP32 accumulation, FP32 parameters and
+ * Adam state.  `state`: a device buffer of pssgp_mlp_state_bytes() bytes
+ * (256-byte aligned).  Parameter layout (pssgp_mlp_param_count() floats):
+ * W1[256][80] (columns >= 65 zero), b1[256], W2[256][256], b2[256],
+ * W3[16][256] (rows >= 3 zero), b3[16].  Normalisation block (144 floats):
+ * feature mean[65], sd[65], target mean[3], sd[3].  Targets are log
+ * hyperparameters (log l, log s2, log R), device double[rows][3]. */
+size_t pssgp_mlp_state_bytes(void);
+int32_t pssgp_mlp_param_count(void);
+/* Device workspace for a minibatch (or prediction batch) of `rows` rows. */
+size_t pssgp_mlp_workspace_size(int32_t rows);
+/* Normalisation statistics from nrows training rows, He-uniform weights from
+ * Philox4x32-10 (seed), zero biases and Adam state. */
+int pssgp_mlp_init(void* state, uint64_t seed, const float* feat,
+                   int64_t nrows, const double* theta, void* stream);
+/* Sets parameters and normalisation (device float arrays in the layouts
+ * above) and clears the Adam state. */
+int pssgp_mlp_set_params(void* state, const float* params, const float* norm,
+                         void* stream);
+/* Loss 1/(2 rows) sum over rows and the 3 outputs of (out - target)^2 in
+ * standardised units, its gradient (device float[param_count], layout
+ * above), the loss (device float, nullable) and the raw outputs (device
+ * float[rows][16], nullable).  rows must be a multiple of 8. */
+int pssgp_mlp_grad(void* state, const float* feat, const double* theta,
+                   int32_t rows, float* grad, float* loss, float* out,
+                   void* ws, size_t ws_bytes, void* stream);
+/* One Adam step (0.9, 0.999, 1e-8; step counts from 1) on the parameters. */
+int pssgp_mlp_adam(void* state, const float* grad, float lr, int32_t step,
+                   void* stream);
+/* Proposed log hyperparameters (device double[rows][3]). */
+int pssgp_mlp_predict(const void* state, const float* feat, int32_t rows,
+                      double* theta, void* ws, size_t ws_bytes, void* stream);
+
 /* ---- CUDA graphs --------------------------------------------------------- */
 /* Record the launches of any sequence of library calls made on `stream`
  * between pssgp_graph_begin and pssgp_graph_end (thread-local stream

@@ -82,6 +82,17 @@ def lib():
         L.pssgp_fit_workspace_size.argtypes = [i32, i64, i32]
         L.pssgp_fit_batched.argtypes = [ctypes.POINTER(PssgpModel), vp, i32, vp, vp, vp, i64, vp, vp, vp,
                                         ctypes.POINTER(FitOptions), vp, sz, vp, ctypes.POINTER(i32)]
+        L.pssgp_simulate_prior.argtypes = [ctypes.POINTER(PssgpModel), vp, i32, vp, ctypes.c_uint64, dp, vp, vp,
+                                           vp, vp]
+        L.pssgp_features.argtypes = [vp, i32, vp, vp, vp, vp]
+        L.pssgp_mlp_state_bytes.restype = sz
+        L.pssgp_mlp_workspace_size.restype = sz
+        L.pssgp_mlp_workspace_size.argtypes = [i32]
+        L.pssgp_mlp_init.argtypes = [vp, ctypes.c_uint64, vp, i64, vp, vp]
+        L.pssgp_mlp_set_params.argtypes = [vp, vp, vp, vp]
+        L.pssgp_mlp_grad.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, sz, vp]
+        L.pssgp_mlp_adam.argtypes = [vp, vp, ctypes.c_float, i32, vp]
+        L.pssgp_mlp_predict.argtypes = [vp, vp, i32, vp, vp, sz, vp]
         L.pssgp_workspace_size_grad.restype = sz
         L.pssgp_workspace_size_grad.argtypes = [i32, i64]
         L.pssgp_loglik_grad.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, vp, vp, sz, vp]
@@ -550,3 +561,101 @@ class Graph:
             except Exception:
                 pass
             self._h = ctypes.c_void_p(None)
+
+
+# ---------------------------------------------------------------------------
+# learned initialisation: prior simulation, features, the network
+# ---------------------------------------------------------------------------
+NFEAT = 65
+
+
+def simulate_prior(model: Model, offsets, params, seed: int, spacing: float = 0.01):
+    """Series drawn from the prior of the model's family at per-series
+    (lengthscale, variance, noise) params[B, 3]; offsets: device int64[B+1].
+    Returns (t, y) device float64 arrays of length offsets[-1]."""
+    dev = offsets.device
+    B = offsets.numel() - 1
+    n = int(offsets[-1].item())
+    params = _f64(params, dev).reshape(-1)
+    t = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+    y = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    rc = lib().pssgp_simulate_prior(ctypes.byref(model.raw), _ptr(offsets), B, _ptr(params), int(seed),
+                                    float(spacing), _ptr(t), _ptr(y), _ptr(st), _stream())
+    _check(rc, "pssgp_simulate_prior")
+    return t[:n], y[:n], st
+
+
+def features(offsets, t, y, out=None):
+    """The 65 log-periodogram features of every series (device float32[B, 65])."""
+    B = offsets.numel() - 1
+    f = out if out is not None else torch.empty(B, NFEAT, dtype=torch.float32, device=t.device)
+    _check(lib().pssgp_features(_ptr(offsets), B, _ptr(t), _ptr(y), _ptr(f), _stream()), "pssgp_features")
+    return f
+
+
+class MLP:
+    """The initialisation network (state in one device buffer, see pssgp.h)."""
+
+    def __init__(self, device="cuda"):
+        self.device = torch.device(device)
+        self.state = torch.zeros(int(lib().pssgp_mlp_state_bytes()), dtype=torch.uint8, device=self.device)
+        self.nparam = int(lib().pssgp_mlp_param_count())
+        self.step = 0
+        self._ws = {}
+
+    def ws(self, rows: int):
+        if rows not in self._ws:
+            self._ws[rows] = torch.empty(int(lib().pssgp_mlp_workspace_size(int(rows))), dtype=torch.uint8,
+                                         device=self.device)
+        return self._ws[rows]
+
+    def init(self, seed: int, feat, theta):
+        _check(lib().pssgp_mlp_init(_ptr(self.state), int(seed), _ptr(feat), feat.shape[0], _ptr(theta),
+                                    _stream()), "pssgp_mlp_init")
+        self.step = 0
+
+    def set_params(self, params, norm):
+        params = torch.as_tensor(params, dtype=torch.float32, device=self.device).contiguous()
+        norm = torch.as_tensor(norm, dtype=torch.float32, device=self.device).contiguous()
+        _check(lib().pssgp_mlp_set_params(_ptr(self.state), _ptr(params), _ptr(norm), _stream()),
+               "pssgp_mlp_set_params")
+        self.step = 0
+
+    def grad(self, feat, theta, grad=None, loss=None, out=None):
+        rows = feat.shape[0]
+        g = grad if grad is not None else torch.empty(self.nparam, dtype=torch.float32, device=self.device)
+        ls = loss if loss is not None else torch.empty(1, dtype=torch.float32, device=self.device)
+        ws = self.ws(rows)
+        _check(lib().pssgp_mlp_grad(_ptr(self.state), _ptr(feat), _ptr(theta), rows, _ptr(g), _ptr(ls), _ptr(out),
+                                    _ptr(ws), ws.numel(), _stream()), "pssgp_mlp_grad")
+        return g, ls
+
+    def adam(self, grad, lr: float):
+        self.step += 1
+        _check(lib().pssgp_mlp_adam(_ptr(self.state), _ptr(grad), float(lr), self.step, _stream()), "pssgp_mlp_adam")
+
+    def train(self, feat, theta, epochs: int, batch: int = 4096, lr: float = 1e-3, lr_final: float = 1e-4):
+        """Adam on consecutive minibatches (the rows are i.i.d. draws, so a
+        fixed order is a random one); cosine-free geometric decay of the step
+        from lr to lr_final.  Returns the loss of every step (device)."""
+        rows = feat.shape[0]
+        nb = rows // batch
+        g = torch.empty(self.nparam, dtype=torch.float32, device=self.device)
+        losses = torch.empty(max(epochs * nb, 1), dtype=torch.float32, device=self.device)
+        total = epochs * nb
+        for e in range(epochs):
+            for b in range(nb):
+                i = e * nb + b
+                a = b * batch
+                self.grad(feat[a:a + batch], theta[a:a + batch], grad=g, loss=losses[i:i + 1])
+                self.adam(g, lr * (lr_final / lr) ** (i / max(total - 1, 1)))
+        return losses[:total]
+
+    def predict(self, feat):
+        rows = feat.shape[0]
+        th = torch.empty(rows, 3, dtype=torch.float64, device=self.device)
+        ws = self.ws(rows)
+        _check(lib().pssgp_mlp_predict(_ptr(self.state), _ptr(feat), rows, _ptr(th), _ptr(ws), ws.numel(),
+                                       _stream()), "pssgp_mlp_predict")
+        return th

@@ -10,7 +10,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SOURCES = [os.path.join(HERE, "csrc", f) for f in ("pssgp_kernels.cu", "pssgp_fit.cu", "pssgp_model.cpp")]
+SOURCES = [os.path.join(HERE, "csrc", f) for f in ("pssgp_kernels.cu", "pssgp_fit.cu", "pssgp_learn.cu", "pssgp_model.cpp")]
 DEPS = SOURCES + sorted(os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc"))
                         if f.endswith(".cuh")) + [os.path.join(ROOT, "include", "pssgp.h")]
 LIB = os.path.join(HERE, "libpssgp.so")

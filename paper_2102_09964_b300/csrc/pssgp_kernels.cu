@@ -30,6 +30,7 @@
 
 #include "../../include/pssgp.h"
 #include "adjoint_ops.cuh"
+#include "host_model.cuh"
 #include "scan_ops.cuh"
 #include "warp_ops.cuh"
 
@@ -794,8 +795,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_smoother_propagate(const DevModel<
 #pragma unroll
     for (int i = 0; i < D; ++i) ms[i] = m2[i];
     copy<D>(P2, Ps);
-    if (a.f_mean) a.f_mean[k] = ms[0] * m.Dsc[0];
-    if (a.f_var) a.f_var[k] = Ps[0][0] * (m.Dsc[0] * m.Dsc[0]);
+    // f = H x = H D z = z_0 (the model is built with H D = e_0^T)
+    if (a.f_mean) a.f_mean[k] = ms[0];
+    if (a.f_var) a.f_var[k] = Ps[0][0];
     if (a.xs) {
 #pragma unroll
       for (int i = 0; i < D; ++i) a.xs[i * a.ld + k] = ms[i] * m.Dsc[i];
@@ -1226,35 +1228,6 @@ __global__ void k_dfma_probe(double* out, int iters) {
 // ---------------------------------------------------------------------------
 // host helpers
 // ---------------------------------------------------------------------------
-template <int D>
-DevModel<D> dev_model(const pssgp_model* pm) {
-  DevModel<D> m;
-  std::memset(&m, 0, sizeof(m));
-  for (int i = 0; i < D; ++i)
-    for (int j = i; j < D; ++j) m.Pinf[pidx<D>(i, j)] = pm->Pinf[i * D + j];
-  for (int i = 0; i < D; ++i) m.Dsc[i] = pm->D[i];
-  for (int e = 0; e < D * D; ++e)
-    for (int t = 0; t < NT; ++t) m.fc[e][t] = pm->fc[e * PSSGP_NTAYLOR + t];
-  for (int i = 0; i < D; ++i)
-    for (int j = i; j < D; ++j)
-      for (int t = 0; t < NT; ++t) m.qc[pidx<D>(i, j)][t] = pm->qc[(i * D + j) * PSSGP_NTAYLOR + t];
-  // thresholds rounded toward zero in float so that a float step never passes a
-  // bound that the double value would fail
-  for (int t = 0; t <= NT; ++t) {
-    m.hthr_f[t] = std::nextafter((float)pm->hthr_f[t], 0.0f);
-    m.hthr_q[t] = std::nextafter((float)pm->hthr_q[t], 0.0f);
-  }
-  m.hmax = std::nextafter((float)pm->hmax, 0.0f);
-  m.companion = pm->companion;
-  for (int i = 0; i < D; ++i)
-    for (int j = 0; j < D; ++j) { m.rsup[i][j] = pm->rsup[i * D + j]; m.rlast[i][j] = pm->rlast[i * D + j]; }
-  return m;
-}
-
-bool model_ok(const pssgp_model* pm) {
-  return pm && pm->d >= 1 && pm->d <= PSSGP_DMAX && pm->hmax > 0.0 && pm->D[0] != 0.0;
-}
-
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PSSGP_OK : PSSGP_ECUDA; }
 
 char* ws_ptr(void* ws, int64_t off) { return static_cast<char*>(ws) + off; }

@@ -69,9 +69,13 @@ __device__ __noinline__ void double_steps(Mat<D>& F, Mat<D>& Q, int s, int smax)
 // P_inf = s2 P_inf1, with (F1, Q1, P_inf1) the model at l = 1, s2 = 1; so one
 // unit model serves a batch of series with uscale = 1/l and qscale = s2 each
 // (both 1 for a model built at its own hyperparameters).
+// all_terms: sum every stored Taylor term (entrywise accuracy of the small
+// entries of Q for short steps, which the per-warp normwise term count does
+// not give; needed where Q is factorised, as in the prior simulation).
 template <int D>
 __device__ __forceinline__ void discretize(const DevModel<D>& m, double h, bool first, bool active,
-                                           Mat<D>& F, Mat<D>& Q, double uscale = 1.0, double qscale = 1.0) {
+                                           Mat<D>& F, Mat<D>& Q, double uscale = 1.0, double qscale = 1.0,
+                                           bool all_terms = false) {
   h *= uscale;
   float hf = (float)h;
   int s = 0;
@@ -89,6 +93,7 @@ __device__ __forceinline__ void discretize(const DevModel<D>& m, double h, bool 
   for (int k = 1; k <= NT; ++k) if (hw <= m.hthr_f[k]) { kf = k; break; }
 #pragma unroll 1
   for (int k = 1; k <= NT; ++k) if (hw <= m.hthr_q[k]) { kq = k; break; }
+  if (all_terms) { kf = NT; kq = NT; }
   const int smax = (int)__reduce_max_sync(0xffffffffu, (unsigned)s);
   double hs = (s > 0) ? h * __longlong_as_double((long long)(1023 - s) << 52) : h;
   if (first || !active) hs = 0.0;

@@ -289,3 +289,16 @@ def test_deterministic():
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[1], b[1])
     assert a[2] == b[2]
+
+
+def test_user_sde_with_scaled_measurement_row():
+    """y = h0 x_0 + e with h0 = 2 (pssgp_model_from_sde): f = H x, so the
+    marginals are those of the oracle run with the same H."""
+    s = wl.sinusoid_small(N=400, M=40)
+    o = om.make_model("matern32", 0.5, 1.0)
+    o.H = 2.0 * o.H
+    fm, fv, res, _ = oracle.predict(o, s.t_train, s.y_train, s.t_test, 0.01)
+    m = P.model_from_sde(o.G, o.L, o.q, o.H)
+    mean, var, ll, ws = P.predict(m, dev(s.t_train), dev(s.y_train), dev(s.t_test), 0.01)
+    assert P.status(ws) == 0
+    check_marginals(host(mean), host(var), float(host(ll)[0]), fm, fv, res.loglik, s.N, 1e-9, "H = 2 e0")

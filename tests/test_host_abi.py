@@ -26,7 +26,7 @@ def lib():
 
 def header_functions():
     text = open(os.path.join(ROOT, "include", "pssgp.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:int|size_t|const char\s*\*)\s*(pssgp_\w+)\s*\(", text, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int32_t|int|size_t|const char\s*\*)\s*(pssgp_\w+)\s*\(", text, flags=re.M)))
 
 
 def test_exports_every_declared_symbol(lib):

@@ -64,19 +64,36 @@ def test_simulated_covariance_is_the_kernel(kind, nu):
             assert abs(c.mean()) < 5 * c.std() / math.sqrt(N), (i, j, c.mean())
 
 
-def test_features_equal_fft_on_even_grids():
+def test_dft_power_equals_fft_bins():
+    """On the regular grid, A(w) at w = 2 pi m / (n dbar) is FFT bin m."""
     rng = np.random.default_rng(1)
     n = 4096
-    w = of.frequencies()
-    y = rng.normal(size=n) + np.cos(w[10] * 0.01 * np.arange(n))
-    for j, mbin in ((10, 50), (40, 700)):
-        dt = 2 * math.pi * mbin / (n * w[j])         # w_j falls on FFT bin mbin
-        t = dt * np.arange(n)
-        f = of.features(t, y)
-        yc = y - y.mean()
-        P = abs(np.fft.fft(yc)[mbin]) ** 2 / (n * np.mean(yc * yc))
-        assert abs(f[j] - math.log(P + 1e-8)) < 1e-9
-    assert abs(f[64] - math.log(np.var(y))) < 1e-12
+    y = rng.normal(size=n) + np.cos(0.3 * np.arange(n))
+    dbar = 0.01
+    yc = y - y.mean()
+    F = np.fft.fft(yc)
+    for mbin in (1, 50, 700, 2047):
+        w = 2 * math.pi * mbin / (n * dbar)
+        A = of.dft_power(y, np.array([w]), dbar)[0]
+        assert abs(A - abs(F[mbin]) ** 2 / (n * np.mean(yc * yc))) <= 1e-9 * A
+
+
+def test_features_structure():
+    """Bins are the averages of four sub-frequencies spread over the bin;
+    the top sub-frequency stays below the Nyquist frequency pi / dbar; the
+    grid is the mean spacing (times only enter through it)."""
+    w = of.sub_frequencies()
+    assert w.shape == (64, 4) and np.all(np.diff(w.ravel()) > 0)
+    assert w.max() < math.pi / 0.01
+    rng = np.random.default_rng(8)
+    t = np.cumsum(rng.exponential(0.01, 2000))
+    y = rng.normal(size=2000)
+    f = of.features(t, y)
+    dbar = (t[-1] - t[0]) / 1999
+    A = of.dft_power(y, w, dbar)
+    assert np.allclose(f[:64], np.log(A.mean(axis=1) + 1e-8), rtol=0, atol=1e-12)
+    t2 = np.linspace(t[0], t[-1], 2000)          # same mean spacing, other times
+    assert np.allclose(of.features(t2, y), f, rtol=0, atol=1e-12)
 
 
 def test_features_invariances_and_edge_cases():
@@ -88,5 +105,79 @@ def test_features_invariances_and_edge_cases():
     assert np.allclose(f[:64], g[:64], atol=1e-10)
     assert abs(g[64] - f[64] - math.log(9.0)) < 1e-12
     assert np.all(of.features(t, np.ones(3000)) == 0.0)
+    assert np.all(of.features(t[:1], y[:1]) == 0.0)
     # white noise: the normalised periodogram averages to 1 over the bins
-    assert abs(np.mean(np.exp(f[:64])) - 1.0) < 0.35
+    assert abs(np.mean(np.exp(f[:64])) - 1.0) < 0.2
+
+
+def test_noise_shows_as_the_high_frequency_plateau():
+    """A smooth signal plus white noise of variance R on the Poisson grid:
+    the top bins sit near R / (s2_signal + R) (the noise's share of the
+    normalised periodogram), the low bins far above it."""
+    rng = np.random.default_rng(9)
+    n = 4096
+    t = np.cumsum(rng.exponential(0.01, n))
+    sig = np.sin(0.7 * t) + 0.5 * np.sin(1.9 * t)
+    R = 0.01
+    y = sig + rng.normal(0, math.sqrt(R), n)
+    f = of.features(t, y)
+    share = R / (np.var(sig) + R)
+    assert abs(np.mean(f[56:64]) - math.log(share)) < 0.5
+    assert f[:8].max() > math.log(share) + 5
+
+
+# ---------------------------------------------------------------------------
+# the network oracle
+# ---------------------------------------------------------------------------
+from oracle import mlp as om_mlp  # noqa: E402
+
+
+def _net_inputs(M=32, seed=3):
+    rng = np.random.default_rng(seed)
+    feat = rng.normal(size=(M, 65)).astype(np.float32)
+    theta = rng.normal(size=(M, 3))
+    norm = np.zeros(144)
+    norm[:65] = rng.normal(0, 0.1, 65)
+    norm[65:130] = rng.uniform(0.5, 2.0, 65)
+    norm[130:133] = rng.normal(0, 0.2, 3)
+    norm[133:136] = rng.uniform(0.5, 2.0, 3)
+    return feat, theta, norm.astype(np.float32).astype(np.float64)
+
+
+def test_bf16_rounding_matches_torch():
+    import torch
+    x = np.random.default_rng(4).normal(size=20_000) * np.exp(np.random.default_rng(5).uniform(-20, 20, 20_000))
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(om_mlp.bf16(x), ref)
+
+
+def test_network_gradient_equals_autograd_and_differences():
+    """Without the bfloat16 rounding the oracle's backward pass is the exact
+    gradient: equal to torch autograd in float64 and to central differences."""
+    import torch
+    feat, theta, norm = _net_inputs()
+    p = om_mlp.random_params(6)
+    loss, g, out = om_mlp.loss_grad(p, norm, feat, theta, rounding=False)
+    pt = torch.tensor(p, dtype=torch.float64, requires_grad=True)
+    W1 = pt[om_mlp.OW1:om_mlp.OB1].reshape(256, 80)
+    W2 = pt[om_mlp.OW2:om_mlp.OB2].reshape(256, 256)
+    W3 = pt[om_mlp.OW3:om_mlp.OB3].reshape(16, 256)
+    X = torch.zeros(32, 80, dtype=torch.float64)
+    X[:, :65] = (torch.tensor(feat, dtype=torch.float64) - torch.tensor(norm[:65])) / torch.tensor(norm[65:130])
+    H1 = torch.relu(X @ W1.T + pt[om_mlp.OB1:om_mlp.OW2])
+    H2 = torch.relu(H1 @ W2.T + pt[om_mlp.OB2:om_mlp.OW3])
+    o = H2 @ W3.T + pt[om_mlp.OB3:]
+    tn = (torch.tensor(theta) - torch.tensor(norm[130:133])) / torch.tensor(norm[133:136])
+    lt = 0.5 * ((o[:, :3] - tn) ** 2).sum() / 32
+    lt.backward()
+    assert abs(lt.item() - loss) < 1e-13 * abs(loss)
+    assert np.allclose(pt.grad.numpy(), g, rtol=1e-10, atol=1e-14)
+    rng = np.random.default_rng(7)
+    for i in rng.choice(np.flatnonzero(g != 0.0), 12, replace=False):
+        h = 1e-6
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (om_mlp.loss_grad(pp, norm, feat, theta, rounding=False)[0]
+              - om_mlp.loss_grad(pm, norm, feat, theta, rounding=False)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(g[i]), 1e-3)

@@ -148,3 +148,28 @@ def subset(bt: Batch, idx) -> Batch:
 
 
 BATCH = dict(seed=3, B=4096, n_min=1000, n_max=65536, spacing=0.01)
+
+
+def prior_spec(seed: int, B: int, n: int | None = None, n_min: int | None = None, n_max: int | None = None,
+               ell=(0.1, 10.0), var=(0.1, 10.0), noise=(1e-3, 1e-1)):
+    """Lengths and hyperparameters of B series to be drawn from a prior:
+    (lengthscale, variance, noise variance) each log-uniform on its range;
+    lengths all n, or log-uniform on [n_min, n_max].  Returns
+    (offsets int64[B+1], params float64[B, 3])."""
+    rng = np.random.default_rng(seed)
+    if n is not None:
+        lengths = np.full(B, int(n), dtype=np.int64)
+    else:
+        lengths = np.rint(np.exp(rng.uniform(np.log(n_min), np.log(n_max), B))).astype(np.int64)
+    offsets = np.zeros(B + 1, dtype=np.int64)
+    np.cumsum(lengths, out=offsets[1:])
+    lo = np.log([ell[0], var[0], noise[0]])
+    hi = np.log([ell[1], var[1], noise[1]])
+    params = np.exp(rng.uniform(lo, hi, (B, 3)))
+    return offsets, params
+
+
+# The learned-initialisation workload: Matern-5/2 prior series, mean spacing
+# 0.01 (a Poisson time grid), log-uniform hyperparameters.
+LEARN_TRAIN = dict(seed=50, B=1_000_000, n=4096)
+LEARN_HELDOUT = dict(seed=51, B=4096, n_min=4096, n_max=65536)
