@@ -336,29 +336,37 @@ int pssgp_autotune_loglik_batched(const pssgp_model* model,
 
 /* ---- batched fit (Sec. 2: hyperparameters by maximising the marginal
  * likelihood) -------------------------------------------------------------- */
+#define PSSGP_FIT_ADAM 0
+#define PSSGP_FIT_LBFGS 1
 typedef struct pssgp_fit_options {
-  int32_t max_iter;      /* iterations at most (e.g. 2000)                      */
+  int32_t max_iter;      /* evaluations at most (e.g. 2000)                     */
   int32_t patience;      /* converged after this many iterations in a row with  */
   double tol;            /*   |l_t - l_{t-1}| / n_s < tol (e.g. 10, 1e-7)        */
   double lr;             /* Adam step on the log hyperparameters (e.g. 0.05)     */
   double beta1, beta2, eps;  /* Adam constants (0.9, 0.999, 1e-8)               */
   int32_t check_every;   /* read the converged flags and drop converged series  */
-  int32_t reserved;      /*   from the scans every this many iterations         */
+                         /*   from the scans every this many iterations         */
+  int32_t method;        /* PSSGP_FIT_ADAM, or PSSGP_FIT_LBFGS: limited-memory
+                          * BFGS (6 pairs) with Armijo backtracking, steps of
+                          * at most 2 in every log parameter; the convergence
+                          * test runs on accepted steps; lr and the Adam
+                          * constants are unused */
 } pssgp_fit_options;
 
 /* Bytes of device workspace for pssgp_fit_batched. */
 size_t pssgp_fit_workspace_size(int32_t d, int64_t n, int32_t B);
 
 /* Fits (log lengthscale, log variance, log noise variance) of B series by
- * Adam ascent on each series' exact log marginal likelihood, with the
- * gradient of pssgp_loglik_grad_batched, all series in every call.
+ * Adam ascent or L-BFGS on each series' exact log marginal likelihood, with
+ * the gradient of pssgp_loglik_grad_batched; every loop iteration evaluates
+ * all series still being fitted in one call.
  *  - offsets_host: HOST int64[B + 1] (as pssgp_loglik_batched's offsets);
  *    t, y, mask: device arrays of length n.
  *  - theta: device double[B][3], the starting point in, the fitted log
  *    hyperparameters out (a converged series keeps the theta at which its
  *    convergence test passed).
  *  - loglik: device double[B], the log-likelihood at the returned theta;
- *    iters: device int32[B], the iterations each series used (0 for empty
+ *    iters: device int32[B], the evaluations each series used (0 for empty
  *    series).  *iterations_run (host, nullable): iterations of the loop.
  *  - A series whose log-likelihood or gradient becomes non-finite stops.
  *  - Synchronises `stream` every check_every iterations (the converged flags

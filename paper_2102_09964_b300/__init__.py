@@ -337,13 +337,16 @@ class FitOptions(ctypes.Structure):
     """pssgp_fit_options."""
     _fields_ = [("max_iter", ctypes.c_int32), ("patience", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
-                ("eps", ctypes.c_double), ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("eps", ctypes.c_double), ("check_every", ctypes.c_int32), ("method", ctypes.c_int32)]
+
+
+FIT_ADAM, FIT_LBFGS = 0, 1
 
 
 def fit_batched(model: Model, offsets, t, y, mask, theta0, max_iter=2000, patience=10, tol=1e-7, lr=0.05,
-                beta1=0.9, beta2=0.999, eps=1e-8, check_every=25, ws=None):
-    """Adam fit of every series' (log l, log s2, log R) on its exact log
-    marginal likelihood (native driver).  offsets: host int64 array [B+1];
+                beta1=0.9, beta2=0.999, eps=1e-8, check_every=25, ws=None, method="adam"):
+    """Adam (method="adam") or L-BFGS (method="lbfgs") fit of every series'
+    (log l, log s2, log R) on its exact log marginal likelihood (native driver).  offsets: host int64 array [B+1];
     t, y, mask: device arrays; theta0: [B, 3] start (log values).
     Returns (theta[B, 3], loglik[B], iters[B], iterations_run)."""
     import numpy as np
@@ -357,7 +360,7 @@ def fit_batched(model: Model, offsets, t, y, mask, theta0, max_iter=2000, patien
     if ws is None:
         ws = torch.empty(int(lib().pssgp_fit_workspace_size(model.d, n, B)), dtype=torch.uint8, device=dev)
     o = FitOptions(int(max_iter), int(patience), float(tol), float(lr), float(beta1), float(beta2), float(eps),
-                   int(check_every), 0)
+                   int(check_every), {"adam": FIT_ADAM, "lbfgs": FIT_LBFGS}[method])
     nrun = ctypes.c_int32(0)
     rc = lib().pssgp_fit_batched(ctypes.byref(model.raw), offs.ctypes.data_as(ctypes.c_void_p), B, _ptr(t), _ptr(y),
                                  _ptr(mask), n, _ptr(theta), _ptr(ll), _ptr(it), ctypes.byref(o), _ptr(ws),

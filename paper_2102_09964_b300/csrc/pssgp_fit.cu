@@ -23,7 +23,7 @@ int64_t align256(int64_t x) { return (x + 255) / 256 * 256; }
 
 struct FitLayout {
   int64_t o_gws, gws_bytes, o_t, o_y, o_mask, o_noff, o_ooff, o_idx, o_par, o_ll, o_g, o_m, o_v, o_llp, o_cnt,
-      o_done, total;
+      o_done, o_lb, total;
 };
 
 FitLayout fit_layout(int d, int64_t n, int B) {
@@ -46,6 +46,7 @@ FitLayout fit_layout(int d, int64_t n, int B) {
   L.o_llp = o; o += align256((int64_t)B * 8);          // previous log-likelihood
   L.o_cnt = o; o += align256((int64_t)B * 4);          // iterations in a row below tol
   L.o_done = o; o += align256((int64_t)B);
+  L.o_lb = o; o += align256((int64_t)B * 512);         // L-BFGS state per series
   L.total = o;
   return L;
 }
@@ -116,6 +117,151 @@ __global__ void k_fit_update(int Ba, const int* idx, const int64_t* ooff, const 
   ll_out[s] = l;
 }
 
+// ---------------------------------------------------------------------------
+// L-BFGS (limited-memory BFGS with an Armijo backtracking line search) per
+// series on f = -loglik, in the log hyperparameters.  Each loop iteration
+// evaluates every active series at its trial point; this kernel then either
+// accepts the trial (history update, convergence test, new direction by the
+// two-loop recursion, trial at step 1) or shortens the step.
+// ---------------------------------------------------------------------------
+constexpr int LB_M = 6;
+struct LbfgsState {
+  double tht[3];          // trial point
+  double g[3];            // gradient of f at the accepted point
+  double p[3];            // search direction
+  double S[LB_M][3], Y[LB_M][3], rho[LB_M];
+  double f, f0, alpha, gp0;
+  int nh, head, stage, pad;
+};
+
+static_assert(sizeof(LbfgsState) <= 512, "L-BFGS state slot");
+
+// trial parameters of the active series (the start point before the first
+// evaluation)
+__global__ void k_fit_params_lbfgs(int Ba, const int* idx, const double* theta, const LbfgsState* state,
+                                   double* par) {
+  const int j = blockIdx.x * FIT_BLOCK + threadIdx.x;
+  if (j >= Ba) return;
+  const int s = idx[j];
+  const LbfgsState& st = state[s];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) par[3 * j + c] = exp(st.stage ? st.tht[c] : theta[3 * s + c]);
+}
+
+__device__ void lb_direction(LbfgsState& st) {
+  double q[3] = {st.g[0], st.g[1], st.g[2]}, a[LB_M];
+  for (int c = 0; c < st.nh; ++c) {                  // newest to oldest
+    const int i = (st.head - 1 - c + LB_M) % LB_M;
+    a[i] = st.rho[i] * (st.S[i][0] * q[0] + st.S[i][1] * q[1] + st.S[i][2] * q[2]);
+    for (int k = 0; k < 3; ++k) q[k] -= a[i] * st.Y[i][k];
+  }
+  double gam = 0.0;
+  if (st.nh > 0) {
+    const int i = (st.head - 1 + LB_M) % LB_M;
+    const double yy = st.Y[i][0] * st.Y[i][0] + st.Y[i][1] * st.Y[i][1] + st.Y[i][2] * st.Y[i][2];
+    gam = 1.0 / (st.rho[i] * yy);                    // s^T y / y^T y
+  } else {
+    const double gi = fmax(fabs(st.g[0]), fmax(fabs(st.g[1]), fabs(st.g[2])));
+    gam = gi > 0.0 ? 0.5 / gi : 1.0;                 // first step: at most 0.5 in every log parameter
+  }
+  for (int k = 0; k < 3; ++k) q[k] *= gam;
+  for (int c = st.nh - 1; c >= 0; --c) {             // oldest to newest
+    const int i = (st.head - 1 - c + LB_M) % LB_M;
+    const double b = st.rho[i] * (st.Y[i][0] * q[0] + st.Y[i][1] * q[1] + st.Y[i][2] * q[2]);
+    for (int k = 0; k < 3; ++k) q[k] += st.S[i][k] * (a[i] - b);
+  }
+  for (int k = 0; k < 3; ++k) st.p[k] = -q[k];
+  double gp = st.g[0] * st.p[0] + st.g[1] * st.p[1] + st.g[2] * st.p[2];
+  if (!(gp < 0.0)) {                                 // not a descent direction: restart
+    st.nh = 0;
+    st.head = 0;
+    const double gi = fmax(fabs(st.g[0]), fmax(fabs(st.g[1]), fabs(st.g[2])));
+    for (int k = 0; k < 3; ++k) st.p[k] = gi > 0.0 ? -0.5 * st.g[k] / gi : 0.0;
+  }
+  const double pm = fmax(fabs(st.p[0]), fmax(fabs(st.p[1]), fabs(st.p[2])));
+  if (pm > 2.0)                                      // at most a factor e^2 per step
+    for (int k = 0; k < 3; ++k) st.p[k] *= 2.0 / pm;
+}
+
+__global__ void k_fit_lbfgs(int Ba, const int* idx, const int64_t* ooff, const double* ll, const double* g,
+                            double* theta, LbfgsState* state, int* cnt, uint8_t* done, int32_t* iters,
+                            double* ll_out, double* par, int it, pssgp_fit_options o) {
+  const int j = blockIdx.x * FIT_BLOCK + threadIdx.x;
+  if (j >= Ba) return;
+  const int s = idx[j];
+  if (done[s]) return;
+  LbfgsState st = state[s];
+  const double ns = fmax((double)(ooff[s + 1] - ooff[s]), 1.0);
+  const double ft = -ll[j];
+  const double gt[3] = {-g[3 * j], -g[3 * j + 1], -g[3 * j + 2]};
+  const bool fin = isfinite(ft) && isfinite(gt[0]) && isfinite(gt[1]) && isfinite(gt[2]);
+  iters[s] = it + 1;
+  bool finish = false;
+  if (st.stage == 0) {                               // first evaluation, at the start point
+    if (!fin) { done[s] = 2; ll_out[s] = ll[j]; return; }
+    for (int k = 0; k < 3; ++k) { st.tht[k] = theta[3 * s + k]; st.g[k] = gt[k]; }
+    st.f = ft;
+    st.nh = 0;
+    st.head = 0;
+    lb_direction(st);
+  } else if (fin && ft <= st.f0 + 1e-4 * st.alpha * st.gp0) {   // Armijo: accept
+    double sv[3], yv[3], sy = 0.0, ss = 0.0, yy = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      sv[k] = st.tht[k] - theta[3 * s + k];
+      yv[k] = gt[k] - st.g[k];
+      sy += sv[k] * yv[k]; ss += sv[k] * sv[k]; yy += yv[k] * yv[k];
+    }
+    if (sy > 1e-12 * sqrt(ss * yy)) {
+      const int h = st.head;
+      for (int k = 0; k < 3; ++k) { st.S[h][k] = sv[k]; st.Y[h][k] = yv[k]; }
+      st.rho[h] = 1.0 / sy;
+      st.head = (h + 1) % LB_M;
+      st.nh = min(st.nh + 1, LB_M);
+    }
+    int c = cnt[s];
+    c = (fabs(ft - st.f) / ns < o.tol) ? c + 1 : 0;
+    cnt[s] = c;
+    for (int k = 0; k < 3; ++k) { theta[3 * s + k] = st.tht[k]; st.g[k] = gt[k]; }
+    st.f = ft;
+    if (c >= o.patience) finish = true;
+    else lb_direction(st);
+  } else {                                           // reject: shorter step
+    const double a = st.alpha;
+    double an = 0.5 * a;
+    if (fin) {                                       // minimiser of the quadratic through f0, gp0, ft
+      const double den = 2.0 * (ft - st.f0 - st.gp0 * a);
+      if (den > 0.0) an = fmin(fmax(-st.gp0 * a * a / den, 0.1 * a), 0.5 * a);
+    }
+    if (an < 1e-10) {
+      if (st.nh > 0) { st.nh = 0; st.head = 0; lb_direction(st); }   // retry along the gradient
+      else finish = true;
+    } else {
+      st.alpha = an;
+      for (int k = 0; k < 3; ++k) st.tht[k] = theta[3 * s + k] + an * st.p[k];
+      for (int k = 0; k < 3; ++k) par[3 * j + k] = exp(st.tht[k]);
+      if (it + 1 >= o.max_iter) finish = true;
+      if (!finish) { state[s] = st; ll_out[s] = -st.f; return; }
+    }
+  }
+  if (finish || it + 1 >= o.max_iter) {
+    done[s] = 1;
+    ll_out[s] = -st.f;
+    state[s] = st;
+    return;
+  }
+  // new line search along p from the accepted point
+  st.stage = 1;
+  st.alpha = 1.0;
+  st.f0 = st.f;
+  st.gp0 = st.g[0] * st.p[0] + st.g[1] * st.p[1] + st.g[2] * st.p[2];
+  for (int k = 0; k < 3; ++k) {
+    st.tht[k] = theta[3 * s + k] + st.p[k];
+    par[3 * j + k] = exp(st.tht[k]);
+  }
+  state[s] = st;
+  ll_out[s] = -st.f;
+}
+
 }  // namespace
 
 extern "C" size_t pssgp_fit_workspace_size(int32_t d, int64_t n, int32_t B) {
@@ -129,7 +275,8 @@ extern "C" int pssgp_fit_batched(const pssgp_model* model, const int64_t* offset
                                  void* stream, int32_t* iterations_run) {
   if (!model || !offsets_host || !t || !y || !mask || !theta || !loglik || !iters || !opt || !ws || B < 1 || n < 1)
     return PSSGP_EINVAL;
-  if (opt->max_iter < 1 || opt->patience < 1 || opt->check_every < 1 || !(opt->lr > 0.0) || !(opt->tol >= 0.0))
+  if (opt->max_iter < 1 || opt->patience < 1 || opt->check_every < 1 || !(opt->lr > 0.0) || !(opt->tol >= 0.0) ||
+      (opt->method != PSSGP_FIT_ADAM && opt->method != PSSGP_FIT_LBFGS))
     return PSSGP_EINVAL;
   if (offsets_host[0] != 0 || offsets_host[B] != n) return PSSGP_EINVAL;
   for (int s = 0; s < B; ++s)
@@ -153,12 +300,14 @@ extern "C" int pssgp_fit_batched(const pssgp_model* model, const int64_t* offset
   double* llp = reinterpret_cast<double*>(w + L.o_llp);
   int* cnt = reinterpret_cast<int*>(w + L.o_cnt);
   uint8_t* done = reinterpret_cast<uint8_t*>(w + L.o_done);
+  LbfgsState* lbs = reinterpret_cast<LbfgsState*>(w + L.o_lb);
+  const bool lbfgs = opt->method == PSSGP_FIT_LBFGS;
 
   auto ok = [](cudaError_t e) { return e == cudaSuccess; };
   if (!ok(cudaMemcpyAsync(ooff, offsets_host, (size_t)(B + 1) * 8, cudaMemcpyHostToDevice, s)) ||
       !ok(cudaMemsetAsync(m1, 0, (size_t)B * 24, s)) || !ok(cudaMemsetAsync(m2, 0, (size_t)B * 24, s)) ||
       !ok(cudaMemsetAsync(cnt, 0, (size_t)B * 4, s)) || !ok(cudaMemsetAsync(iters, 0, (size_t)B * 4, s)) ||
-      !ok(cudaMemsetAsync(loglik, 0, (size_t)B * 8, s)))
+      !ok(cudaMemsetAsync(loglik, 0, (size_t)B * 8, s)) || !ok(cudaMemsetAsync(lbs, 0, (size_t)B * 512, s)))
     return PSSGP_ECUDA;
   // empty series are done from the start (log-likelihood 0, no iterations)
   std::vector<uint8_t> hdone(B);
@@ -189,7 +338,10 @@ extern "C" int pssgp_fit_batched(const pssgp_model* model, const int64_t* offset
     k_fit_gather<<<(unsigned)((n_new + FIT_BLOCK - 1) / FIT_BLOCK), FIT_BLOCK, 0, s>>>(n_new, noff, Ba, idx, ooff,
                                                                                        t, y, mask, tc, yc, mc);
     if (!ok(cudaGetLastError())) return PSSGP_ECUDA;
-    k_fit_params<<<(unsigned)((Ba + FIT_BLOCK - 1) / FIT_BLOCK), FIT_BLOCK, 0, s>>>(Ba, idx, theta, par);
+    if (lbfgs)
+      k_fit_params_lbfgs<<<(unsigned)((Ba + FIT_BLOCK - 1) / FIT_BLOCK), FIT_BLOCK, 0, s>>>(Ba, idx, theta, lbs, par);
+    else
+      k_fit_params<<<(unsigned)((Ba + FIT_BLOCK - 1) / FIT_BLOCK), FIT_BLOCK, 0, s>>>(Ba, idx, theta, par);
     return ok(cudaGetLastError()) ? PSSGP_OK : PSSGP_ECUDA;
   };
   int rc = compact();
@@ -198,8 +350,12 @@ extern "C" int pssgp_fit_batched(const pssgp_model* model, const int64_t* offset
   for (; it < opt->max_iter && Ba > 0; ++it) {
     rc = pssgp_loglik_grad_batched(model, noff, Ba, par, tc, yc, mc, n_new, ll, g, gws, (size_t)L.gws_bytes, stream);
     if (rc) return rc;
-    k_fit_update<<<(unsigned)((Ba + FIT_BLOCK - 1) / FIT_BLOCK), FIT_BLOCK, 0, s>>>(
-        Ba, idx, ooff, ll, g, theta, m1, m2, llp, cnt, done, iters, loglik, par, it, *opt);
+    if (lbfgs)
+      k_fit_lbfgs<<<(unsigned)((Ba + FIT_BLOCK - 1) / FIT_BLOCK), FIT_BLOCK, 0, s>>>(
+          Ba, idx, ooff, ll, g, theta, lbs, cnt, done, iters, loglik, par, it, *opt);
+    else
+      k_fit_update<<<(unsigned)((Ba + FIT_BLOCK - 1) / FIT_BLOCK), FIT_BLOCK, 0, s>>>(
+          Ba, idx, ooff, ll, g, theta, m1, m2, llp, cnt, done, iters, loglik, par, it, *opt);
     if (!ok(cudaGetLastError())) return PSSGP_ECUDA;
     if ((it + 1) % opt->check_every == 0 || it + 1 == opt->max_iter) {
       std::vector<uint8_t> now(B);

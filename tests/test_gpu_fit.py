@@ -83,3 +83,32 @@ def test_fit_options_are_checked():
     bt = wl.series_batch(seed=43, lengths=[100, 200])
     with pytest.raises(P.PssgpError):
         run_fit("matern32", bt, np.zeros((2, 3)), max_iter=0)
+
+
+def test_lbfgs_reaches_the_cpu_optimum_in_fewer_evaluations_than_adam():
+    bt = wl.series_batch(seed=44, lengths=[1500, 0, 800, 2500, 1, 4000])
+    th0 = np.zeros((bt.B, 3))
+    th, ll, it, _ = run_fit("matern52", bt, th0, max_iter=500, patience=3, tol=1e-10, method="lbfgs",
+                            check_every=5)
+    tha, lla, ita, _ = run_fit("matern52", bt, th0, max_iter=3000)
+    assert it[1] == 0 and ll[1] == 0.0
+    for s in (0, 2, 3, 5):
+        a, b = bt.offsets[s], bt.offsets[s + 1]
+        t, y = bt.t[a:b], bt.y[a:b]
+        ref = oracle.loglik_at("matern52", np.exp(th[s, 0]), np.exp(th[s, 1]), t, y, np.ones(b - a, np.uint8),
+                               np.exp(th[s, 2]))
+        assert abs(ll[s] - ref) <= 1e-9 * max(abs(ref), b - a)
+        _, best = cpu_fit("matern52", t, y, th0[s])
+        assert ll[s] >= best - 1e-6 * (b - a), (s, ll[s], best)
+    assert it[[0, 2, 3, 5]].sum() < ita[[0, 2, 3, 5]].sum()
+
+
+def test_lbfgs_single_series_stand_in():
+    """One long series (the shape of the paper's L-BFGS learning loop)."""
+    s = wl.sinusoid_large(N=3200, M=0, T=270.0)
+    bt = wl.Batch(s.t_train, s.y_train, np.array([0, 3200]), ["matern32"], np.ones(1), np.ones(1), np.ones(1))
+    th, ll, it, nrun = run_fit("matern32", bt, np.zeros((1, 3)), max_iter=300, patience=3, tol=1e-12,
+                               method="lbfgs", check_every=10)
+    _, best = cpu_fit("matern32", s.t_train, s.y_train, np.zeros(3))
+    assert ll[0] >= best - 1e-6 * 3200
+    assert it[0] < 100
