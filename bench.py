@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--timing-steps", type=int, default=3)
     ap.add_argument("--warps-per-sm", type=int, default=0, help="scan lanes per SM / 32 (0 = library default)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 4,096-series batched measurement")
+    ap.add_argument("--no-fit", action="store_true", help="skip the learned-vs-plain fit and Table-1 measurements")
+    ap.add_argument("--fit-adam", action="store_true", help="also time the Adam fits (about a minute)")
     ap.add_argument("--n-train", type=int, default=0,
                     help="profile a prefix of the workload with this many training points (0 = full 2^20)")
     return ap.parse_args()
@@ -311,6 +313,87 @@ def batched_bench(args, P, wl, dev, barrier, world, rank):
             "l2": "inputs and workspace ~17 GB per evaluation, far above the 126 MB L2"}
 
 
+def fit_bench(args, P, wl):
+    """Learned initialisation (row f3): train the network on 10^6 simulated
+    Matern-5/2 prior series of 4,096 steps, then fit 4,096 held-out prior
+    series (lengths log-uniform in [4096, 65536]) from the plain default and
+    from the network's proposals with the same optimiser; series per second
+    of the whole fit (device wall clock) and the share of learned-init fits
+    within 1e-3 nats per point of the plain fit's log-likelihood."""
+    import torch
+    from paper_2102_09964_b300 import learn as L
+    m = P.build_model("matern52", 1.0, 1.0)
+    offs, params = wl.prior_spec(wl.LEARN_TRAIN["seed"], wl.LEARN_TRAIN["B"], n=wl.LEARN_TRAIN["n"])
+    net, train_s, losses = L.train_network(m, offs, params, seed=500, epochs=8)
+    ho, hp = wl.prior_spec(**wl.LEARN_HELDOUT)
+    t, y = L.heldout_series(m, ho, hp, seed=510)
+    out = {"workload": "train: 10^6 Matern-5/2 prior series x 4,096 steps (Poisson grid, mean spacing 0.01), "
+                       "l, s2 log-uniform [0.1, 10], R log-uniform [1e-3, 1e-1]; held-out: 4,096 prior series, "
+                       "lengths log-uniform [4096, 65536]; plain init l = s2 = R = 1",
+           "train_s": round(train_s, 3), "train_loss_final": float(losses[-64:].mean().item()),
+           "heldout_steps": int(ho[-1])}
+    runs = [("lbfgs", dict(method="lbfgs", patience=3, tol=1e-9, max_iter=500, check_every=5))]
+    if args.fit_adam:
+        runs.append(("adam", dict(method="adam", patience=10, tol=1e-7, max_iter=2000, check_every=25)))
+    for name, kw in runs:
+        r = L.compare_fits(net, m, ho, t, y, **kw)
+        out[name] = {"plain": r["plain"], "learned": r["learned"],
+                     "speedup": round(r["plain"]["gpu_s"] / r["learned"]["gpu_s"], 3),
+                     "learned_within_1e-3_nats_per_point": r["learned_within_1e-3_nats_per_point"],
+                     "options": kw}
+    del t, y
+    torch.cuda.empty_cache()
+    return out
+
+
+def table1_bench(P, wl):
+    """The paper's learning loop (Sec. 5.2, Table 1) on a shape-only stand-in:
+    L-BFGS on the log-likelihood of N = 1200 / 2200 / 3200 monthly points
+    (Matern-3/2, start l = s2 = R = 1), milliseconds per function/gradient
+    evaluation; then the daily interpolation at 96,000 prediction times."""
+    import time
+    import torch
+    s = wl.sunspot_like()
+    out = {"workload": "sunspot-shaped synthetic series (no sunspot data): monthly training times, 96,000 daily "
+                       "prediction times, Matern-3/2", "paper_ms_per_eval": {"1200": 39, "2200": 46, "3200": 48},
+           "paper_interpolation_s": 0.14, "paper_hardware": "as stated in the paper (context only)"}
+    m = P.build_model("matern32", 1.0, 1.0)
+    best = None
+    for N in (1200, 2200, 3200):
+        t = torch.as_tensor(s.t_train[:N], device="cuda")
+        y = torch.as_tensor(s.y_train[:N], device="cuda")
+        mask = torch.ones(N, dtype=torch.uint8, device="cuda")
+        P.fit_batched(m, np.array([0, N]), t, y, mask, np.zeros((1, 3)), method="lbfgs", max_iter=20)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        th, ll, it, _ = P.fit_batched(m, np.array([0, N]), t, y, mask, np.zeros((1, 3)), method="lbfgs",
+                                      patience=3, tol=1e-12, max_iter=500, check_every=10)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ev = int(it[0].item())
+        out[f"N{N}"] = {"evaluations": ev, "fit_s": round(dt, 5), "ms_per_eval": round(1e3 * dt / max(ev, 1), 4),
+                        "loglik": float(ll[0].item())}
+        best = th[0].cpu().numpy()
+    ell, s2, R = np.exp(best)
+    mf = P.build_model("matern32", float(ell), float(s2))
+    tt = torch.as_tensor(s.t_train, device="cuda")
+    yy = torch.as_tensor(s.y_train, device="cuda")
+    ts = torch.as_tensor(s.t_test, device="cuda")
+    ws = P.workspace(mf.d, tt.numel() + ts.numel(), torch.device("cuda"))
+    for _ in range(3):
+        P.predict(mf, tt, yy, ts, float(R), ws=ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        P.predict(mf, tt, yy, ts, float(R), ws=ws)
+    e1.record()
+    e1.synchronize()
+    out["interpolation_s"] = round(e0.elapsed_time(e1) / 10 / 1e3, 6)
+    out["fitted"] = {"lengthscale": float(ell), "variance": float(s2), "noise": float(R)}
+    return out
+
+
 def run_ours(args, wl_params):
     import torch
     import paper_2102_09964_b300 as P
@@ -470,6 +553,9 @@ def run_ours(args, wl_params):
             "whole_path_tflops": round(whole, 4), "kernels": kernels}
     if not args.no_batched:
         line["batched"] = batched_bench(args, P, wl, dev, barrier, world, rank)
+    if not args.no_fit:
+        line["fit"] = fit_bench(args, P, wl)
+        line["table1"] = table1_bench(P, wl)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl_params)
     if rank == 0:

@@ -556,13 +556,22 @@ __global__ void k_colstats(const T* X, int64_t M, int ld, float* mean, float* sd
   }
 }
 
-// network outputs to log hyperparameters
+// network outputs to log hyperparameters; a row with a non-finite output or
+// one more than 4 standard deviations of the training targets from their
+// mean falls back to the plain default 0 (l = s2 = R = 1) in all three
 __global__ void k_mlp_decode(const float* Out, int64_t M, const float* norm, double* theta) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M * 3) return;
-  const int64_t r = i / 3;
-  const int o = (int)(i % 3);
-  theta[i] = (double)Out[r * NOUT + o] * (double)norm[2 * NFEAT + 3 + o] + (double)norm[2 * NFEAT + o];
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= M) return;
+  double th[3];
+  bool ok = true;
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    const float z = Out[r * NOUT + o];
+    ok = ok && isfinite(z) && fabsf(z) <= 4.0f;
+    th[o] = (double)z * (double)norm[2 * NFEAT + 3 + o] + (double)norm[2 * NFEAT + o];
+  }
+#pragma unroll
+  for (int o = 0; o < 3; ++o) theta[r * 3 + o] = ok ? th[o] : 0.0;
 }
 
 }  // namespace
@@ -706,6 +715,6 @@ extern "C" int pssgp_mlp_predict(const void* state, const float* feat, int32_t r
   (void)cudaGetLastError();
   const Net n = net_of(const_cast<void*>(state));
   forward(n, a, feat, rows, s);
-  k_mlp_decode<<<blocks((int64_t)rows * 3, 256), 256, 0, s>>>(a.Out, rows, n.norm, theta);
+  k_mlp_decode<<<blocks(rows, 256), 256, 0, s>>>(a.Out, rows, n.norm, theta);
   return rc_of(cudaGetLastError());
 }

@@ -13,7 +13,7 @@ import time
 import numpy as np
 import torch
 
-from . import MLP, NFEAT, build_model, features, fit_batched, simulate_prior
+from . import MLP, NFEAT, features, fit_batched, simulate_prior
 
 
 def prior_features(model, offsets: np.ndarray, params: np.ndarray, seed: int, chunk: int = 65_536,
@@ -47,23 +47,22 @@ def train_network(model, offsets, params, seed: int, epochs: int = 8, batch: int
     return net, time.perf_counter() - t0, losses
 
 
-def compare_fits(net, model, offsets: np.ndarray, t, y, max_iter: int = 2000, tol: float = 1e-7,
-                 lr: float = 0.05):
+def compare_fits(net, model, offsets: np.ndarray, t, y, **fit_kw):
     """Plain-init and learned-init fits of the same series.  Times are device
     wall-clock around each fit (the learned one includes its features and
-    the network's forward pass).  Returns a dict of results."""
+    the network's forward pass).  fit_kw: options of fit_batched (the same
+    for both fits).  Returns a dict of results."""
     B = offsets.size - 1
     dev = t.device
     mask = torch.ones(t.numel(), dtype=torch.uint8, device=dev)
     off = torch.as_tensor(offsets, dtype=torch.int64, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    th_p, ll_p, it_p, n_p = fit_batched(model, offsets, t, y, mask, np.zeros((B, 3)), max_iter=max_iter, tol=tol,
-                                        lr=lr)
+    th_p, ll_p, it_p, n_p = fit_batched(model, offsets, t, y, mask, np.zeros((B, 3)), **fit_kw)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     init = net.predict(features(off, t, y))
-    th_l, ll_l, it_l, n_l = fit_batched(model, offsets, t, y, mask, init, max_iter=max_iter, tol=tol, lr=lr)
+    th_l, ll_l, it_l, n_l = fit_batched(model, offsets, t, y, mask, init, **fit_kw)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     n = np.diff(offsets).astype(np.float64)

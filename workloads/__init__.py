@@ -173,3 +173,18 @@ def prior_spec(seed: int, B: int, n: int | None = None, n_min: int | None = None
 # 0.01 (a Poisson time grid), log-uniform hyperparameters.
 LEARN_TRAIN = dict(seed=50, B=1_000_000, n=4096)
 LEARN_HELDOUT = dict(seed=51, B=4096, n_min=4096, n_max=65536)
+
+
+def sunspot_like(seed: int = 7, N: int = 3200, M: int = 96_000) -> Series:
+    """Shape-only stand-in for the paper's monthly sunspot series (Sec. 5.2:
+    N = 3,200 monthly training points, 96,000 daily prediction times): times
+    in years, monthly training times (k + 1/2) / 12, daily prediction times
+    (j + 1/2) / 365.25, and an 11-year quasi-periodic non-negative signal
+    80 |sin(pi t / 11)|^1.5 (1 + 0.3 sin(2 pi t / 90)) with N(0, 15^2) noise.
+    No sunspot data is reproduced."""
+    rng = np.random.default_rng(seed)
+    t = (np.arange(N) + 0.5) / 12.0
+    sig = 80.0 * np.abs(np.sin(np.pi * t / 11.0)) ** 1.5 * (1.0 + 0.3 * np.sin(2.0 * np.pi * t / 90.0))
+    y = sig + rng.normal(0.0, 15.0, N)
+    ts = (np.arange(M) + 0.5) / 365.25
+    return Series(t, y, ts)
