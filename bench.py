@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 4,096-series batched measurement")
     ap.add_argument("--no-fit", action="store_true", help="skip the learned-vs-plain fit and Table-1 measurements")
     ap.add_argument("--fit-adam", action="store_true", help="also time the Adam fits (about a minute)")
+    ap.add_argument("--profile", default="", choices=["", "grad", "batched", "batched_grad", "learn"],
+                    help="run one small case 3 times for a profiler and exit (no JSON line)")
     ap.add_argument("--n-train", type=int, default=0,
                     help="profile a prefix of the workload with this many training points (0 = full 2^20)")
     return ap.parse_args()
@@ -566,8 +568,58 @@ def run_ours(args, wl_params):
     return 0
 
 
+def profile_case(args):
+    """Small cases for ncu captures (inputs larger than L2, a few GB at most):
+    grad: log-likelihood + gradient of RBF-6 on 2^18 training points;
+    batched / batched_grad: log-likelihood (+ gradient) of 256 Matern-5/2
+    series of the batched workload's length range; learn: prior simulation and
+    features of 16,384 series x 4,096 steps and 8 training steps."""
+    import torch
+    import paper_2102_09964_b300 as P
+    import workloads as wl
+    from paper_2102_09964_b300 import build as B
+    torch.cuda.set_device(0)
+    B.build()
+    dev = torch.device("cuda", 0)
+    if args.profile == "grad":
+        s = wl.prefix(wl.sinusoid_large(), 1 << 18)
+        m = P.build_model("rbf", 1.0, 1.0)
+        t = torch.as_tensor(s.t_train, device=dev)
+        y = torch.as_tensor(s.y_train, device=dev)
+        mask = torch.ones(t.numel(), dtype=torch.uint8, device=dev)
+        ws = P.workspace_grad(m.d, t.numel(), dev)
+        for _ in range(3):
+            P.loglik_grad(m, t, y, mask, 0.01, ws=ws)
+    elif args.profile in ("batched", "batched_grad"):
+        bt = wl.series_batch(seed=3, B=256)
+        m = P.build_model("matern52", 1.0, 1.0)
+        a = (torch.as_tensor(bt.offsets, device=dev), torch.as_tensor(bt.params(), device=dev),
+             torch.as_tensor(bt.t, device=dev), torch.as_tensor(bt.y, device=dev),
+             torch.ones(bt.t.size, dtype=torch.uint8, device=dev))
+        ws = (P.workspace_grad if args.profile == "batched_grad" else P.workspace)(m.d, bt.t.size, dev)
+        for _ in range(3):
+            if args.profile == "batched":
+                P.loglik_batched(m, *a, ws=ws)
+            else:
+                P.loglik_grad_batched(m, *a, ws=ws)
+    else:
+        from paper_2102_09964_b300 import learn as L
+        m = P.build_model("matern52", 1.0, 1.0)
+        offs, params = wl.prior_spec(50, 16_384, n=4096)
+        for _ in range(3):
+            feat = L.prior_features(m, offs, params, seed=500)
+        net = P.MLP(dev)
+        th = torch.as_tensor(np.log(params), device=dev)
+        net.init(1, feat, th)
+        net.train(feat, th, epochs=1, batch=2048)
+    torch.cuda.synchronize()
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile:
+        return profile_case(args)
     wl_params = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl_params)

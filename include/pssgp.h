@@ -411,7 +411,7 @@ int pssgp_simulate_prior(const pssgp_model* model, const int64_t* offsets,
  * A at w_lo r^(j + (q - 3/2) / 4), q < 4, r = (w_hi / w_lo)^(1/63),
  * w_lo = 2 pi / 40.96, w_hi = 0.9 pi / 0.01; zeros for a series with fewer
  * than 2 steps or s2 = 0.  Computed in FP32 (phase re-anchored from FP64
- * every 32 steps). */
+ * every 128 steps). */
 int pssgp_features(const int64_t* offsets, int32_t B, const double* t,
                    const double* y, float* feat, void* stream);
 

@@ -386,19 +386,23 @@ __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_batched(const DevMode
   flag(status, bits);
 }
 
-// one warp per series: fixed-order sum of the per-step log-likelihood pieces
-__global__ void __launch_bounds__(BLOCK) k_segment_sum(const double* v, int64_t n, const int64_t* offsets, int B,
-                                                           double* out, int ostride) {
-  const int s = (int)((int64_t)blockIdx.x * (BLOCK / 32) + (threadIdx.x >> 5));
-  const int lane = threadIdx.x & 31;
+// per-series sums of pieces written at the first step of every (lane chunk,
+// series) pair: for series [a, b) the positions a and every chunk start g L
+// in (a, b), summed in that order (deterministic); nothing else of v is read.
+// nv arrays of stride n at once, out[s * ostride + i] for array i.
+__global__ void __launch_bounds__(128) k_segment_pieces(const double* v, int nv, int64_t n, int64_t L,
+                                                       const int64_t* offsets, int B, double* out, int ostride) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B) return;
   const int64_t a = min(max(offsets[s], (int64_t)0), n);     // clamped: bad offsets are
   const int64_t b = min(max(offsets[s + 1], a), n);           // flagged by k_discretize_batched
-  double acc = 0.0;
-  for (int64_t k = a + lane; k < b; k += 32) acc += v[k];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) out[(int64_t)s * ostride] = acc;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  if (b > a) {
+    for (int i = 0; i < nv; ++i) acc[i] = v[(int64_t)i * n + a];
+    for (int64_t k = (a / L + 1) * L; k < b; k += L)
+      for (int i = 0; i < nv; ++i) acc[i] += v[(int64_t)i * n + k];
+  }
+  for (int i = 0; i < nv; ++i) out[(int64_t)s * ostride + i] = acc[i];
 }
 
 // shared memory of k_filter_reduce: A (two buffers), J (packed) and eta per
@@ -575,7 +579,6 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
         qsum = 0.0;
         lp = LogProd();
       }
-      a.ll_step[k] = 0.0;
     }
     Mat<D> F, Q, T, Pm;
     Vec<D> xm;
@@ -1097,12 +1100,11 @@ __global__ void __launch_bounds__(BLOCK, 1) k_adjoint_cov(const DevModel<D> m, c
         }
       gl = fma(-tau, fma(2.0, t2, fma(q, t3, t1)), gl);
     }
-    if (a.g_step) {   // batched: one piece per (chunk, series), at its first step in the chunk
-      const bool flush = (k == k0) || a.seg_start[k];
-      a.g_step[k] = flush ? gl : 0.0;
-      a.g_step[a.n + k] = flush ? gs : 0.0;
-      a.g_step[2 * a.n + k] = flush ? gr : 0.0;
-      if (flush) { gl = 0.0; gs = 0.0; gr = 0.0; }
+    if (a.g_step && ((k == k0) || a.seg_start[k])) {   // batched: one piece per (chunk, series),
+      a.g_step[k] = gl;                                   // at its first step in the chunk
+      a.g_step[a.n + k] = gs;
+      a.g_step[2 * a.n + k] = gr;
+      gl = 0.0; gs = 0.0; gr = 0.0;
     }
   }
   if (!a.g_step) {
@@ -1535,7 +1537,7 @@ extern "C" int pssgp_loglik_batched(const pssgp_model* model, const int64_t* off
   });
   {
     Timed tm(s, T_LL);
-    k_segment_sum<<<(unsigned)((B + BLOCK / 32 - 1) / (BLOCK / 32)), BLOCK, 0, s>>>(a.ll_step, n, offsets, B, loglik, 1);
+    k_segment_pieces<<<(unsigned)((B + 127) / 128), 128, 0, s>>>(a.ll_step, 1, n, p.L, offsets, B, loglik, 1);
     after_launch();
   }
   return end_call();
@@ -1605,15 +1607,13 @@ extern "C" int pssgp_loglik_grad_batched(const pssgp_model* model, const int64_t
   });
   {
     Timed tm(s, T_LL);
-    const unsigned sg = (unsigned)((B + BLOCK / 32 - 1) / (BLOCK / 32));
+    const unsigned sg = (unsigned)((B + 127) / 128);
     if (loglik) {
-      k_segment_sum<<<sg, BLOCK, 0, s>>>(a.ll_step, n, offsets, B, loglik, 1);
+      k_segment_pieces<<<sg, 128, 0, s>>>(a.ll_step, 1, n, p.L, offsets, B, loglik, 1);
       after_launch();
     }
-    for (int i = 0; i < 3; ++i) {
-      k_segment_sum<<<sg, BLOCK, 0, s>>>(a.g_step + i * n, n, offsets, B, grad + i, 3);
-      after_launch();
-    }
+    k_segment_pieces<<<sg, 128, 0, s>>>(a.g_step, 3, n, p.L, offsets, B, grad, 3);
+    after_launch();
   }
   return end_call();
 }

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(128) k_simulate_prior(const DevModel<D> m, dou
 // One warp per series; lane l owns bins l and l + 32 (8 sub-frequencies).
 // On the regular grid the phase factor advances by a constant rotation per
 // step (FP32 complex multiply) and is re-anchored from the FP64 phase
-// w dbar k (reduced mod 2 pi) every 32 steps.  The sums run in FP32.
+// w dbar k (reduced mod 2 pi) every 128 steps.  The sums run in FP32.
 // ---------------------------------------------------------------------------
 constexpr int NFEAT = 65;
 constexpr int NFREQ = 64;
@@ -213,26 +213,33 @@ __global__ void __launch_bounds__(128) k_features(const int64_t* offsets, int B,
     rr[f] = (float)cs; ri[f] = (float)-sn;      // exp(-i wd)
     zr[f] = 1.f; zi[f] = 0.f; sr[f] = 0.f; si[f] = 0.f;
   }
+  // each lane converts one value per 32 steps; the warp reads them back by
+  // shuffles (the FP64 work is one subtraction and one conversion per step)
 #pragma unroll 1
-  for (int64_t k = 0; k < n; ++k) {
-    const float yc = (float)(y[a + k] - ybar);
-    if ((k & 31) == 0 && k > 0) {
+  for (int64_t k0 = 0; k0 < n; k0 += 32) {
+    const float ycl = (k0 + lane < n) ? (float)(y[a + k0 + lane] - ybar) : 0.f;
+    if ((k0 & 127) == 0 && k0 > 0) {           // re-anchor from the FP64 phase
 #pragma unroll
       for (int f = 0; f < 8; ++f) {
-        double p = wd[f] * (double)k;
+        double p = wd[f] * (double)k0;
         p = fma(-twopi, rint(p * inv2pi), p);
         float sn, cs;
         sincosf((float)p, &sn, &cs);
         zr[f] = cs; zi[f] = -sn;
       }
     }
+    const int cnt = (int)min((int64_t)32, n - k0);
+#pragma unroll 1
+    for (int j = 0; j < cnt; ++j) {
+      const float yc = __shfl_sync(0xffffffffu, ycl, j);
 #pragma unroll
-    for (int f = 0; f < 8; ++f) {
-      sr[f] = fmaf(yc, zr[f], sr[f]);
-      si[f] = fmaf(yc, zi[f], si[f]);
-      const float r2 = zr[f] * rr[f] - zi[f] * ri[f];
-      const float i2 = zr[f] * ri[f] + zi[f] * rr[f];
-      zr[f] = r2; zi[f] = i2;
+      for (int f = 0; f < 8; ++f) {
+        sr[f] = fmaf(yc, zr[f], sr[f]);
+        si[f] = fmaf(yc, zi[f], si[f]);
+        const float r2 = zr[f] * rr[f] - zi[f] * ri[f];
+        const float i2 = zr[f] * ri[f] + zi[f] * rr[f];
+        zr[f] = r2; zi[f] = i2;
+      }
     }
   }
   const double den = 4.0 * (double)n * s2;

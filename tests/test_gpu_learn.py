@@ -6,8 +6,8 @@ an end-to-end check of what the trained network gains.
   coordinates, the device rescales one balanced unit model; the Cholesky
   factor is covariant under the positive diagonal change of coordinates, so
   y agrees up to rounding.
-* Features: FP32 sums on the device (phase re-anchored every 32 steps) against
-  float64 direct sums; |d log P_j| <= 2e-3 (FP32 rotation error over 32 steps
+* Features: FP32 sums on the device (phase re-anchored every 128 steps) against
+  float64 direct sums; |d log P_j| <= 2e-3 (FP32 rotation error over 128 steps
   relative to the sums), |d log s2| <= 1e-6 (features are stored in FP32).
 * Network: the oracle rounds to bfloat16 at the same points in float64; the
   device accumulates in FP32, so a value within the FP32/FP64 difference of a
