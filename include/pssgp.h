@@ -286,6 +286,20 @@ int pssgp_predict(const pssgp_model* model, const double* t_train,
                   int64_t M, double R, double* mean_test, double* var_test,
                   double* loglik, void* ws, size_t ws_bytes, void* stream);
 
+/* pssgp_predict from and to HOST memory: copies the inputs (host arrays
+ * t_train, y_train [N], t_test [M]) into staging after the workspace, runs
+ * pssgp_predict, and copies mean_test, var_test [M] and loglik (nullable,
+ * one double) back to host memory, all enqueued on `stream` (asynchronous:
+ * synchronise the stream before reading the outputs).  With page-locked host
+ * buffers the copies are truly asynchronous, so calls on two streams with two
+ * workspaces overlap one call's copies with another's kernels.  Workspace:
+ * pssgp_predict_host_workspace_size(d, N, M) bytes. */
+size_t pssgp_predict_host_workspace_size(int32_t d, int64_t N, int64_t M);
+int pssgp_predict_host(const pssgp_model* model, const double* t_train,
+                       const double* y_train, int64_t N, const double* t_test,
+                       int64_t M, double R, double* mean_test, double* var_test,
+                       double* loglik, void* ws, size_t ws_bytes, void* stream);
+
 /* ---- diagnostics ------------------------------------------------------- */
 /* Chunk aggregates of the filter's first scan level, for tests: runs the
  * filter on (t, y, mask, R) with `lanes` lanes (a multiple of 128, 0 =

@@ -99,6 +99,10 @@ def lib():
         L.pssgp_loglik_grad_batched.argtypes = [ctypes.POINTER(PssgpModel), vp, i32, vp, vp, vp, vp, i64, vp, vp,
                                                 vp, sz, vp]
         L.pssgp_predict.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, i64, vp, i64, dp, vp, vp, vp, vp, sz, vp]
+        L.pssgp_predict_host.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, i64, vp, i64, dp, vp, vp, vp, vp, sz,
+                                         vp]
+        L.pssgp_predict_host_workspace_size.restype = sz
+        L.pssgp_predict_host_workspace_size.argtypes = [i32, i64, i64]
         L.pssgp_debug_filter_aggregates.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i64, i32,
                                                     vp, vp, ctypes.POINTER(i32), vp, sz, vp]
         L.pssgp_fp64_fma_rate.argtypes = [ctypes.POINTER(dp)]
@@ -409,6 +413,22 @@ def predict(model: Model, t_train, y_train, t_test, R: float, ws=None, out=None,
                              _stream())
     _check(rc, "pssgp_predict")
     return mean, var, ll, ws
+
+
+def predict_host(model: Model, t_train, y_train, t_test, R: float, out, ws=None, stream=None):
+    """pssgp_predict from and to host tensors (page-locked for overlap):
+    out = (mean[M], var[M], loglik[1]) host float64 tensors.  Asynchronous on
+    `stream` (default: the current stream); returns the workspace."""
+    N, M = t_train.numel(), t_test.numel()
+    if ws is None:
+        ws = torch.empty(int(lib().pssgp_predict_host_workspace_size(model.d, N, M)), dtype=torch.uint8,
+                         device="cuda")
+    st = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    mean, var, ll = out
+    rc = lib().pssgp_predict_host(ctypes.byref(model.raw), _ptr(t_train), _ptr(y_train), N, _ptr(t_test), M,
+                                  float(R), _ptr(mean), _ptr(var), _ptr(ll), _ptr(ws), ws.numel(), st)
+    _check(rc, "pssgp_predict_host")
+    return ws
 
 
 def debug_filter_aggregates(model: Model, t, y, mask, R, lanes: int = 0):

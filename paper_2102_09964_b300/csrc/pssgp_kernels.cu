@@ -1645,6 +1645,58 @@ extern "C" int pssgp_smooth(const pssgp_model* model, const double* t, const dou
   return end_call();
 }
 
+// host staging of pssgp_predict_host, after the regular workspace
+namespace {
+struct HostStage { int64_t o_tt, o_yy, o_ts, o_mean, o_var, o_ll, total; };
+HostStage host_stage(int d, int64_t N, int64_t M) {
+  HostStage h{};
+  int64_t o = (int64_t)pssgp_workspace_size(d, N + M);
+  auto take = [&o](int64_t bytes) { const int64_t r = o; o += (bytes + 255) / 256 * 256; return r; };
+  h.o_tt = take(N * 8); h.o_yy = take(N * 8); h.o_ts = take(M * 8);
+  h.o_mean = take(M * 8); h.o_var = take(M * 8); h.o_ll = take(8);
+  h.total = o;
+  return h;
+}
+}  // namespace
+
+extern "C" size_t pssgp_predict_host_workspace_size(int32_t d, int64_t N, int64_t M) {
+  if (d < 1 || d > PSSGP_DMAX || N < 1 || M < 0) return 0;
+  return (size_t)host_stage(d, N, M).total;
+}
+
+extern "C" int pssgp_predict(const pssgp_model* model, const double* t_train, const double* y_train, int64_t N,
+                             const double* t_test, int64_t M, double R, double* mean_test, double* var_test,
+                             double* loglik, void* ws, size_t ws_bytes, void* stream);
+
+extern "C" int pssgp_predict_host(const pssgp_model* model, const double* t_train, const double* y_train, int64_t N,
+                                  const double* t_test, int64_t M, double R, double* mean_test, double* var_test,
+                                  double* loglik, void* ws, size_t ws_bytes, void* stream) {
+  if (!model_ok(model) || !t_train || !y_train || N < 1 || M < 0 || !ws) return PSSGP_EINVAL;
+  if (M > 0 && (!t_test || !mean_test || !var_test)) return PSSGP_EINVAL;
+  const HostStage h = host_stage(model->d, N, M);
+  if ((int64_t)ws_bytes < h.total || (reinterpret_cast<uintptr_t>(ws) & 255) != 0) return PSSGP_EWORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  double* tt = reinterpret_cast<double*>(w + h.o_tt);
+  double* yy = reinterpret_cast<double*>(w + h.o_yy);
+  double* ts = reinterpret_cast<double*>(w + h.o_ts);
+  double* dm = reinterpret_cast<double*>(w + h.o_mean);
+  double* dv = reinterpret_cast<double*>(w + h.o_var);
+  double* dl = reinterpret_cast<double*>(w + h.o_ll);
+  if (cudaMemcpyAsync(tt, t_train, (size_t)N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(yy, y_train, (size_t)N * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      (M > 0 && cudaMemcpyAsync(ts, t_test, (size_t)M * 8, cudaMemcpyHostToDevice, s) != cudaSuccess))
+    return PSSGP_ECUDA;
+  const int rc = pssgp_predict(model, tt, yy, N, M > 0 ? ts : nullptr, M, R, M > 0 ? dm : nullptr,
+                               M > 0 ? dv : nullptr, loglik ? dl : nullptr, ws, (size_t)h.o_tt, stream);
+  if (rc) return rc;
+  if ((M > 0 && (cudaMemcpyAsync(mean_test, dm, (size_t)M * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                 cudaMemcpyAsync(var_test, dv, (size_t)M * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)) ||
+      (loglik && cudaMemcpyAsync(loglik, dl, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess))
+    return PSSGP_ECUDA;
+  return PSSGP_OK;
+}
+
 extern "C" int pssgp_predict(const pssgp_model* model, const double* t_train, const double* y_train, int64_t N,
                              const double* t_test, int64_t M, double R, double* mean_test, double* var_test,
                              double* loglik, void* ws, size_t ws_bytes, void* stream) {

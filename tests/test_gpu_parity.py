@@ -302,3 +302,21 @@ def test_user_sde_with_scaled_measurement_row():
     mean, var, ll, ws = P.predict(m, dev(s.t_train), dev(s.y_train), dev(s.t_test), 0.01)
     assert P.status(ws) == 0
     check_marginals(host(mean), host(var), float(host(ll)[0]), fm, fv, res.loglik, s.N, 1e-9, "H = 2 e0")
+
+
+def test_predict_from_host_buffers_equals_device_call():
+    """pssgp_predict_host (host inputs and outputs, copies inside the call) on
+    two streams gives the device call's results."""
+    s = wl.prefix(wl.sinusoid_large(), 50_000)
+    m = P.build_model("matern52", 1.0, 1.0)
+    mean, var, ll, ws = P.predict(m, dev(s.t_train), dev(s.y_train), dev(s.t_test), 0.01)
+    ref = (host(mean), host(var), host(ll))
+    ht = [torch.as_tensor(x).pin_memory() for x in (s.t_train, s.y_train, s.t_test)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = [tuple(torch.empty(k, dtype=torch.float64).pin_memory() for k in (s.M, s.M, 1)) for _ in streams]
+    keep = [P.predict_host(m, *ht, 0.01, o, stream=st) for st, o in zip(streams, outs)]   # workspaces stay alive
+    torch.cuda.synchronize()
+    del keep
+    for o in outs:
+        assert np.array_equal(o[0].numpy(), ref[0]) and np.array_equal(o[1].numpy(), ref[1])
+        assert o[2].numpy()[0] == ref[2][0]
