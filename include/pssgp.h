@@ -112,6 +112,12 @@ typedef struct pssgp_model {
   double rsup[PSSGP_DMAX * PSSGP_DMAX];
   double rlast[PSSGP_DMAX * PSSGP_DMAX];
   double lengthscale, variance;          /* metadata                            */
+  /* hthr_f32[K] / hthr_q32[K]: largest step h for which the terms from K on
+   * stay below 2^-36 (relative, same exact norms); those terms may be summed
+   * in FP32 (error below 2^-55).  All 0 when a coefficient is outside the
+   * FP32-safe range [1e-30, 1e30]. */
+  double hthr_f32[PSSGP_NTAYLOR + 1];
+  double hthr_q32[PSSGP_NTAYLOR + 1];
 } pssgp_model;
 
 /* Kernel -> SDE (G, L, q, H) (Sec. 2: exact for Matern nu = 1/2, 3/2, 5/2;

@@ -47,7 +47,8 @@ class PssgpModel(ctypes.Structure):
                 ("hthr_f", ctypes.c_double * (NTAYLOR + 1)), ("hthr_q", ctypes.c_double * (NTAYLOR + 1)),
                 ("hmax", ctypes.c_double), ("companion", ctypes.c_int32), ("reserved2", ctypes.c_int32),
                 ("rsup", ctypes.c_double * (DMAX * DMAX)), ("rlast", ctypes.c_double * (DMAX * DMAX)),
-                ("lengthscale", ctypes.c_double), ("variance", ctypes.c_double)]
+                ("lengthscale", ctypes.c_double), ("variance", ctypes.c_double),
+                ("hthr_f32", ctypes.c_double * (NTAYLOR + 1)), ("hthr_q32", ctypes.c_double * (NTAYLOR + 1))]
 
 
 class PssgpError(RuntimeError):

@@ -28,6 +28,15 @@ inline DevModel<D> dev_model(const pssgp_model* pm) {
     m.hthr_q[t] = std::nextafter((float)pm->hthr_q[t], 0.0f);
   }
   m.hmax = std::nextafter((float)pm->hmax, 0.0f);
+  for (int e = 0; e < D * D; ++e)
+    for (int t = 0; t < NT; ++t) m.fc32[e][t] = (float)pm->fc[e * PSSGP_NTAYLOR + t];
+  for (int i = 0; i < D; ++i)
+    for (int j = i; j < D; ++j)
+      for (int t = 0; t < NT; ++t) m.qc32[pidx<D>(i, j)][t] = (float)pm->qc[(i * D + j) * PSSGP_NTAYLOR + t];
+  for (int t = 0; t <= NT; ++t) {
+    m.hthr_f32[t] = std::nextafter((float)pm->hthr_f32[t], 0.0f);
+    m.hthr_q32[t] = std::nextafter((float)pm->hthr_q32[t], 0.0f);
+  }
   m.companion = pm->companion;
   for (int i = 0; i < D; ++i)
     for (int j = 0; j < D; ++j) { m.rsup[i][j] = pm->rsup[i * D + j]; m.rlast[i][j] = pm->rlast[i * D + j]; }

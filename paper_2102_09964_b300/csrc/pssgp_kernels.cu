@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_batched(const DevMode
     }
   }
   Mat<D> F, Q;
-  discretize<D>(m, h, first, act, F, Q, uscale, qscale);
+  discretize<D, true>(m, h, first, act, F, Q, uscale, qscale);
   store_fq<D>(stage, threadIdx.x, F, Q);
   if (act) {
     Rstep[k] = R;

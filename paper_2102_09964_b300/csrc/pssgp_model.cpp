@@ -260,20 +260,34 @@ int finish_model(int d, int kind, const ld* G0, const ld* L0, ld q, const ld* H0
     for (int m = K; m < MN; ++m) { s += wnm[m + 1] * hm / fm; hm *= h; fm *= (m + 2); }
     return s / w1;
   };
-  auto largest_h = [&](auto tail, int K) {
+  auto largest_h = [&](auto tail, int K, ld bound) {
     ld lo = 0.0L, hi = 1.0L;
-    while (tail(K, hi) <= eps && hi < 1e6L) { lo = hi; hi *= 2.0L; }
+    while (tail(K, hi) <= bound && hi < 1e6L) { lo = hi; hi *= 2.0L; }
     for (int it = 0; it < 200; ++it) {
       const ld mid = 0.5L * (lo + hi);
-      if (tail(K, mid) <= eps) lo = mid; else hi = mid;
+      if (tail(K, mid) <= bound) lo = mid; else hi = mid;
     }
     return lo;
   };
   out->hthr_f[0] = 0.0;
   out->hthr_q[0] = 0.0;
   for (int K = 1; K <= PSSGP_NTAYLOR; ++K) {
-    out->hthr_f[K] = (double)(0.999L * largest_h(tail_f, K));
-    out->hthr_q[K] = (double)(0.999L * largest_h(tail_q, K));
+    out->hthr_f[K] = (double)(0.999L * largest_h(tail_f, K, eps));
+    out->hthr_q[K] = (double)(0.999L * largest_h(tail_q, K, eps));
+  }
+  // split points of the mixed-precision sums: terms from K on below 2^-36 may
+  // be summed in FP32 (Horner error at most 2 x 16 x 2^-24 of their size, i.e.
+  // below 2^-55), if every coefficient is zero or within the FP32-safe range
+  bool f32ok = true;
+  for (int e = 0; e < d * d * PSSGP_NTAYLOR; ++e)
+    for (const double c : {out->fc[e], out->qc[e]})
+      if (c != 0.0 && !(std::fabs(c) >= 1e-30 && std::fabs(c) <= 1e30)) f32ok = false;
+  const ld eps32 = ldexpl(1.0L, -36);
+  out->hthr_f32[0] = 0.0;
+  out->hthr_q32[0] = 0.0;
+  for (int K = 1; K <= PSSGP_NTAYLOR; ++K) {
+    out->hthr_f32[K] = f32ok ? (double)(0.999L * largest_h(tail_f, K, eps32)) : 0.0;
+    out->hthr_q32[K] = f32ok ? (double)(0.999L * largest_h(tail_q, K, eps32)) : 0.0;
   }
   out->hmax = std::min(out->hthr_f[PSSGP_NTAYLOR], out->hthr_q[PSSGP_NTAYLOR]);
   if (!(out->hmax > 0.0)) return PSSGP_EMODEL;

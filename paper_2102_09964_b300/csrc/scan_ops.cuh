@@ -34,6 +34,12 @@ struct DevModel {
   float hthr_q[NT + 1];
   float hmax;
   int companion;
+  // mixed precision: the terms from the split point on (table hthr_*32) are
+  // summed in FP32 with these coefficients
+  float fc32[D * D][NT];
+  float qc32[Sym<D>::N][NT];
+  float hthr_f32[NT + 1];
+  float hthr_q32[NT + 1];
 };
 
 // ---------------------------------------------------------------------------
@@ -73,7 +79,7 @@ __device__ __noinline__ void double_steps(Mat<D>& F, Mat<D>& Q, int s, int smax)
 // entries of Q for short steps, which the per-warp normwise term count does
 // not give; needed where Q is factorised, as in the prior simulation).
 template <int D>
-__device__ __forceinline__ void discretize(const DevModel<D>& m, double h, bool first, bool active,
+__device__ __forceinline__ void discretize_fp64(const DevModel<D>& m, double h, bool first, bool active,
                                            Mat<D>& F, Mat<D>& Q, double uscale = 1.0, double qscale = 1.0,
                                            bool all_terms = false) {
   h *= uscale;
@@ -152,6 +158,164 @@ __device__ __forceinline__ void discretize(const DevModel<D>& m, double h, bool 
         Q[i][j] = qscale * m.Pinf[i <= j ? pidx<D>(i, j) : pidx<D>(j, i)];
       }
   }
+}
+
+template <int D>
+__device__ __forceinline__ void discretize_split(const DevModel<D>& m, double h, bool first, bool active,
+                                           Mat<D>& F, Mat<D>& Q, double uscale = 1.0, double qscale = 1.0,
+                                           bool all_terms = false) {
+  h *= uscale;
+  float hf = (float)h;
+  int s = 0;
+  if (active && !first && hf > m.hmax) {
+    s = (int)ceilf(log2f(hf / m.hmax));
+    if (s < 0) s = 0;
+    if (s > 60) s = 60;
+    hf = ldexpf(hf, -s);
+    if (hf > m.hmax) { ++s; hf *= 0.5f; }
+  }
+  if (!active || first || !(hf > 0.0f)) hf = 0.0f;
+  const float hw = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(hf)));
+  // term counts: the first K with hw <= thr[K] (thresholds non-decreasing in
+  // K), i.e. 1 + the number of thresholds below hw, by independent compares
+  int kf = 1, kq = 1, mf = 1, mq = 1;
+#pragma unroll
+  for (int k = 1; k < NT; ++k) {
+    kf += (hw > m.hthr_f[k]) ? 1 : 0;
+    kq += (hw > m.hthr_q[k]) ? 1 : 0;
+    mf += (hw > m.hthr_f32[k]) ? 1 : 0;
+    mq += (hw > m.hthr_q32[k]) ? 1 : 0;
+  }
+  // split points: terms from mf / mq on are summed in FP32 (below 2^-36 of
+  // the series, so their FP32 rounding stays below 2^-55); used only when the
+  // split moves at least 3 terms (the FP32 -> FP64 conversion of each entry
+  // costs about one FP64 operation), never with all_terms
+  if (all_terms) { kf = NT; kq = NT; }
+  if (all_terms || kf - mf < 3) mf = kf;
+  if (all_terms || kq - mq < 3) mq = kq;
+  const int smax = (int)__reduce_max_sync(0xffffffffu, (unsigned)s);
+  double hs = (s > 0) ? h * __longlong_as_double((long long)(1023 - s) << 52) : h;
+  if (first || !active) hs = 0.0;
+  const float h32 = (float)hs;
+  if (m.companion) {
+    // row 0 by Horner (FP32 tail, FP64 head), the other rows by the
+    // companion recursion
+    int t0 = kf - 2;
+    if (mf < kf) {
+      float a[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) a[j] = m.fc32[j][kf - 1];
+#pragma unroll 1
+      for (int t = kf - 2; t >= mf; --t) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) a[j] = fmaf(a[j], h32, m.fc32[j][t]);
+      }
+#pragma unroll
+      for (int j = 0; j < D; ++j) F[0][j] = (double)a[j];
+      t0 = mf - 1;
+    } else {
+#pragma unroll
+      for (int j = 0; j < D; ++j) F[0][j] = m.fc[j][kf - 1];
+    }
+#pragma unroll 1
+    for (int t = t0; t >= 0; --t) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) F[0][j] = fma(F[0][j], hs, m.fc[j][t]);
+    }
+#pragma unroll
+    for (int i = 0; i + 1 < D; ++i) {
+      F[i + 1][0] = F[i][D - 1] * m.rlast[i][0];
+#pragma unroll
+      for (int j = 1; j < D; ++j) F[i + 1][j] = fma(F[i][j - 1], m.rsup[i][j], F[i][D - 1] * m.rlast[i][j]);
+    }
+  } else {
+    int t0 = kf - 2;
+    if (mf < kf) {
+      float a[D * D];
+#pragma unroll
+      for (int e = 0; e < D * D; ++e) a[e] = m.fc32[e][kf - 1];
+#pragma unroll 1
+      for (int t = kf - 2; t >= mf; --t) {
+#pragma unroll
+        for (int e = 0; e < D * D; ++e) a[e] = fmaf(a[e], h32, m.fc32[e][t]);
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) F[i][j] = (double)a[i * D + j];
+      t0 = mf - 1;
+    } else {
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) F[i][j] = m.fc[i * D + j][kf - 1];
+    }
+#pragma unroll 1
+    for (int t = t0; t >= 0; --t) {
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) F[i][j] = fma(F[i][j], hs, m.fc[i * D + j][t]);
+    }
+  }
+  {
+    int t0 = kq - 2;
+    if (mq < kq) {
+      float a[Sym<D>::N];
+#pragma unroll
+      for (int e = 0; e < Sym<D>::N; ++e) a[e] = m.qc32[e][kq - 1];
+#pragma unroll 1
+      for (int t = kq - 2; t >= mq; --t) {
+#pragma unroll
+        for (int e = 0; e < Sym<D>::N; ++e) a[e] = fmaf(a[e], h32, m.qc32[e][t]);
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = i; j < D; ++j) Q[i][j] = (double)a[pidx<D>(i, j)];
+      t0 = mq - 1;
+    } else {
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = i; j < D; ++j) Q[i][j] = m.qc[pidx<D>(i, j)][kq - 1];
+    }
+#pragma unroll 1
+    for (int t = t0; t >= 0; --t) {
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = i; j < D; ++j) Q[i][j] = fma(Q[i][j], hs, m.qc[pidx<D>(i, j)][t]);
+    }
+  }
+  const double hq = hs * qscale;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) { Q[i][j] *= hq; Q[j][i] = Q[i][j]; }
+  // doubling for long steps (rare; each lane applies its own count)
+  if (smax > 0) double_steps<D>(F, Q, s, smax);
+  if (first) {
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        F[i][j] = 0.0;
+        Q[i][j] = qscale * m.Pinf[i <= j ? pidx<D>(i, j) : pidx<D>(j, i)];
+      }
+  }
+}
+
+// SPLIT = true: mixed precision (the terms below 2^-36 of the series summed in
+// FP32), for kernels where steps are long relative to the model's scale (the
+// batched path); SPLIT = false keeps every term in FP64 and the term counts
+// warp-uniform through the uniform datapath.
+template <int D, bool SPLIT = false>
+__device__ __forceinline__ void discretize(const DevModel<D>& m, double h, bool first, bool active,
+                                           Mat<D>& F, Mat<D>& Q, double uscale = 1.0, double qscale = 1.0,
+                                           bool all_terms = false) {
+  if constexpr (SPLIT) discretize_split<D>(m, h, first, active, F, Q, uscale, qscale, all_terms);
+  else discretize_fp64<D>(m, h, first, active, F, Q, uscale, qscale, all_terms);
 }
 
 // ---------------------------------------------------------------------------

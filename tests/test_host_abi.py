@@ -168,3 +168,24 @@ def test_workspace_size_grows_linearly(lib):
     a = P.workspace_size(6, 1 << 16)
     b = P.workspace_size(6, 1 << 17)
     assert 1.8 < b / a < 2.2
+
+
+@pytest.mark.parametrize("kind", ["matern32", "matern52", "rbf"])
+def test_fp32_split_thresholds_bound_the_tail(kind):
+    """At h = hthr_f32[K] the terms of exp(hG) from K on sum below 2^-36 in
+    the 1-norm (recomputed here from the model's own balanced drift), the
+    thresholds grow with K and are looser than the FP64 truncation ones."""
+    m = P.build_model(kind, 1.0, 1.0)
+    d = m.d
+    G = m.matrix("G")
+    hf32 = np.array(m.raw.hthr_f32[:17])
+    hf = np.array(m.raw.hthr_f[:17])
+    assert np.all(np.diff(hf32[1:]) > 0) and np.all(hf32[1:] >= hf[1:])
+    for K in (3, 6, 9, 12):
+        h = hf32[K]
+        tail, Gm, fact = 0.0, np.linalg.matrix_power(G, K), math.factorial(K)
+        for mm in range(K, 80):
+            tail += np.abs(Gm).sum(axis=0).max() * h ** mm / fact
+            Gm = Gm @ G
+            fact *= mm + 1
+        assert tail <= 2.0 ** -36 * 1.01, (K, tail)
