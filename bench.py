@@ -114,6 +114,28 @@ def flops_rts_step(d):
     return 2 * d * d + (2 * d ** 3 - d * d) + 2 * s * d
 
 
+def flops_adjoint_fold(d, observed_frac):
+    """Mean-adjoint chunk product in the filter pass: Pi F^T, Pi[:,0] v/S,
+    Pi - Pi[:,0] K^T."""
+    return (2 * d ** 3 - d * d) + observed_frac * (2 * d + 2 * d * d)
+
+
+def flops_adjoint_step(d, observed_frac):
+    """One backward step of the covariance adjoint as evaluated: xb = F^T mb,
+    F^T M F accumulated row by row (d rows of L F, d x Sym outer updates),
+    w = R K, K^T R K, the rank-2 corrections, mb = A xb + e0 v/S."""
+    s = d * (d + 1) // 2
+    return 2 * d * d + d * (2 * d * d + 2 * s) + observed_frac * (2 * d * d + 2 * d + 2 * d + 8)
+
+
+def flops_adjoint_terms(d, observed_frac, companion=True):
+    """The derivative terms of one step: tr(Mb Q), tr(Mb W), mb^T G m,
+    tr(Mb G M) (companion drift: 2d - 1 entries of M Mb), dl/dR."""
+    s = d * (d + 1) // 2
+    gm = (2 * d - 1) * 2 * d if companion else 2 * d ** 3
+    return 4 * s + gm + 4 * d + 8 + observed_frac * 6
+
+
 def taylor_terms(model, t, lanes, L):
     """Mean Taylor term counts as the device picks them: per warp and per
     in-chunk iteration, from the longest step over the warp's 32 lanes."""
@@ -313,6 +335,57 @@ def batched_bench(args, P, wl, dev, barrier, world, rank):
             "tuning": tuning, "gpu_launches_per_eval": int(sum(c for _, c in per.values())),
             "kernels_ms": {k: round(v[0], 4) for k, v in per.items()},
             "l2": "inputs and workspace ~17 GB per evaluation, far above the 126 MB L2"}
+
+
+def gradient_bench(args, P, wl, dev):
+    """Log-likelihood + gradient (row f2): RBF-6 on the 2^20 training points of
+    the large workload (one pssgp_loglik_grad per step, inputs resident), with
+    per-kernel times and the roofline of the dominant adjoint kernel."""
+    import torch
+    s = wl.sinusoid_large()
+    m = P.build_model("rbf", 1.0, 1.0)
+    t = torch.as_tensor(s.t_train, device=dev)
+    y = torch.as_tensor(s.y_train, device=dev)
+    mask = torch.ones(t.numel(), dtype=torch.uint8, device=dev)
+    ws = P.workspace_grad(m.d, t.numel(), dev)
+    wsl = P.workspace(m.d, t.numel(), dev)
+    for _ in range(max(args.warmup, 3)):
+        P.loglik_grad(m, t, y, mask, 0.01, ws=ws)
+    torch.cuda.synchronize()
+
+    def timed(fn, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    ms_g = timed(lambda: P.loglik_grad(m, t, y, mask, 0.01, ws=ws), args.steps)
+    ms_l = timed(lambda: P.loglik(m, t, y, mask, 0.01, ws=wsl), args.steps)
+    P.timing(1)
+    P.loglik_grad(m, t, y, mask, 0.01, ws=ws)
+    torch.cuda.synchronize()
+    per = P.timing(2)
+    P.timing(0)
+    n, d = t.numel(), m.d
+    alg = {"adjoint_cov": n * (flops_adjoint_step(d, 1.0) + flops_adjoint_terms(d, 1.0)),
+           "adjoint_mean": n * flops_adjoint_step(d, 1.0),
+           "filter_propagate": n * (flops_kf_step(d, 1.0) + flops_adjoint_fold(d, 1.0)),
+           "filter_reduce": n * flops_filter_fold(d, 1.0)}
+    peak = 2 * P.fp64_fma_rate() / 1e12
+    dom = max(alg, key=lambda k: per[k][0])
+    ach = alg[dom] / (per[dom][0] * 1e-3) / 1e12
+    return {"workload": "RBF Taylor-6 (d = 6), the 2^20 training points of the large workload, l = s2 = 1, "
+                        "R = 0.01; d loglik / d(log l, log s2, log R)",
+            "ms_loglik_grad": round(ms_g, 4), "ms_loglik": round(ms_l, 4), "ratio": round(ms_g / ms_l, 3),
+            "steps_per_s": n / (ms_g * 1e-3),
+            "kernels_ms": {k: round(v[0], 4) for k, v in per.items()},
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": round(ach, 4), "peak": round(peak, 4),
+                         "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                         "algorithmic_flops_per_launch": alg[dom],
+                         "peak_source": "measured FP64 FMA rate of this GPU (pssgp_fp64_fma_rate, x2 flops)"}}
 
 
 def fit_bench(args, P, wl):
@@ -558,6 +631,7 @@ def run_ours(args, wl_params):
             "whole_path_tflops": round(whole, 4), "kernels": kernels}
     if not args.no_batched:
         line["batched"] = batched_bench(args, P, wl, dev, barrier, world, rank)
+    line["gradient"] = gradient_bench(args, P, wl, dev)
     if not args.no_fit:
         line["fit"] = fit_bench(args, P, wl)
         line["table1"] = table1_bench(P, wl)
