@@ -591,14 +591,13 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
       if (!smoother_element<D>(x, P, T, xm, Pm, e)) bad = true;
       store_egl<D>(a.rec_egl, k - 1, e);
     }
+    // the update without a branch (1/S and v are 0 on a missing step)
     const bool obs = a.mask[k] != 0;
-    double Si = 0.0, v = 0.0;
-    if (obs) {
-      const double Rk = a.R_per_step ? a.R[k] : R0;
-      const double S = Pm[0][0] + Rk;
-      if (bad_pos(S)) bad = true;
-      Si = __drcp_rn(S);
-      v = a.y[k] - xm[0];
+    const double S = Pm[0][0] + (a.R_per_step ? a.R[k] : R0);
+    if (obs && bad_pos(S)) bad = true;
+    const double Si = obs ? __drcp_rn(S) : 0.0;
+    const double v = obs ? a.y[k] - xm[0] : 0.0;
+    {
       Vec<D> K;
 #pragma unroll
       for (int i = 0; i < D; ++i) K[i] = Pm[i][0] * Si;
@@ -608,17 +607,13 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
 #pragma unroll
         for (int j = i; j < D; ++j) { P[i][j] = fma(-K[i], Pm[0][j], Pm[i][j]); P[j][i] = P[i][j]; }
       }
-      qsum = fma(v * Si, v, qsum);
-      lp.mul(S);
-      ++nobs;
-    } else {
-#pragma unroll
-      for (int i = 0; i < D; ++i) x[i] = xm[i];
-      copy<D>(Pm, P);
     }
+    qsum = fma(v * Si, v, qsum);
+    lp.mul(obs ? S : 1.0);
+    nobs += obs ? 1 : 0;
     if (fuse) {   // smoother chunk aggregate by forward recursion (state in shared memory)
       if (k == k0) fixed_point_start_smem<D, BLOCK>(sSig, sV, smu, x, P);
-      else fixed_point_step_smem<D, BLOCK>(sSig, sV, smu, F, obs, Pm, Si, v);
+      else fixed_point_step_smem<D, BLOCK>(sSig, sV, smu, F, true, Pm, Si, v);   // Si = v = 0: no update
     }
     if (a.adj) {  // gradient: forward moments and the mean-adjoint chunk product
       store_adj<D>(a.rec_adj, k, xm, Pm, v, Si);

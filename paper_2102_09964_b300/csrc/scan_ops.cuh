@@ -432,58 +432,41 @@ __device__ __forceinline__ void fagg_fold_step_smem(Vec<D>& b, Mat<D>& C, const 
     for (int k = 1; k < D; ++k) s = fma(F[0][k], Ain[(k * D + j) * SST], s);
     w[j] = s;
   }
-  if (observed) {
-    const double S = Pm[0][0] + R;
-    if (bad_pos(S)) bad = true;
-    const double Si = __drcp_rn(S);
-    const double r = y - bm[0];
-    Vec<D> K;
+  // the update without a branch: on a missing step 1/S and the innovation
+  // are 0, so every line below reduces exactly to the prediction (keeps the
+  // step one basic block for the scheduler)
+  const double S = Pm[0][0] + R;
+  if (observed && bad_pos(S)) bad = true;
+  const double Si = observed ? __drcp_rn(S) : 0.0;
+  const double r = observed ? y - bm[0] : 0.0;
+  Vec<D> K;
 #pragma unroll
-    for (int i = 0; i < D; ++i) K[i] = Pm[i][0] * Si;
+  for (int i = 0; i < D; ++i) K[i] = Pm[i][0] * Si;
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-      const double wsi = w[i] * Si;
+  for (int i = 0; i < D; ++i) {
+    const double wsi = w[i] * Si;
 #pragma unroll
-      for (int j = i; j < D; ++j) J[pidx<D>(i, j) * SST] = fma(wsi, w[j], J[pidx<D>(i, j) * SST]);
-      eta[i * SST] = fma(wsi, r, eta[i * SST]);
-    }
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      b[i] = fma(K[i], r, bm[i]);
-#pragma unroll
-      for (int j = i; j < D; ++j) { C[i][j] = fma(-K[i], Pm[0][j], Pm[i][j]); C[j][i] = C[i][j]; }
-    }
-    // A' = (F A) - K w, row by row (row 0 of F A is w)
-#pragma unroll
-    for (int j = 0; j < D; ++j) Aout[(0 * D + j) * SST] = fma(-K[0], w[j], w[j]);
-#pragma unroll
-    for (int i = 1; i < D; ++i)
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        double s = F[i][0] * Ain[(0 * D + j) * SST];
-#pragma unroll
-        for (int k = 1; k < D; ++k) s = fma(F[i][k], Ain[(k * D + j) * SST], s);
-        Aout[(i * D + j) * SST] = fma(-K[i], w[j], s);
-      }
-  } else {
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      b[i] = bm[i];
-#pragma unroll
-      for (int j = 0; j < D; ++j) C[i][j] = Pm[i][j];
-    }
-#pragma unroll
-    for (int j = 0; j < D; ++j) Aout[(0 * D + j) * SST] = w[j];
-#pragma unroll
-    for (int i = 1; i < D; ++i)
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        double s = F[i][0] * Ain[(0 * D + j) * SST];
-#pragma unroll
-        for (int k = 1; k < D; ++k) s = fma(F[i][k], Ain[(k * D + j) * SST], s);
-        Aout[(i * D + j) * SST] = s;
-      }
+    for (int j = i; j < D; ++j) J[pidx<D>(i, j) * SST] = fma(wsi, w[j], J[pidx<D>(i, j) * SST]);
+    eta[i * SST] = fma(wsi, r, eta[i * SST]);
   }
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    b[i] = fma(K[i], r, bm[i]);
+#pragma unroll
+    for (int j = i; j < D; ++j) { C[i][j] = fma(-K[i], Pm[0][j], Pm[i][j]); C[j][i] = C[i][j]; }
+  }
+  // A' = (F A) - K w, row by row (row 0 of F A is w)
+#pragma unroll
+  for (int j = 0; j < D; ++j) Aout[(0 * D + j) * SST] = fma(-K[0], w[j], w[j]);
+#pragma unroll
+  for (int i = 1; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double s = F[i][0] * Ain[(0 * D + j) * SST];
+#pragma unroll
+      for (int k = 1; k < D; ++k) s = fma(F[i][k], Ain[(k * D + j) * SST], s);
+      Aout[(i * D + j) * SST] = fma(-K[i], w[j], s);
+    }
 }
 
 // General filtering operator of Sec. 3, o = a (earlier) x b (later):
