@@ -37,7 +37,7 @@ METRIC = "filter+smoother time steps/s at N=2^20,d=6 FP64"
 # current kernels on a 2^18-step case (profiles/fp64_instruction_counts_rbf6_n264k.md);
 # traffic grows in proportion to the steps, so a launch's traffic is this x n.
 # Reset an entry to None whenever its kernel changes.
-PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": None, "filter_reduce": None, "discretize": 372.0,
+PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1344.0, "filter_reduce": 1348.0, "discretize": 370.0,
                                 "smoother_propagate": 560.0}
 UNIT = "steps/s"
 WORKLOADS = {
@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--warps-per-sm", type=int, default=0, help="scan lanes per SM / 32 (0 = library default)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 4,096-series batched measurement")
     ap.add_argument("--no-fit", action="store_true", help="skip the learned-vs-plain fit and Table-1 measurements")
+    ap.add_argument("--no-gradient", action="store_true", help="skip the log-likelihood gradient measurement")
     ap.add_argument("--fit-adam", action="store_true", help="also time the Adam fits (about a minute)")
     ap.add_argument("--profile", default="", choices=["", "grad", "batched", "batched_grad", "learn"],
                     help="run one small case 3 times for a profiler and exit (no JSON line)")
@@ -631,7 +632,8 @@ def run_ours(args, wl_params):
             "whole_path_tflops": round(whole, 4), "kernels": kernels}
     if not args.no_batched:
         line["batched"] = batched_bench(args, P, wl, dev, barrier, world, rank)
-    line["gradient"] = gradient_bench(args, P, wl, dev)
+    if not args.no_gradient:
+        line["gradient"] = gradient_bench(args, P, wl, dev)
     if not args.no_fit:
         line["fit"] = fit_bench(args, P, wl)
         line["table1"] = table1_bench(P, wl)
