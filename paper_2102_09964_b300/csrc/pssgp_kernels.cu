@@ -1038,9 +1038,12 @@ __global__ void __launch_bounds__(BLOCK, 1) k_adjoint_cov(const DevModel<D> m, c
     mb[0] += vSi - kx;
     // sM = Mb_k, mb = mb_k: the step's contributions
     gs += adj_trace_smem_rec<D, BLOCK>(sM, a.rec_fq + k * fqs_of<D>() + D * D);
-    if (Si != 0.0) gr = fma(kPk - vSi * kx + c, a.R_per_step ? a.R[k] : R0, gr);
+    // no branches (one basic block per step): on a missing step K, v/S and c
+    // are 0, so the noise term is 0; tau = 0 (a series' first step or a
+    // zero-length step) makes the lengthscale term 0
+    gr = fma(kPk - vSi * kx + c, a.R_per_step ? a.R[k] : R0, gr);
     const double tau = a.tauq[2 * k];
-    if (tau != 0.0) {
+    {
       const double q = a.tauq[2 * k + 1];
       Mat<D> Mk, Mbk;
 #pragma unroll
