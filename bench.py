@@ -226,6 +226,25 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(v: float, world: int, device) -> float:
+    """The largest value over all ranks (the slowest rank's time); a no-op on
+    one rank.  `device`: where the collective's tensor lives (the GPU for
+    NCCL, the CPU for gloo)."""
+    if world <= 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput of replicas: every rank processes units_per_rank
+    in each step; the job's step time is the slowest rank's."""
+    return units_per_rank * world / (ms_max * 1e-3)
+
+
 def cpu_baseline(wl_params, n_sample_train=1 << 19):
     """The oracle as it stands on the host cores, on a bounded prefix sample of
     the same workload; returns steps/s and a description."""
@@ -316,11 +335,7 @@ def batched_bench(args, P, wl, dev, barrier, world, rank):
     e1.synchronize()
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        tmax = torch.tensor([ms], device=dev)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        ms = float(tmax.item())
+    ms = max_over_ranks(ms, world, dev)
     P.timing(1)
     for d in parts:
         call(d)
@@ -332,7 +347,7 @@ def batched_bench(args, P, wl, dev, barrier, world, rank):
                         "mixed, l log-uniform [0.1, 10], s2 = 1, R log-uniform [1e-3, 1e-1]; log-likelihood of "
                         "every series, one pssgp_loglik_batched per family, replayed as one CUDA graph",
             "series": bt.B, "steps_total": int(n_all), "ms_per_eval": ms,
-            "series_per_s": bt.B * world / (ms * 1e-3), "steps_per_s": n_all * world / (ms * 1e-3),
+            "series_per_s": job_throughput(bt.B, world, ms), "steps_per_s": job_throughput(n_all, world, ms),
             "tuning": tuning, "gpu_launches_per_eval": int(sum(c for _, c in per.values())),
             "kernels_ms": {k: round(v[0], 4) for k, v in per.items()},
             "l2": "inputs and workspace ~17 GB per evaluation, far above the 126 MB L2"}
@@ -533,12 +548,8 @@ def run_ours(args, wl_params):
     barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        tmax = torch.tensor([ms], device=dev)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        ms = float(tmax.item())
-    value = n * world / (ms * 1e-3)
+    ms = max_over_ranks(ms, world, dev)
+    value = job_throughput(n, world, ms)
 
     # --- end to end through the C ABI from pinned host buffers ---
     # pssgp_predict_host: every step copies its inputs host -> device and its
@@ -571,12 +582,8 @@ def run_ours(args, wl_params):
     f1.record(stream)
     f1.synchronize()
     ms_e2e = f0.elapsed_time(f1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        tmax = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        ms_e2e = float(tmax.item())
-    e2e = {"value": n * world / (ms_e2e * 1e-3), "unit": UNIT,
+    ms_e2e = max_over_ranks(ms_e2e, world, dev)
+    e2e = {"value": job_throughput(n, world, ms_e2e), "unit": UNIT,
            "h2d_bytes_per_step": int((2 * N + M) * 8), "d2h_bytes_per_step": int((2 * M + 1) * 8)}
 
     # --- per-kernel times (events around each launch) for the roofline ---
