@@ -320,3 +320,50 @@ def test_predict_from_host_buffers_equals_device_call():
     for o in outs:
         assert np.array_equal(o[0].numpy(), ref[0]) and np.array_equal(o[1].numpy(), ref[1])
         assert o[2].numpy()[0] == ref[2][0]
+
+
+@pytest.mark.parametrize("order", [2, 4, 8])
+def test_predict_rbf_orders_up_to_the_largest_state(order):
+    """RBF Taylor orders up to 8 (d = 8, the largest state dimension)."""
+    s = wl.prefix(wl.sinusoid_large(N=1 << 15, M=400), 6000)
+    m = P.build_model("rbf", 1.0, 1.0, order=order)
+    mean, var, ll, ws = P.predict(m, dev(s.t_train), dev(s.y_train), dev(s.t_test), 0.01)
+    assert P.status(ws) == 0
+    o = om.make_model("rbf", 1.0, 1.0, order=order)
+    fm, fv, res, _ = oracle.predict(o, s.t_train, s.y_train, s.t_test, 0.01)
+    check_marginals(host(mean), host(var), float(host(ll)[0]), fm, fv, res.loglik, s.N, 1e-6, f"rbf{order}")
+
+
+def _non_companion_sde():
+    """Matern-5/2 in coordinates z = T^-1 x with T's first row e_0 (so
+    H T = e_0^T) and the rest mixing: G' = T^-1 G T is not in companion form,
+    the GP it defines is the same."""
+    o = om.make_model("matern52", 0.7, 1.3)
+    T = np.array([[1.0, 0.0, 0.0], [0.3, 1.0, -0.2], [0.5, 0.4, 1.0]])
+    Ti = np.linalg.inv(T)
+    return o, Ti @ o.G @ T, Ti @ o.L, o.H @ T
+
+
+def test_non_companion_user_sde_predict():
+    s = wl.prefix(wl.sinusoid_large(N=1 << 15, M=400), 8000)
+    o, G, L, H = _non_companion_sde()
+    m = P.model_from_sde(G, L, o.q, H, balance=False)
+    assert m.raw.companion == 0
+    mean, var, ll, ws = P.predict(m, dev(s.t_train), dev(s.y_train), dev(s.t_test), 0.02)
+    assert P.status(ws) == 0
+    fm, fv, res, _ = oracle.predict(o, s.t_train, s.y_train, s.t_test, 0.02)
+    check_marginals(host(mean), host(var), float(host(ll)[0]), fm, fv, res.loglik, s.N, 1e-9, "user SDE")
+
+
+def test_non_companion_user_sde_gradient():
+    """The gradient of the rescaled family of the user SDE is the Matern
+    family's gradient (the log-likelihood does not depend on coordinates)."""
+    s = wl.prefix(wl.sinusoid_large(N=1 << 15, M=0), 6000)
+    o, G, L, H = _non_companion_sde()
+    m = P.model_from_sde(G, L, o.q, H, balance=False)
+    mask = np.ones(s.N, np.uint8)
+    ll, g, ws = P.loglik_grad(m, dev(s.t_train), dev(s.y_train), dev(mask, torch.uint8), 0.02)
+    assert P.status(ws) == 0
+    rll, rg = oracle.loglik_grad_fwd("matern52", 0.7, 1.3, s.t_train, s.y_train, mask, 0.02)
+    assert abs(float(ll.item()) - rll) <= 1e-9 * max(abs(rll), s.N)
+    assert np.max(np.abs(g.cpu().numpy() - rg) / np.maximum(np.abs(rg), s.N)) <= 1e-9
