@@ -465,8 +465,9 @@ int pssgp_mlp_grad(void* state, const float* feat, const double* theta,
 /* One Adam step (0.9, 0.999, 1e-8; step counts from 1) on the parameters. */
 int pssgp_mlp_adam(void* state, const float* grad, float lr, int32_t step,
                    void* stream);
-/* Proposed log hyperparameters (device double[rows][3]); a row whose
- * standardised output is not finite or lies more than 4 standard deviations
+/* Proposed log hyperparameters (device double[rows][3]); a row with a
+ * non-finite feature, or whose standardised output is not finite or lies
+ * more than 4 standard deviations
  * of the training targets from their mean gets the plain default 0
  * (l = s2 = R = 1) instead. */
 int pssgp_mlp_predict(const void* state, const float* feat, int32_t rows,

@@ -563,14 +563,16 @@ __global__ void k_colstats(const T* X, int64_t M, int ld, float* mean, float* sd
   }
 }
 
-// network outputs to log hyperparameters; a row with a non-finite output or
-// one more than 4 standard deviations of the training targets from their
-// mean falls back to the plain default 0 (l = s2 = R = 1) in all three
-__global__ void k_mlp_decode(const float* Out, int64_t M, const float* norm, double* theta) {
+// network outputs to log hyperparameters; a row with a non-finite feature
+// (the ReLU, fmaxf, would hide it), a non-finite output or one more than 4
+// standard deviations of the training targets from their mean falls back to
+// the plain default 0 (l = s2 = R = 1) in all three
+__global__ void k_mlp_decode(const float* Out, const float* feat, int64_t M, const float* norm, double* theta) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= M) return;
   double th[3];
   bool ok = true;
+  for (int c = 0; c < NFEAT; ++c) ok = ok && isfinite(feat[r * NFEAT + c]);
 #pragma unroll
   for (int o = 0; o < 3; ++o) {
     const float z = Out[r * NOUT + o];
@@ -722,6 +724,6 @@ extern "C" int pssgp_mlp_predict(const void* state, const float* feat, int32_t r
   (void)cudaGetLastError();
   const Net n = net_of(const_cast<void*>(state));
   forward(n, a, feat, rows, s);
-  k_mlp_decode<<<blocks(rows, 256), 256, 0, s>>>(a.Out, rows, n.norm, theta);
+  k_mlp_decode<<<blocks(rows, 256), 256, 0, s>>>(a.Out, feat, rows, n.norm, theta);
   return rc_of(cudaGetLastError());
 }

@@ -112,3 +112,26 @@ def test_lbfgs_single_series_stand_in():
     _, best = cpu_fit("matern32", s.t_train, s.y_train, np.zeros(3))
     assert ll[0] >= best - 1e-6 * 3200
     assert it[0] < 100
+
+
+def test_lbfgs_fit_with_missing_measurements():
+    bt = wl.series_batch(seed=45, lengths=[2000, 1500, 3000])
+    rng = np.random.default_rng(46)
+    mask = (rng.uniform(size=bt.t.size) > 0.3).astype(np.uint8)
+    m = P.build_model("matern32", 1.0, 1.0)
+    th, ll, it, _ = P.fit_batched(m, bt.offsets, dev(bt.t), dev(bt.y), dev(mask, torch.uint8), np.zeros((3, 3)),
+                                  method="lbfgs", patience=3, tol=1e-10, max_iter=500, check_every=5)
+    th, ll = th.cpu().numpy(), ll.cpu().numpy()
+    for s in range(bt.B):
+        a, b = bt.offsets[s], bt.offsets[s + 1]
+        t, y, ms = bt.t[a:b], bt.y[a:b], mask[a:b]
+        ref = oracle.loglik_at("matern32", np.exp(th[s, 0]), np.exp(th[s, 1]), t, y, ms, np.exp(th[s, 2]))
+        assert abs(ll[s] - ref) <= 1e-9 * max(abs(ref), ms.sum())
+
+        def f(x):
+            l, g = oracle.loglik_grad_fwd("matern32", np.exp(x[0]), np.exp(x[1]), t, y, ms, np.exp(x[2]))
+            return -l, -g
+
+        best = -minimize(f, np.zeros(3), jac=True, method="L-BFGS-B", bounds=[(-6, 6)] * 3,
+                         options=dict(maxiter=500, ftol=1e-14, gtol=1e-9)).fun
+        assert ll[s] >= best - 1e-6 * ms.sum()

@@ -154,3 +154,30 @@ def test_learned_init_fits_match_plain_fits_in_fewer_iterations():
     ok = ll_l.cpu().numpy() >= ll_plain.cpu().numpy() - 1e-3 * n
     assert ok.mean() >= 0.95
     assert it_l.sum().item() < it_plain.sum().item()
+
+
+def test_network_falls_back_to_the_default_init():
+    """A proposal from a non-finite input (which the ReLU would otherwise
+    hide), or one far outside the training targets, is replaced by the plain
+    default 0 (l = s2 = R = 1)."""
+    rng = np.random.default_rng(70)
+    norm = np.zeros(144)
+    norm[65:130] = 1.0
+    norm[133:136] = 1.0
+    p = omlp.random_params(71)
+    net = P.MLP()
+    net.set_params(p, norm)
+    feat = rng.normal(size=(8, 65)).astype(np.float32)
+    feat[2, 10] = np.nan
+    th = net.predict(dev(feat, torch.float32)).cpu().numpy()
+    out, _ = omlp.forward(p, norm, feat)
+    for r in range(8):
+        z = out[r, :3]
+        if np.all(np.isfinite(z)) and np.any(np.abs(np.abs(z) - 4.0) < 0.05):
+            continue                          # too close to the cut to compare FP32 with FP64
+        ok = np.all(np.isfinite(z)) and np.all(np.abs(z) <= 4.0)
+        if ok:
+            assert np.allclose(th[r], z, atol=2.0 ** -6 * max(1.0, np.abs(z).max()))
+        else:
+            assert np.all(th[r] == 0.0)
+    assert np.all(th[2] == 0.0)
