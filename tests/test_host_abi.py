@@ -189,3 +189,53 @@ def test_fp32_split_thresholds_bound_the_tail(kind):
             Gm = Gm @ G
             fact *= mm + 1
         assert tail <= 2.0 ** -36 * 1.01, (K, tail)
+
+
+def test_host_argument_errors_of_the_newer_entry_points(lib):
+    """Rejected on the host before anything is launched (dummy pointers are
+    never dereferenced)."""
+    import ctypes
+    fake = ctypes.c_void_p(256)
+    mm = P.build_model("matern52", 1.0, 1.0)
+    EINVAL, EMODEL, EWS = -1, -6, -4
+    # gradient: null grad output, bad n
+    assert lib.pssgp_loglik_grad(ctypes.byref(mm.raw), fake, fake, fake, fake, 0, 10, None, None, fake, 1 << 30,
+                                 None) == EINVAL
+    assert lib.pssgp_loglik_grad_batched(ctypes.byref(mm.raw), fake, 0, fake, fake, fake, fake, 10, None, fake,
+                                         fake, 1 << 30, None) == EINVAL
+    # fit: options out of range, offsets that do not end at n
+    offs = np.array([0, 5, 10], dtype=np.int64)
+    bad = [dict(max_iter=0), dict(patience=0), dict(lr=0.0), dict(check_every=0), dict(method=7)]
+    for kw in bad:
+        o = P.FitOptions(kw.get("max_iter", 10), kw.get("patience", 2), 1e-7, kw.get("lr", 0.05), 0.9, 0.999, 1e-8,
+                         kw.get("check_every", 5), kw.get("method", 0))
+        assert lib.pssgp_fit_batched(ctypes.byref(mm.raw), offs.ctypes.data_as(ctypes.c_void_p), 2, fake, fake,
+                                     fake, 10, fake, fake, fake, ctypes.byref(o), fake, 1 << 30, None,
+                                     None) == EINVAL
+    o = P.FitOptions(10, 2, 1e-7, 0.05, 0.9, 0.999, 1e-8, 5, 1)
+    assert lib.pssgp_fit_batched(ctypes.byref(mm.raw), offs.ctypes.data_as(ctypes.c_void_p), 2, fake, fake, fake,
+                                 11, fake, fake, fake, ctypes.byref(o), fake, 1 << 30, None, None) == EINVAL
+    assert lib.pssgp_fit_batched(ctypes.byref(mm.raw), offs.ctypes.data_as(ctypes.c_void_p), 2, fake, fake, fake,
+                                 10, fake, fake, fake, ctypes.byref(o), fake, 16, None, None) == EWS
+    # simulation: the model must carry its hyperparameters; spacing > 0
+    o5 = om.make_model("matern52", 1.0, 1.0)
+    sde = P.model_from_sde(o5.G, o5.L, o5.q, o5.H)
+    assert lib.pssgp_simulate_prior(ctypes.byref(sde.raw), fake, 1, fake, 1, 0.01, fake, fake, fake,
+                                    None) == EMODEL
+    assert lib.pssgp_simulate_prior(ctypes.byref(mm.raw), fake, 1, fake, 1, 0.0, fake, fake, fake, None) == EINVAL
+    assert lib.pssgp_features(None, 1, fake, fake, fake, None) == EINVAL
+    # network: minibatch rows a multiple of 8, workspace size and alignment
+    assert lib.pssgp_mlp_grad(fake, fake, fake, 12, fake, None, None, fake, 1 << 30, None) == EINVAL
+    assert lib.pssgp_mlp_grad(fake, fake, fake, 16, fake, None, None, fake, 16, None) == EWS
+    assert lib.pssgp_mlp_predict(fake, fake, 16, fake, ctypes.c_void_p(257), 1 << 30, None) == EWS
+    assert lib.pssgp_mlp_adam(fake, fake, 1e-3, 0, None) == EINVAL
+    assert lib.pssgp_mlp_workspace_size(0) == 0 and lib.pssgp_mlp_state_bytes() > 0
+    assert lib.pssgp_mlp_param_count() == 256 * 80 + 256 + 256 * 256 + 256 + 16 * 256 + 16
+    # host-buffer prediction: workspace too small
+    assert lib.pssgp_predict_host(ctypes.byref(mm.raw), fake, fake, 10, fake, 5, 0.01, fake, fake, None, fake,
+                                  1024, None) == EWS
+    assert lib.pssgp_predict_host_workspace_size(3, 10, 5) >= lib.pssgp_workspace_size(3, 15)
+    # workspaces
+    assert lib.pssgp_workspace_size_grad(3, 1000) > lib.pssgp_workspace_size(3, 1000)
+    assert lib.pssgp_fit_workspace_size(3, 1000, 4) > lib.pssgp_workspace_size_grad(3, 1000)
+    assert lib.pssgp_tune_set(0, 8) == -2 and lib.pssgp_tune_set(3, 5) == EINVAL and lib.pssgp_tune_get(9) == -2
