@@ -273,6 +273,56 @@ __device__ __forceinline__ void store_egl(double* rec, int64_t k, const SAgg<D>&
 #pragma unroll
     for (int j = i; j < D; ++j) p[D * D + D + pidx<D>(i, j)] = e.L[i][j];
 }
+// smoother_element() written to the record of step k as it is formed, in the
+// same arithmetic order: W = Lc^{-1} T in place of T, then L = P - W^T W,
+// then E row by row with g (row j of E = Lc^{-T} applied to column j of W), so
+// that at most one row of E is held.  P_k (packed) is read from shared memory
+// (entry e at sP[e * SST]), so that its registers are free once T = F P_k is
+// formed.
+template <int D, int SST>
+__device__ __forceinline__ bool smoother_element_store(double* rec, int64_t k, const Vec<D>& x, const double* sP,
+                                                       Mat<D>& T, const Vec<D>& xm, const Mat<D>& Pm) {
+  double* p = rec + k * egs_of<D>();
+  Mat<D> Lc;
+  double invd[D];
+  const bool ok = cholesky<D>(Pm, Lc, invd);
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double s = T[i][j];
+#pragma unroll
+      for (int q = 0; q < i; ++q) s = fma(-Lc[i][q], T[q][j], s);
+      T[i][j] = s * invd[i];
+    }
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) {
+      double s = sP[pidx<D>(i, j) * SST];
+#pragma unroll
+      for (int q = 0; q < D; ++q) s = fma(-T[q][i], T[q][j], s);
+      p[D * D + D + pidx<D>(i, j)] = s;
+    }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    double r[D];
+#pragma unroll
+    for (int i = D - 1; i >= 0; --i) {
+      double s = T[i][j];
+#pragma unroll
+      for (int q = i + 1; q < D; ++q) s = fma(-Lc[q][i], r[q], s);
+      r[i] = s * invd[i];
+    }
+    double gj = x[j];
+#pragma unroll
+    for (int q = 0; q < D; ++q) gj = fma(-r[q], xm[q], gj);
+#pragma unroll
+    for (int i = 0; i < D; ++i) p[j * D + i] = r[i];
+    p[D * D + j] = gj;
+  }
+  return ok;
+}
 template <int D>
 __device__ __forceinline__ void load_egl(const double* rec, int64_t k, SAgg<D>& e) {
   const double* p = rec + k * egs_of<D>();
@@ -525,14 +575,23 @@ __device__ __forceinline__ double ll_piece(int nobs, const LogProd& lp, double q
 // filter level 3 (+ smoother levels 0/1 when fused)
 // shared memory of k_filter_propagate: the fixed-point state Sig, V (packed),
 // mu per thread, entry-major with stride BLOCK
-template <int D> constexpr int propagate_smem_doubles() { return (D * D + Sym<D>::N + D) * BLOCK; }
+// (+ the filter covariance P_k, packed, in the fused mode)
+template <int D, int MODE> constexpr int propagate_smem_doubles() {
+  return (D * D + Sym<D>::N + D + (MODE == 1 ? Sym<D>::N : 0)) * BLOCK;
+}
 
-template <int D>
+// MODE: PROP_PLAIN (filter outputs / log-likelihood), PROP_FUSE (+ smoother
+// levels 0/1), PROP_ADJ (+ the forward part of the gradient); a template
+// parameter so that each instance holds only its own state in the step loop
+enum { PROP_PLAIN = 0, PROP_FUSE = 1, PROP_ADJ = 2 };
+
+template <int D, int MODE>
 __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D> m, const ScanArgs a) {
   extern __shared__ double psm[];
   double* sSig = psm + threadIdx.x;
   double* sV = sSig + D * D * BLOCK;
   double* smu = sV + Sym<D>::N * BLOCK;
+  double* sP = smu + D * BLOCK;     // fused mode only
   const int64_t g = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int64_t w = g >> 5;
@@ -564,7 +623,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
     copy<D>(P2, P);
   }
   const double R0 = a.R ? a.R[0] : a.R_scalar;
-  const int fuse = a.fuse_smoother;
+  constexpr bool fuse = MODE == PROP_FUSE;
+  constexpr bool adj = MODE == PROP_ADJ;
   double qsum = 0.0;
   LogProd lp;
   int nobs = 0;
@@ -586,17 +646,20 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
     mulv<D>(F, x, xm);
     mul<D>(F, P, T);
     mul_Bt_sym_add<D>(T, F, Q, Pm);
-    if (fuse && k > k0) {
-      SAgg<D> e;
-      if (!smoother_element<D>(x, P, T, xm, Pm, e)) bad = true;
-      store_egl<D>(a.rec_egl, k - 1, e);
-    }
     // the update without a branch (1/S and v are 0 on a missing step)
     const bool obs = a.mask[k] != 0;
     const double S = Pm[0][0] + (a.R_per_step ? a.R[k] : R0);
     if (obs && bad_pos(S)) bad = true;
     const double Si = obs ? __drcp_rn(S) : 0.0;
     const double v = obs ? a.y[k] - xm[0] : 0.0;
+    if constexpr (fuse) {
+      if (k > k0) {
+        // smoother chunk aggregate by forward recursion (state in shared
+        // memory); first, so that F is dead before the smoother element
+        fixed_point_step_smem<D, BLOCK>(sSig, sV, smu, F, true, Pm, Si, v);   // Si = v = 0: no update
+        if (!smoother_element_store<D, BLOCK>(a.rec_egl, k - 1, x, sP, T, xm, Pm)) bad = true;
+      }
+    }
     {
       Vec<D> K;
 #pragma unroll
@@ -611,11 +674,14 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
     qsum = fma(v * Si, v, qsum);
     lp.mul(obs ? S : 1.0);
     nobs += obs ? 1 : 0;
-    if (fuse) {   // smoother chunk aggregate by forward recursion (state in shared memory)
+    if constexpr (fuse) {
       if (k == k0) fixed_point_start_smem<D, BLOCK>(sSig, sV, smu, x, P);
-      else fixed_point_step_smem<D, BLOCK>(sSig, sV, smu, F, true, Pm, Si, v);   // Si = v = 0: no update
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = i; j < D; ++j) sP[pidx<D>(i, j) * BLOCK] = P[i][j];
     }
-    if (a.adj) {  // gradient: forward moments and the mean-adjoint chunk product
+    if constexpr (adj) {  // gradient: forward moments and the mean-adjoint chunk product
       store_adj<D>(a.rec_adj, k, xm, Pm, v, Si);
       Vec<D> Kv;
 #pragma unroll
@@ -636,7 +702,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
   }
   a.llp[g] = ll_piece(nobs, lp, qsum);
   if (a.ll_step && k1 > k0) a.ll_step[lpos] = a.llp[g];
-  if (a.adj) {
+  if constexpr (adj) {
     SAgg<D> sa;
     if (k1 > k0) {
       // last factor: the transition into the next chunk's first step (none
@@ -673,7 +739,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
     }
     store_sagg<D>(a.lagg_s + g, a.P0, sa);
     if (lane == 0) store_sagg<D>(a.wagg_s + w, a.P2, sa);
-  } else if (fuse) {
+  } else if constexpr (fuse) {
     SAgg<D> sa;
     if (k1 > k0) {
       // element of the chunk's last step (the transition into the next step,
@@ -1326,10 +1392,12 @@ void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s
   }
   a.wfin_f = run_filter_level2<D>(p, a.wagg_f, a.status, s);
   {
-    constexpr int psmem = propagate_smem_doubles<D>() * 8;
-    cudaFuncSetAttribute(k_filter_propagate<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);
+    const int psmem = (a.fuse_smoother ? propagate_smem_doubles<D, PROP_FUSE>() : propagate_smem_doubles<D, PROP_PLAIN>()) * 8;
+    auto kern = a.adj ? k_filter_propagate<D, PROP_ADJ>
+                      : a.fuse_smoother ? k_filter_propagate<D, PROP_FUSE> : k_filter_propagate<D, PROP_PLAIN>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);
     Timed tm(s, T_FPROP);
-    k_filter_propagate<D><<<grid, BLOCK, psmem, s>>>(m, a);
+    kern<<<grid, BLOCK, psmem, s>>>(m, a);
     after_launch();
   }
 }
