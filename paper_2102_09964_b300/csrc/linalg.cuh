@@ -230,4 +230,33 @@ __device__ __forceinline__ bool cholesky(const Mat<D>& S, Mat<D>& Lc, double (&i
   return ok;
 }
 
+// Square-root-free factorisation S = Lu diag(d) Lu^T of a symmetric positive
+// definite S, Lu unit lower triangular (entries below the diagonal are set,
+// the rest are not used); rd[i] = 1 / d_i.  Returns false if a pivot d_i is
+// not strictly positive and finite.  Z holds Lu[i][k] d_k for the dot
+// products.
+template <int D>
+__device__ __forceinline__ bool ldlt(const Mat<D>& S, Mat<D>& Lu, double (&rd)[D]) {
+  bool ok = true;
+  Mat<D> Z;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    double s = S[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) s = fma(-Z[j][k], Lu[j][k], s);
+    if (bad_pos(s)) ok = false;
+    const double r = __drcp_rn(s);
+    rd[j] = r;
+#pragma unroll
+    for (int i = j + 1; i < D; ++i) {
+      double t = S[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) t = fma(-Z[i][k], Lu[j][k], t);
+      Z[i][j] = t;
+      Lu[i][j] = t * r;
+    }
+  }
+  return ok;
+}
+
 }  // namespace pssgp

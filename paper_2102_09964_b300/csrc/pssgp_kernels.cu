@@ -273,37 +273,45 @@ __device__ __forceinline__ void store_egl(double* rec, int64_t k, const SAgg<D>&
 #pragma unroll
     for (int j = i; j < D; ++j) p[D * D + D + pidx<D>(i, j)] = e.L[i][j];
 }
-// smoother_element() written to the record of step k as it is formed, in the
-// same arithmetic order: W = Lc^{-1} T in place of T, then L = P - W^T W,
-// then E row by row with g (row j of E = Lc^{-T} applied to column j of W), so
-// that at most one row of E is held.  P_k (packed) is read from shared memory
-// (entry e at sP[e * SST]), so that its registers are free once T = F P_k is
-// formed.
+// smoother_element() written to the record of step k as it is formed:
+// W = Lu^{-1} T in place of T, L = P - W^T V with V = diag(rd) W (V replaces
+// W row by row), then E row by row with g (row j of E = Lu^{-T} applied to column j of V), so that at
+// most one row of E is held.  P_k (packed) is read from shared memory (entry
+// e at sP[e * SST]), so that its registers are free once T = F P_k is formed.
 template <int D, int SST>
 __device__ __forceinline__ bool smoother_element_store(double* rec, int64_t k, const Vec<D>& x, const double* sP,
                                                        Mat<D>& T, const Vec<D>& xm, const Mat<D>& Pm) {
   double* p = rec + k * egs_of<D>();
-  Mat<D> Lc;
-  double invd[D];
-  const bool ok = cholesky<D>(Pm, Lc, invd);
+  Mat<D> Lu;
+  double rd[D];
+  const bool ok = ldlt<D>(Pm, Lu, rd);
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       double s = T[i][j];
 #pragma unroll
-      for (int q = 0; q < i; ++q) s = fma(-Lc[i][q], T[q][j], s);
-      T[i][j] = s * invd[i];
+      for (int q = 0; q < i; ++q) s = fma(-Lu[i][q], T[q][j], s);
+      T[i][j] = s;
     }
+  // L = P - sum_q W_q^T V_q over the rows q; row q of T becomes V_q once used
+  double Ls[Sym<D>::N];
 #pragma unroll
-  for (int i = 0; i < D; ++i)
+  for (int e = 0; e < Sym<D>::N; ++e) Ls[e] = sP[e * SST];
 #pragma unroll
-    for (int j = i; j < D; ++j) {
-      double s = sP[pidx<D>(i, j) * SST];
+  for (int q = 0; q < D; ++q) {
+    double vq[D];
 #pragma unroll
-      for (int q = 0; q < D; ++q) s = fma(-T[q][i], T[q][j], s);
-      p[D * D + D + pidx<D>(i, j)] = s;
-    }
+    for (int j = 0; j < D; ++j) vq[j] = T[q][j] * rd[q];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = i; j < D; ++j) Ls[pidx<D>(i, j)] = fma(-T[q][i], vq[j], Ls[pidx<D>(i, j)]);
+#pragma unroll
+    for (int j = 0; j < D; ++j) T[q][j] = vq[j];
+  }
+#pragma unroll
+  for (int e = 0; e < Sym<D>::N; ++e) p[D * D + D + e] = Ls[e];
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     double r[D];
@@ -311,8 +319,8 @@ __device__ __forceinline__ bool smoother_element_store(double* rec, int64_t k, c
     for (int i = D - 1; i >= 0; --i) {
       double s = T[i][j];
 #pragma unroll
-      for (int q = i + 1; q < D; ++q) s = fma(-Lc[q][i], r[q], s);
-      r[i] = s * invd[i];
+      for (int q = i + 1; q < D; ++q) s = fma(-Lu[q][i], r[q], s);
+      r[i] = s;
     }
     double gj = x[j];
 #pragma unroll
@@ -323,6 +331,7 @@ __device__ __forceinline__ bool smoother_element_store(double* rec, int64_t k, c
   }
   return ok;
 }
+
 template <int D>
 __device__ __forceinline__ void load_egl(const double* rec, int64_t k, SAgg<D>& e) {
   const double* p = rec + k * egs_of<D>();

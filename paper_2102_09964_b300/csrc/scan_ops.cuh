@@ -635,30 +635,52 @@ __device__ __forceinline__ void sagg_combine(const SAgg<D>& a, const SAgg<D>& b,
 // transition into step k+1, given T = F P_k, x^- = F x_k and
 // P^- = F P_k F^T + Q (the Kalman prediction of step k+1):
 //   E = P_k F^T (P^-)^{-1}, g = x_k - E x^-, L = P_k - E F P_k,
-// with P^- = Lc Lc^T (Cholesky), W = Lc^{-1} T, E^T = Lc^{-T} W, L = P_k - W^T W.
+// with P^- = Lu diag(d) Lu^T (square-root free), W = Lu^{-1} T,
+// V = diag(1/d) W, L = P_k - W^T V, E^T = Lu^{-T} V.
 template <int D>
 __device__ __forceinline__ bool smoother_element(const Vec<D>& x, const Mat<D>& P, const Mat<D>& T,
                                                  const Vec<D>& xm, const Mat<D>& Pm, SAgg<D>& e) {
-  Mat<D> Lc, Wm;
-  double invd[D];
-  const bool ok = cholesky<D>(Pm, Lc, invd);
+  Mat<D> Lu, V;
+  double rd[D];
+  const bool ok = ldlt<D>(Pm, Lu, rd);
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       double s = T[i][j];
 #pragma unroll
-      for (int k = 0; k < i; ++k) s = fma(-Lc[i][k], Wm[k][j], s);
-      Wm[i][j] = s * invd[i];
+      for (int k = 0; k < i; ++k) s = fma(-Lu[i][k], V[k][j], s);
+      V[i][j] = s;
     }
+  // L = P - sum_k W_k^T V_k over the rows k; row k of W becomes V_k once used
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) e.L[i][j] = P[i][j];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    double vk[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) vk[j] = V[k][j] * rd[k];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = i; j < D; ++j) e.L[i][j] = fma(-V[k][i], vk[j], e.L[i][j]);
+#pragma unroll
+    for (int j = 0; j < D; ++j) V[k][j] = vk[j];
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < i; ++j) e.L[i][j] = e.L[j][i];
 #pragma unroll
   for (int i = D - 1; i >= 0; --i)
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      double s = Wm[i][j];
+      double s = V[i][j];
 #pragma unroll
-      for (int k = i + 1; k < D; ++k) s = fma(-Lc[k][i], e.E[j][k], s);
-      e.E[j][i] = s * invd[i];
+      for (int k = i + 1; k < D; ++k) s = fma(-Lu[k][i], e.E[j][k], s);
+      e.E[j][i] = s;
     }
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -667,16 +689,6 @@ __device__ __forceinline__ bool smoother_element(const Vec<D>& x, const Mat<D>& 
     for (int k = 0; k < D; ++k) s = fma(-e.E[i][k], xm[k], s);
     e.g[i] = s;
   }
-#pragma unroll
-  for (int i = 0; i < D; ++i)
-#pragma unroll
-    for (int j = i; j < D; ++j) {
-      double s = P[i][j];
-#pragma unroll
-      for (int k = 0; k < D; ++k) s = fma(-Wm[k][i], Wm[k][j], s);
-      e.L[i][j] = s;
-      e.L[j][i] = s;
-    }
   return ok;
 }
 
