@@ -37,7 +37,7 @@ METRIC = "filter+smoother time steps/s at N=2^20,d=6 FP64"
 # current kernels on a 2^18-step case (profiles/fp64_instruction_counts_rbf6_n264k.md);
 # traffic grows in proportion to the steps, so a launch's traffic is this x n.
 # Reset an entry to None whenever its kernel changes.
-PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1344.0, "filter_reduce": 1348.0, "discretize": 370.0,
+PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1363.0, "filter_reduce": 1354.0, "discretize": 371.0,
                                 "smoother_propagate": 560.0}
 UNIT = "steps/s"
 WORKLOADS = {

@@ -331,7 +331,7 @@ const char* pssgp_timing_name(int32_t slot);
 
 /* Scan tuning: the number of chunks ("lanes", one per thread) of the scans
  * is SMs x warps_per_sm x 32, i.e. n / (SMs x warps_per_sm x 32) steps per
- * thread; warps_per_sm is 4, 8, 12 or 16 (default 4).  More lanes give each
+ * thread; warps_per_sm is 4, 8, 12 or 16 (default 8 for d <= 3, else 4).  More lanes give each
  * SM more warps to hide latency but shorter chunks and more scan overhead.
  * Affects calls planned afterwards.  pssgp_set_warps_per_sm sets every state
  * dimension; pssgp_tune_set one (PSSGP_EDIM for d outside 1..8);

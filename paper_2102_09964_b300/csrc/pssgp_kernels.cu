@@ -41,7 +41,9 @@ namespace {
 constexpr int BLOCK = 128;           // 4 warps: one per SM sub-partition
 // lanes per SM / 32, per state dimension (pssgp_set_warps_per_sm, pssgp_tune_set)
 constexpr int WARPS_MAX = 16;
-int g_warps_per_sm[PSSGP_DMAX + 1] = {4, 4, 4, 4, 4, 4, 4, 4, 4};
+// default: 8 for d <= 3 (short per-step work, more warps hide its latency;
+// measured 8-12 % faster than 4 at 2^20 steps), 4 above (255 registers)
+int g_warps_per_sm[PSSGP_DMAX + 1] = {8, 8, 8, 8, 4, 4, 4, 4, 4};
 constexpr int MIN_CHUNK = 8;         // steps per lane below which fewer lanes are used
 
 // ---------------------------------------------------------------------------
