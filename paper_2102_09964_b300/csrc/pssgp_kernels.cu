@@ -71,9 +71,9 @@ constexpr int TIMING_SLOTS = 16;
 const char* const kTimingNames[TIMING_SLOTS] = {
     "merge", "filter_reduce", "filter_level2", "filter_propagate", "smoother_level2", "smoother_propagate",
     "smoother_elements", "gather", "loglik_reduce", "discretize", "adjoint_level2", "adjoint_mean",
-    "adjoint_cov", "", "", ""};
+    "adjoint_cov", "loglik_chunks", "", ""};
 enum { T_MERGE = 0, T_FRED, T_FL2, T_FPROP, T_SL2, T_SPROP, T_SELEM, T_GATHER, T_LL, T_DISC, T_AL2, T_AMEAN,
-       T_ACOV };
+       T_ACOV, T_LLC };
 bool g_timing = false;
 struct TimingRec { cudaEvent_t a, b; int slot; };
 std::vector<TimingRec> g_pending;
@@ -217,6 +217,8 @@ struct ScanArgs {
   double* dbg_agg;       // optional: level-0 lane aggregates (tests)
   const uint8_t* seg_start;  // batched: series starts (null for one series)
   double* ll_step;           // batched: per-step log-likelihood pieces
+  double* lane_ll;           // [1 + D + D(D+1)/2][P0] log-likelihood-only path: per chunk the
+                             // log-likelihood of its first series piece given the state 0, eta, J
   // gradient (adjoint) mode
   int adj;                   // 1: the filter pass stores rec_adj and folds the mean-adjoint aggregate
   double* rec_adj;           // [n][adjs] predicted moments, v, 1/S
@@ -466,11 +468,35 @@ __global__ void __launch_bounds__(128) k_segment_pieces(const double* v, int nv,
   for (int i = 0; i < nv; ++i) out[(int64_t)s * ostride + i] = acc[i];
 }
 
+// natural log of a product of positive numbers kept as mantissa and binary
+// exponent: one multiply per factor instead of one logarithm
+struct LogProd {
+  double mant = 1.0;
+  long long expo = 0;
+  __device__ __forceinline__ void mul(double s) {
+    mant *= s;
+    const long long b = __double_as_longlong(mant);
+    expo += ((b >> 52) & 0x7ff) - 1023;
+    mant = __longlong_as_double((b & ~(0x7ffLL << 52)) | (1023LL << 52));
+  }
+  __device__ __forceinline__ double ln() const { return ::log(mant) + (double)expo * 0.69314718055994530942; }
+};
+
+// log-likelihood of nobs observed steps from log prod S and sum v^2/S
+__device__ __forceinline__ double ll_piece(int nobs, const LogProd& lp, double qsum) {
+  return (nobs > 0) ? -0.5 * ((double)nobs * 1.8378770664093454836 + lp.ln() + qsum) : 0.0;
+}
+
 // shared memory of k_filter_reduce: A (two buffers), J (packed) and eta per
 // thread, entry-major with stride BLOCK
 template <int D> constexpr int reduce_smem_doubles() { return (2 * D * D + Sym<D>::N + D) * BLOCK; }
 
-template <int D>
+// LL: also the log-likelihood of the chunk's observations given the state 0
+// before it (the terms of the fold's zero-start Kalman filter), split where a
+// series starts inside the chunk; pieces after the first are exact and written
+// to ll_step, the first goes with the lane's own (eta, J) to lane_ll for
+// k_filter_llfinish.
+template <int D, bool LL>
 __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m, const ScanArgs a) {
   extern __shared__ double smem[];
   double* sA0 = smem + threadIdx.x;
@@ -498,18 +524,51 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
   double* Ain = sA0;
   double* Aout = sA1;
   const double R0 = a.R ? a.R[0] : a.R_scalar;
+  double qsum = 0.0, cfirst = 0.0;
+  LogProd lp;
+  int nobs = 0;
+  bool first = true;
+  int64_t lpos = k0;
 #pragma unroll 1
   for (int64_t k = k0; k < k1; ++k) {
+    if constexpr (LL) {
+      if (a.ll_step && k > k0 && a.seg_start[k]) {   // a series starts inside the chunk
+        const double piece = ll_piece(nobs, lp, qsum);
+        if (first) cfirst = piece;
+        else a.ll_step[lpos] = piece;
+        first = false;
+        lpos = k;
+        nobs = 0;
+        qsum = 0.0;
+        lp = LogProd();
+      }
+    }
     Mat<D> F, Q;
     load_fq<D>(a.rec_fq, k, F, Q);
     const bool obs = a.mask[k] != 0;
     const double yk = a.y[k];
     const double Rk = a.R_per_step ? a.R[k] : R0;
     if (obs && nonfinite(yk)) bits |= PSSGP_ENAN;
-    fagg_fold_step_smem<D, BLOCK>(b, C, Ain, Aout, sJ, seta, F, Q, obs, yk, Rk, bad);
+    double S, Si, r;
+    fagg_fold_step_smem<D, BLOCK>(b, C, Ain, Aout, sJ, seta, F, Q, obs, yk, Rk, bad, S, Si, r);
+    if constexpr (LL) {
+      qsum = fma(r * Si, r, qsum);
+      lp.mul(obs ? S : 1.0);
+      nobs += obs ? 1 : 0;
+    }
     double* tsw = Ain;
     Ain = Aout;
     Aout = tsw;
+  }
+  if constexpr (LL) {
+    const double piece = ll_piece(nobs, lp, qsum);
+    if (first) cfirst = piece;
+    else a.ll_step[lpos] = piece;
+    a.lane_ll[g] = cfirst;
+#pragma unroll
+    for (int i = 0; i < D; ++i) a.lane_ll[(1 + i) * a.P0 + g] = seta[i * BLOCK];
+#pragma unroll
+    for (int e = 0; e < Sym<D>::N; ++e) a.lane_ll[(1 + D + e) * a.P0 + g] = sJ[e * BLOCK];
   }
   FAgg<D> ag;
 #pragma unroll
@@ -564,23 +623,118 @@ __global__ void __launch_bounds__(BLOCK) k_filter_ks(const double* in, double* o
   if (!ok && lane == 0) flag(status, PSSGP_ENOTPD);
 }
 
-// natural log of a product of positive numbers kept as mantissa and binary
-// exponent: one multiply per factor instead of one logarithm
-struct LogProd {
-  double mant = 1.0;
-  long long expo = 0;
-  __device__ __forceinline__ void mul(double s) {
-    mant *= s;
-    const long long b = __double_as_longlong(mant);
-    expo += ((b >> 52) & 0x7ff) - 1023;
-    mant = __longlong_as_double((b & ~(0x7ffLL << 52)) | (1023LL << 52));
+// Log-likelihood of a chunk's observations given the filter state N(x, P)
+// before it.  For a state z before the chunk, the chunk's aggregate gives
+// log p(y | z) = c + eta^T z - z^T J z / 2 exactly (c: the log-likelihood the
+// fold accumulates from the state 0; eta, J: Sec. 3's information terms), and
+// the Gaussian integral over z ~ N(x, P) is
+//   c + eta^T x - x^T J x / 2 + r^T (I + P J)^{-1} P r / 2 - log det(I + P J) / 2,
+//   r = eta - J x.
+// Returns false if a pivot of I + P J is zero or its determinant is not
+// positive (it is at least 1 for P, J positive semi-definite).
+template <int D>
+__device__ __noinline__ bool chunk_loglik(const Vec<D>& x, const Mat<D>& P, const Vec<D>& eta, const Mat<D>& J,
+                                          double c, double& out) {
+  Vec<D> r;
+  double lin = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double jx = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) jx = fma(J[i][k], x[k], jx);
+    r[i] = eta[i] - jx;
+    lin = fma(x[i], fma(-0.5, jx, eta[i]), lin);
   }
-  __device__ __forceinline__ double ln() const { return ::log(mant) + (double)expo * 0.69314718055994530942; }
-};
+  Mat<D> M;
+  double X[D][1];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) s = fma(P[i][k], r[k], s);
+    X[i][0] = s;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double t = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) t = fma(P[i][k], J[k][j], t);
+      M[i][j] = t;
+    }
+  }
+  int perm[D];
+  double invd[D];
+  bool ok = lu_factor<D>(M, perm, invd);
+  lu_solve<D, 1>(M, perm, invd, X);
+  double quad = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) quad = fma(r[i], X[i][0], quad);
+  LogProd ld;
+  int neg = 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    if (perm[i] != i) ++neg;
+    if (M[i][i] < 0.0) ++neg;
+    ld.mul(fabs(M[i][i]));
+  }
+  if (neg & 1) ok = false;
+  out = c + lin + 0.5 * quad - 0.5 * ld.ln();
+  return ok;
+}
 
-// log-likelihood of nobs observed steps from log prod S and sum v^2/S
-__device__ __forceinline__ double ll_piece(int nobs, const LogProd& lp, double qsum) {
-  return (nobs > 0) ? -0.5 * ((double)nobs * 1.8378770664093454836 + lp.ln() + qsum) : 0.0;
+// log-likelihood-only path, after level 2 (replaces the propagate pass): the
+// filter state before each chunk from the scan, then the chunk's first series
+// piece by chunk_loglik, per lane (llp) and, batched, as the piece at the
+// chunk's first step
+template <int D>
+__global__ void __launch_bounds__(BLOCK) k_filter_llfinish(const DevModel<D> m, const ScanArgs a) {
+  const int64_t g = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t w = g >> 5;
+  const int64_t k0 = g * a.L;
+  const int64_t k1 = min(k0 + a.L, a.n);
+  if (k1 <= k0) {
+    a.llp[g] = 0.0;
+    return;
+  }
+  bool bad = false;
+  Vec<D> x;
+  Mat<D> P;
+#pragma unroll
+  for (int i = 0; i < D; ++i) x[i] = 0.0;
+  set_zero<D>(P);
+  if (w > 0) {
+    FAgg<D> W;
+    load_fagg<D>(a.wfin_f + (w - 1), a.P2, W);
+#pragma unroll
+    for (int i = 0; i < D; ++i) x[i] = W.b[i];
+    copy<D>(W.C, P);
+  }
+  if (lane > 0) {
+    FAgg<D> I;
+    load_fagg<D>(a.lagg_f + (g - 1), a.P0, I);
+    Vec<D> x2;
+    Mat<D> P2;
+    if (!fstate_combine<D>(x, P, I, x2, P2)) bad = true;
+#pragma unroll
+    for (int i = 0; i < D; ++i) x[i] = x2[i];
+    copy<D>(P2, P);
+  }
+  Vec<D> eta;
+  Mat<D> J;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    eta[i] = a.lane_ll[(1 + i) * a.P0 + g];
+#pragma unroll
+    for (int j = i; j < D; ++j) {
+      J[i][j] = a.lane_ll[(1 + D + pidx<D>(i, j)) * a.P0 + g];
+      J[j][i] = J[i][j];
+    }
+  }
+  double ll;
+  if (!chunk_loglik<D>(x, P, eta, J, a.lane_ll[g], ll)) bad = true;
+  a.llp[g] = ll;
+  if (a.ll_step) a.ll_step[k0] = ll;
+  if (bad) flag(a.status, PSSGP_ENOTPD);
 }
 
 // filter level 3 (+ smoother levels 0/1 when fused)
@@ -1321,6 +1475,7 @@ ScanArgs base_args(const Plan& p, void* ws) {
   a.lagg_f = reinterpret_cast<double*>(ws_ptr(ws, p.o_laggf));
   a.wagg_f = reinterpret_cast<double*>(ws_ptr(ws, p.o_waggf));
   a.lagg_s = reinterpret_cast<double*>(ws_ptr(ws, p.o_laggs));
+  a.lane_ll = a.lagg_s;   // [1 + d + d(d+1)/2][P0] fits in the smoother's [ns][P0], unused without a smoother
   a.wagg_s = reinterpret_cast<double*>(ws_ptr(ws, p.o_waggs));
   a.llp = reinterpret_cast<double*>(ws_ptr(ws, p.o_llp));
   a.status = reinterpret_cast<int*>(ws_ptr(ws, p.o_status));
@@ -1374,8 +1529,11 @@ struct BatchArgs {
   uint8_t* seg;
 };
 
+// ll_only: the log-likelihood alone (reduce with the zero-start terms, level
+// 2, k_filter_llfinish) instead of the propagate pass
 template <int D>
-void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s, const BatchArgs* bt = nullptr) {
+void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s, const BatchArgs* bt = nullptr,
+                bool ll_only = false) {
   const int grid = (int)(p.P0 / BLOCK);
   {
     Timed tm(s, T_DISC);
@@ -1396,12 +1554,19 @@ void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s
   }
   {
     constexpr int smem = reduce_smem_doubles<D>() * 8;
-    cudaFuncSetAttribute(k_filter_reduce<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto kern = ll_only ? k_filter_reduce<D, true> : k_filter_reduce<D, false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     Timed tm(s, T_FRED);
-    k_filter_reduce<D><<<grid, BLOCK, smem, s>>>(m, a);
+    kern<<<grid, BLOCK, smem, s>>>(m, a);
     after_launch();
   }
   a.wfin_f = run_filter_level2<D>(p, a.wagg_f, a.status, s);
+  if (ll_only) {
+    Timed tm(s, T_LLC);
+    k_filter_llfinish<D><<<grid, BLOCK, 0, s>>>(m, a);
+    after_launch();
+    return;
+  }
   {
     const int psmem = (a.fuse_smoother ? propagate_smem_doubles<D, PROP_FUSE>() : propagate_smem_doubles<D, PROP_PLAIN>()) * 8;
     auto kern = a.adj ? k_filter_propagate<D, PROP_ADJ>
@@ -1508,9 +1673,11 @@ int filter_common(const pssgp_model* model, const double* t, const double* y, co
   a.fuse_smoother = 0;
   a.dbg_agg = dbg;
   if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess) return PSSGP_ECUDA;
+  // without per-step outputs the log-likelihood needs no propagate pass
+  const bool ll_only = !xf && !Pf && !dbg;
   PSSGP_DISPATCH(model->d, {
     const DevModel<D> m = dev_model<D>(model);
-    run_filter<D>(m, p, a, s);
+    run_filter<D>(m, p, a, s, nullptr, ll_only);
   });
   if (loglik) {
     Timed tm(s, T_LL);
@@ -1610,7 +1777,7 @@ extern "C" int pssgp_loglik_batched(const pssgp_model* model, const int64_t* off
   if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess) return PSSGP_ECUDA;
   PSSGP_DISPATCH(model->d, {
     const DevModel<D> m = dev_model<D>(model);
-    run_filter<D>(m, p, a, s, &bt);
+    run_filter<D>(m, p, a, s, &bt, true);
   });
   {
     Timed tm(s, T_LL);

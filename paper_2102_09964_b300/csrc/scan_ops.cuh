@@ -396,12 +396,15 @@ __device__ __forceinline__ void fagg_fold_step(FAgg<D>& a, const Mat<D>& F, cons
 // shared memory (A double-buffered, J and eta; element e of a thread's
 // matrix at ptr[e * SST], so a warp's accesses hit 32 consecutive banks).
 // P^- = F C F^T + Q is built one row of F C at a time, and A' = F A row by
-// row, which keeps the register footprint low enough to avoid spills.
+// row.  Returns the step's S = H P^- H^T + R, 1/S and innovation r = y - H F b
+// (1/S = r = 0 on a missing step): the terms of the chunk's log-likelihood
+// given the state 0 before it.
 template <int D, int SST>
 __device__ __forceinline__ void fagg_fold_step_smem(Vec<D>& b, Mat<D>& C, const double* __restrict__ Ain,
                                                     double* __restrict__ Aout, double* __restrict__ J,
                                                     double* __restrict__ eta, const Mat<D>& F, const Mat<D>& Q,
-                                                    bool observed, double y, double R, bool& bad) {
+                                                    bool observed, double y, double R, bool& bad, double& S_out,
+                                                    double& Si_out, double& r_out) {
   Mat<D> Pm;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -439,6 +442,9 @@ __device__ __forceinline__ void fagg_fold_step_smem(Vec<D>& b, Mat<D>& C, const 
   if (observed && bad_pos(S)) bad = true;
   const double Si = observed ? __drcp_rn(S) : 0.0;
   const double r = observed ? y - bm[0] : 0.0;
+  S_out = S;
+  Si_out = Si;
+  r_out = r;
   Vec<D> K;
 #pragma unroll
   for (int i = 0; i < D; ++i) K[i] = Pm[i][0] * Si;

@@ -138,8 +138,10 @@ def test_filter_and_smoother_states(kind, n):
     assert P.status(ws2) == 0
     check_marginals(host(fm), host(fv), None, res.f_mean, res.f_var, None, s.N, TOL[kind], "smooth")
     check_states(host(xs).T, unpack(host(Ps), d), res.ms, res.Ps, 10 * TOL[kind], "smooth states")
+    # the log-likelihood entry point sums per chunk from the fold's zero-start
+    # terms (no propagate pass): the same value up to the summation order
     ll2, _ = P.loglik(m, tg, yg, mg, 0.01)
-    assert float(host(ll2)[0]) == float(host(ll)[0])
+    assert abs(float(host(ll2)[0]) - float(host(ll)[0])) <= 1e-11 * max(abs(float(host(ll)[0])), s.N)
 
 
 @pytest.mark.parametrize("kind", ["matern32", "matern52", "rbf"])
