@@ -423,9 +423,9 @@ def fit_bench(args, P, wl):
                        "lengths log-uniform [4096, 65536]; plain init l = s2 = R = 1",
            "train_s": round(train_s, 3), "train_loss_final": float(losses[-64:].mean().item()),
            "heldout_steps": int(ho[-1])}
-    runs = [("lbfgs", dict(method="lbfgs", patience=3, tol=1e-9, max_iter=500, check_every=5))]
+    runs = [("lbfgs", dict(method="lbfgs", patience=3, tol=1e-9, max_iter=500, check_every=1))]
     if args.fit_adam:
-        runs.append(("adam", dict(method="adam", patience=10, tol=1e-7, max_iter=2000, check_every=25)))
+        runs.append(("adam", dict(method="adam", patience=10, tol=1e-7, max_iter=2000, check_every=1)))
     for name, kw in runs:
         r = L.compare_fits(net, m, ho, t, y, **kw)
         out[name] = {"plain": r["plain"], "learned": r["learned"],

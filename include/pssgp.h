@@ -365,7 +365,9 @@ typedef struct pssgp_fit_options {
   double lr;             /* Adam step on the log hyperparameters (e.g. 0.05)     */
   double beta1, beta2, eps;  /* Adam constants (0.9, 0.999, 1e-8)               */
   int32_t check_every;   /* read the converged flags and drop converged series  */
-                         /*   from the scans every this many iterations         */
+                         /*   from the scans every this many iterations (1 is  */
+                         /*   usually fastest: the read is B bytes, and frozen */
+                         /*   series still cost a full evaluation each)        */
   int32_t method;        /* PSSGP_FIT_ADAM, or PSSGP_FIT_LBFGS: limited-memory
                           * BFGS (6 pairs) with Armijo backtracking, steps of
                           * at most 2 in every log parameter; the convergence

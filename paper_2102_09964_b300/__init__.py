@@ -349,7 +349,7 @@ FIT_ADAM, FIT_LBFGS = 0, 1
 
 
 def fit_batched(model: Model, offsets, t, y, mask, theta0, max_iter=2000, patience=10, tol=1e-7, lr=0.05,
-                beta1=0.9, beta2=0.999, eps=1e-8, check_every=25, ws=None, method="adam"):
+                beta1=0.9, beta2=0.999, eps=1e-8, check_every=1, ws=None, method="adam"):
     """Adam (method="adam") or L-BFGS (method="lbfgs") fit of every series'
     (log l, log s2, log R) on its exact log marginal likelihood (native driver).  offsets: host int64 array [B+1];
     t, y, mask: device arrays; theta0: [B, 3] start (log values).
