@@ -450,23 +450,37 @@ __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_batched(const DevMode
 }
 
 // per-series sums of pieces written at the first step of every (lane chunk,
-// series) pair: for series [a, b) the positions a and every chunk start g L
-// in (a, b), summed in that order (deterministic); nothing else of v is read.
-// nv arrays of stride n at once, out[s * ostride + i] for array i.
-__global__ void __launch_bounds__(128) k_segment_pieces(const double* v, int nv, int64_t n, int64_t L,
-                                                       const int64_t* offsets, int B, double* out, int ostride) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= B) return;
+// series) pair: for series [a, b) the positions a and every chunk start c L
+// in (a, b); nothing else of v is read.  One warp per series: lane j adds the
+// pieces j, j + 32, ... of that list, then a fixed shuffle tree adds the lanes
+// (deterministic).  nv <= 4 arrays of stride n at once, out[s * ostride + i]
+// for array i.
+constexpr int SEG_WARPS = 4;   // series per 128-thread block
+__global__ void __launch_bounds__(32 * SEG_WARPS) k_segment_pieces(const double* v, int nv, int64_t n, int64_t L,
+                                                                 const int64_t* offsets, int B, double* out,
+                                                                 int ostride) {
+  const int s = blockIdx.x * SEG_WARPS + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= B) return;                                         // the whole warp
   const int64_t a = min(max(offsets[s], (int64_t)0), n);     // clamped: bad offsets are
   const int64_t b = min(max(offsets[s + 1], a), n);           // flagged by k_discretize_batched
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   if (b > a) {
-    for (int i = 0; i < nv; ++i) acc[i] = v[(int64_t)i * n + a];
-    for (int64_t k = (a / L + 1) * L; k < b; k += L)
+    const int64_t c0 = a / L + 1;                  // first chunk starting after a
+    const int64_t np = 1 + (b - 1) / L - a / L;    // a, and the chunk starts c L with c0 <= c <= (b - 1) / L
+    for (int64_t j = lane; j < np; j += 32) {
+      const int64_t k = (j == 0) ? a : (c0 + j - 1) * L;
       for (int i = 0; i < nv; ++i) acc[i] += v[(int64_t)i * n + k];
+    }
   }
-  for (int i = 0; i < nv; ++i) out[(int64_t)s * ostride + i] = acc[i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], off);
+  if (lane == 0)
+    for (int i = 0; i < nv; ++i) out[(int64_t)s * ostride + i] = acc[i];
 }
+unsigned segment_grid(int B) { return (unsigned)((B + SEG_WARPS - 1) / SEG_WARPS); }
 
 // natural log of a product of positive numbers kept as mantissa and binary
 // exponent: one multiply per factor instead of one logarithm
@@ -1781,7 +1795,7 @@ extern "C" int pssgp_loglik_batched(const pssgp_model* model, const int64_t* off
   });
   {
     Timed tm(s, T_LL);
-    k_segment_pieces<<<(unsigned)((B + 127) / 128), 128, 0, s>>>(a.ll_step, 1, n, p.L, offsets, B, loglik, 1);
+    k_segment_pieces<<<segment_grid(B), 32 * SEG_WARPS, 0, s>>>(a.ll_step, 1, n, p.L, offsets, B, loglik, 1);
     after_launch();
   }
   return end_call();
@@ -1851,12 +1865,12 @@ extern "C" int pssgp_loglik_grad_batched(const pssgp_model* model, const int64_t
   });
   {
     Timed tm(s, T_LL);
-    const unsigned sg = (unsigned)((B + 127) / 128);
+    const unsigned sg = segment_grid(B);
     if (loglik) {
-      k_segment_pieces<<<sg, 128, 0, s>>>(a.ll_step, 1, n, p.L, offsets, B, loglik, 1);
+      k_segment_pieces<<<sg, 32 * SEG_WARPS, 0, s>>>(a.ll_step, 1, n, p.L, offsets, B, loglik, 1);
       after_launch();
     }
-    k_segment_pieces<<<sg, 128, 0, s>>>(a.g_step, 3, n, p.L, offsets, B, grad, 3);
+    k_segment_pieces<<<sg, 32 * SEG_WARPS, 0, s>>>(a.g_step, 3, n, p.L, offsets, B, grad, 3);
     after_launch();
   }
   return end_call();
