@@ -265,11 +265,26 @@ def cpu_baseline(wl_params, n_sample_train=1 << 19):
                       f"{dt:.1f} s wall; long-double sequential KF + RTS, discretisation on {cores} threads"}
 
 
+def workload_config(workload, d, n):
+    """The `config` object of both arms' JSON lines."""
+    return {"workload": f"{workload}: N=2^20 training times U[0,1000] + M=10^4 prediction times, "
+                        f"y=sin(0.3t)+0.5sin(1.7t)+N(0,0.1^2), d={d}, l=1, s2=1, R=0.01; "
+                        "one pssgp_predict (merge+filter+smoother+gather+loglik) per step",
+            "merged_steps": n, "per_rank_replica": True,
+            "l2": "workspace traffic ~1 GB per step exceeds the 126 MB L2 (no explicit flush)"}
+
+
 def run_reference(args, wl_params):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    import workloads as wl
+    from oracle import model as om
     cb = cpu_baseline(wl_params, n_sample_train=1 << 15)
+    full = wl.sinusoid_large()
+    n_full = int(full.N + full.M)       # merged steps of the timed workload (the sample is a prefix)
+    d = om.make_model(wl_params["kind"], wl_params["lengthscale"], wl_params["variance"],
+                      order=wl_params["order"] or 6).d
     times = []
     for i in range(args.warmup + args.steps):
         c = cpu_baseline(wl_params, n_sample_train=1 << 15)
@@ -279,7 +294,7 @@ def run_reference(args, wl_params):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: sampled prefix of the 2^20+10^4 noisy-sinusoid series"},
+            "config": workload_config(args.workload, d, n_full),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -630,11 +645,7 @@ def run_ours(args, wl_params):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: N=2^20 training times U[0,1000] + M=10^4 prediction times, "
-                                   f"y=sin(0.3t)+0.5sin(1.7t)+N(0,0.1^2), d={d}, l=1, s2=1, R=0.01; "
-                                   "one pssgp_predict (merge+filter+smoother+gather+loglik) per step",
-                       "merged_steps": n, "per_rank_replica": True,
-                       "l2": "workspace traffic ~1 GB per step exceeds the 126 MB L2 (no explicit flush)"},
+            "config": workload_config(args.workload, d, n),
             "e2e": e2e, "gpu_launches": int(gpu_launches), "clocks": clocks, "roofline": roofline,
             "whole_path_tflops": round(whole, 4), "kernels": kernels}
     if not args.no_batched:
