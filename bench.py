@@ -37,8 +37,8 @@ METRIC = "filter+smoother time steps/s at N=2^20,d=6 FP64"
 # current kernels on a 2^18-step case (profiles/fp64_instruction_counts_rbf6_n264k.md);
 # traffic grows in proportion to the steps, so a launch's traffic is this x n.
 # Reset an entry to None whenever its kernel changes.
-PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1363.0, "filter_reduce": 1354.0, "discretize": 371.0,
-                                "smoother_propagate": 560.0}
+PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1240.0, "filter_reduce": 1377.0, "discretize": 371.0,
+                                "smoother_propagate": 524.0}
 UNIT = "steps/s"
 WORKLOADS = {
     "rbf6": dict(kind="rbf", order=6, lengthscale=1.0, variance=1.0, noise=0.01),
@@ -95,19 +95,17 @@ def flops_kf_step(d, observed_frac):
 
 
 def flops_smoother_element(d):
+    """E, g, L from P^- = Lu diag(dd) Lu^T (square-root free; one reciprocal
+    per pivot): W = Lu^{-1} T, V = diag(1/dd) W, L = P - W^T V,
+    E^T = Lu^{-T} V, g = x - E x^-."""
     s = d * (d + 1) // 2
-    chol = sum(2 * j + 1 + (d - 1 - j) * (2 * j + 1) for j in range(d)) + d   # + d reciprocal square roots
-    return chol + 2 * d ** 3 + 2 * d * d + 2 * s * d                       # W, E^T, g, L
+    ldl = sum(2 * j + 1 + (d - 1 - j) * (2 * j + 1) for j in range(d))
+    return ldl + 2 * d * d * (d - 1) + d * d + 2 * s * d + 2 * d * d
 
 
 def flops_smoother_fold(d):
     s = d * (d + 1) // 2
     return (2 * d ** 3 - d * d) * 2 + 2 * d * d + 2 * s * d                # E_a E, E_a L, E_a g + g_a, (.)E_a^T + L_a
-
-
-def flops_fixed_point(d, observed_frac):
-    s = d * (d + 1) // 2
-    return (2 * d ** 3 - d * d) + observed_frac * (4 * d + 2 * s + 2 * d * d)   # Sig F^T, rank-one updates
 
 
 def flops_rts_step(d):
@@ -622,7 +620,8 @@ def run_ours(args, wl_params):
     alg = {
         "discretize": n * flops_discretize(d, kf, kq, bool(m.raw.companion)),
         "filter_reduce": n * flops_filter_fold(d, obs),
-        "filter_propagate": n * (flops_kf_step(d, obs) + flops_smoother_element(d) + flops_fixed_point(d, obs)),
+        # the smoother chunk aggregate is formed once per lane (not per step)
+        "filter_propagate": n * (flops_kf_step(d, obs) + flops_smoother_element(d)),
         "smoother_propagate": n * flops_rts_step(d),
     }
     ts = max(args.timing_steps, 1)

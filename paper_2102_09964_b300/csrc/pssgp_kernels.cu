@@ -219,6 +219,8 @@ struct ScanArgs {
   double* ll_step;           // batched: per-step log-likelihood pieces
   double* lane_ll;           // [1 + D + D(D+1)/2][P0] log-likelihood-only path: per chunk the
                              // log-likelihood of its first series piece given the state 0, eta, J
+  double* lane_fp;           // [D*D + D + D(D+1)/2][P0] fused smoother: (A, eta, J) of the filter
+                             // aggregate of the lane's steps but the last (all of them in the last lane)
   // gradient (adjoint) mode
   int adj;                   // 1: the filter pass stores rec_adj and folds the mean-adjoint aggregate
   double* rec_adj;           // [n][adjs] predicted moments, v, 1/S
@@ -277,6 +279,22 @@ __device__ __forceinline__ void store_egl(double* rec, int64_t k, const SAgg<D>&
 #pragma unroll
     for (int j = i; j < D; ++j) p[D * D + D + pidx<D>(i, j)] = e.L[i][j];
 }
+// a symmetric matrix, packed upper, in shared memory (entry e at p[e * SST])
+template <int D, int SST>
+__device__ __forceinline__ void store_sym_smem(double* p, const Mat<D>& M) {
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) p[pidx<D>(i, j) * SST] = M[i][j];
+}
+template <int D, int SST>
+__device__ __forceinline__ void load_sym_smem(const double* p, Mat<D>& M) {
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) { M[i][j] = p[pidx<D>(i, j) * SST]; M[j][i] = M[i][j]; }
+}
+
 // smoother_element() written to the record of step k as it is formed:
 // W = Lu^{-1} T in place of T, L = P - W^T V with V = diag(rd) W (V replaces
 // W row by row), then E row by row with g (row j of E = Lu^{-T} applied to column j of V), so that at
@@ -505,13 +523,31 @@ __device__ __forceinline__ double ll_piece(int nobs, const LogProd& lp, double q
 // thread, entry-major with stride BLOCK
 template <int D> constexpr int reduce_smem_doubles() { return (2 * D * D + Sym<D>::N + D) * BLOCK; }
 
-// LL: also the log-likelihood of the chunk's observations given the state 0
-// before it (the terms of the fold's zero-start Kalman filter), split where a
-// series starts inside the chunk; pieces after the first are exact and written
-// to ll_step, the first goes with the lane's own (eta, J) to lane_ll for
-// k_filter_llfinish.
-template <int D, bool LL>
+// RMODE:
+//  RED_LL: also the log-likelihood of the chunk's observations given the
+//    state 0 before it (the terms of the fold's zero-start Kalman filter),
+//    split where a series starts inside the chunk; pieces after the first are
+//    exact and written to ll_step, the first goes with the lane's own (eta, J)
+//    to lane_ll for k_filter_llfinish.
+//  RED_SMOOTH: also (A, eta, J) of the aggregate of the lane's steps but the
+//    last (of all its steps in the lane holding the series' last step) to
+//    lane_fp, from which k_filter_propagate forms the smoother chunk aggregate.
+enum { RED_PLAIN = 0, RED_LL = 1, RED_SMOOTH = 2 };
+
+template <int D>
+__device__ __forceinline__ void save_fold_state(const ScanArgs& a, int64_t g, const double* A, const double* eta,
+                                                const double* J) {
+#pragma unroll
+  for (int e = 0; e < D * D; ++e) a.lane_fp[e * a.P0 + g] = A[e * BLOCK];
+#pragma unroll
+  for (int i = 0; i < D; ++i) a.lane_fp[(D * D + i) * a.P0 + g] = eta[i * BLOCK];
+#pragma unroll
+  for (int e = 0; e < Sym<D>::N; ++e) a.lane_fp[(D * D + D + e) * a.P0 + g] = J[e * BLOCK];
+}
+
+template <int D, int RMODE>
 __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m, const ScanArgs a) {
+  constexpr bool LL = RMODE == RED_LL;
   extern __shared__ double smem[];
   double* sA0 = smem + threadIdx.x;
   double* sA1 = sA0 + D * D * BLOCK;
@@ -557,6 +593,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
         lp = LogProd();
       }
     }
+    if constexpr (RMODE == RED_SMOOTH) {
+      if (k == k1 - 1 && k1 < a.n) save_fold_state<D>(a, g, Ain, seta, sJ);   // steps k0 .. k1-2
+    }
     Mat<D> F, Q;
     load_fq<D>(a.rec_fq, k, F, Q);
     const bool obs = a.mask[k] != 0;
@@ -573,6 +612,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
     double* tsw = Ain;
     Ain = Aout;
     Aout = tsw;
+  }
+  if constexpr (RMODE == RED_SMOOTH) {
+    if (k1 == a.n && k1 > k0) save_fold_state<D>(a, g, Ain, seta, sJ);      // the lane with the last step
   }
   if constexpr (LL) {
     const double piece = ll_piece(nobs, lp, qsum);
@@ -754,9 +796,11 @@ __global__ void __launch_bounds__(BLOCK) k_filter_llfinish(const DevModel<D> m, 
 // filter level 3 (+ smoother levels 0/1 when fused)
 // shared memory of k_filter_propagate: the fixed-point state Sig, V (packed),
 // mu per thread, entry-major with stride BLOCK
-// (+ the filter covariance P_k, packed, in the fused mode)
+// The fused mode uses them for the start state (x0 in mu, P0 in V) and F of
+// the lane's last step (in Sig), plus the filter covariance P_k (packed) and
+// the prediction (x^-, P^-) of the last step.
 template <int D, int MODE> constexpr int propagate_smem_doubles() {
-  return (D * D + Sym<D>::N + D + (MODE == 1 ? Sym<D>::N : 0)) * BLOCK;
+  return (D * D + Sym<D>::N + D + (MODE == 1 ? 2 * Sym<D>::N + D : 0)) * BLOCK;
 }
 
 // MODE: PROP_PLAIN (filter outputs / log-likelihood), PROP_FUSE (+ smoother
@@ -771,6 +815,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
   double* sV = sSig + D * D * BLOCK;
   double* smu = sV + Sym<D>::N * BLOCK;
   double* sP = smu + D * BLOCK;     // fused mode only
+  double* sxm1 = sP + Sym<D>::N * BLOCK;
+  double* sPm1 = sxm1 + D * BLOCK;
   const int64_t g = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int64_t w = g >> 5;
@@ -804,6 +850,11 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
   const double R0 = a.R ? a.R[0] : a.R_scalar;
   constexpr bool fuse = MODE == PROP_FUSE;
   constexpr bool adj = MODE == PROP_ADJ;
+  if constexpr (fuse) {   // the filter state before the chunk, for the smoother chunk aggregate
+#pragma unroll
+    for (int i = 0; i < D; ++i) smu[i * BLOCK] = x[i];
+    store_sym_smem<D, BLOCK>(sV, P);
+  }
   double qsum = 0.0;
   LogProd lp;
   int nobs = 0;
@@ -832,12 +883,16 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
     const double Si = obs ? __drcp_rn(S) : 0.0;
     const double v = obs ? a.y[k] - xm[0] : 0.0;
     if constexpr (fuse) {
-      if (k > k0) {
-        // smoother chunk aggregate by forward recursion (state in shared
-        // memory); first, so that F is dead before the smoother element
-        fixed_point_step_smem<D, BLOCK>(sSig, sV, smu, F, true, Pm, Si, v);   // Si = v = 0: no update
-        if (!smoother_element_store<D, BLOCK>(a.rec_egl, k - 1, x, sP, T, xm, Pm)) bad = true;
+      if (k == k1 - 1) {   // the prediction of the lane's last step closes the smoother chunk aggregate
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          sxm1[i * BLOCK] = xm[i];
+#pragma unroll
+          for (int j = 0; j < D; ++j) sSig[(i * D + j) * BLOCK] = F[i][j];
+        }
+        store_sym_smem<D, BLOCK>(sPm1, Pm);
       }
+      if (k > k0 && !smoother_element_store<D, BLOCK>(a.rec_egl, k - 1, x, sP, T, xm, Pm)) bad = true;
     }
     {
       Vec<D> K;
@@ -853,13 +908,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
     qsum = fma(v * Si, v, qsum);
     lp.mul(obs ? S : 1.0);
     nobs += obs ? 1 : 0;
-    if constexpr (fuse) {
-      if (k == k0) fixed_point_start_smem<D, BLOCK>(sSig, sV, smu, x, P);
-#pragma unroll
-      for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int j = i; j < D; ++j) sP[pidx<D>(i, j) * BLOCK] = P[i][j];
-    }
+    if constexpr (fuse) store_sym_smem<D, BLOCK>(sP, P);
     if constexpr (adj) {  // gradient: forward moments and the mean-adjoint chunk product
       store_adj<D>(a.rec_adj, k, xm, Pm, v, Si);
       Vec<D> Kv;
@@ -919,37 +968,97 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
     store_sagg<D>(a.lagg_s + g, a.P0, sa);
     if (lane == 0) store_sagg<D>(a.wagg_s + w, a.P2, sa);
   } else if constexpr (fuse) {
+    // The lane's smoother chunk is the elements k0-1 .. k1-2 (k0-1 .. n-1 in
+    // the lane with the last step; element -1 of lane 0 is void: its start
+    // state is 0).  Its aggregate p(x_{k0-1} | x_{k1-1}, y_{1:k1-2}) comes from
+    // the filter state (x0, P0) before the chunk and the filter aggregate
+    // (A, eta, J) of steps k0 .. k1-2 saved by k_filter_reduce: with
+    // M = I + P0 J,
+    //   mu  = M^{-1} (x0 + P0 eta) = E[x_{k0-1} | y_{1:k1-2}],
+    //   V   = M^{-1} P0            = Cov(x_{k0-1} | y_{1:k1-2}),
+    //   Sig = V A^T                = Cov(x_{k0-1}, x_{k1-2} | y_{1:k1-2})
+    // (A M^{-1} is the filter's closed-loop transition over those steps), and
+    // the prediction of step k1-1 closes it (fixed_point_finish).  The lane
+    // with the last step ends on the series' last element (E = 0), which
+    // gives E = 0, g = mu, L = V over all its steps.
     SAgg<D> sa;
     if (k1 > k0) {
-      // element of the chunk's last step (the transition into the next step,
-      // or E = 0, g = x, L = P at the end of the series) and the chunk aggregate
-      SAgg<D> e;
+      FixedPoint<D> fp;
+      {
+        Mat<D> P0, J, M;
+        Vec<D> eta;
+        load_sym_smem<D, BLOCK>(sV, P0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          eta[i] = a.lane_fp[(D * D + i) * a.P0 + g];
+#pragma unroll
+          for (int j = i; j < D; ++j) {
+            J[i][j] = a.lane_fp[(D * D + D + pidx<D>(i, j)) * a.P0 + g];
+            J[j][i] = J[i][j];
+          }
+        }
+        constexpr int NR = D + 1;
+        double X[D][NR];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          double sx = smu[i * BLOCK];
+#pragma unroll
+          for (int k = 0; k < D; ++k) sx = fma(P0[i][k], eta[k], sx);
+          X[i][0] = sx;
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            X[i][1 + j] = P0[i][j];
+            double t = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) t = fma(P0[i][k], J[k][j], t);
+            M[i][j] = t;
+          }
+        }
+        int perm[D];
+        double invm[D];
+        if (!lu_factor<D>(M, perm, invm)) bad = true;
+        lu_solve<D, NR>(M, perm, invm, X);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          fp.mu[i] = X[i][0];
+#pragma unroll
+          for (int j = 0; j < D; ++j) fp.V[i][j] = 0.5 * (X[i][1 + j] + X[j][1 + i]);
+        }
+      }
       if (k1 < a.n) {
-        Mat<D> F, Q, T, Pm, Lc;
-        Vec<D> xm;
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) s = fma(fp.V[i][k], a.lane_fp[(j * D + k) * a.P0 + g], s);
+            fp.Sig[i][j] = s;
+          }
+        Mat<D> F1, Pm1, Lc;
+        Vec<D> xm1;
         double invd[D];
-        load_fq<D>(a.rec_fq, k1, F, Q);
-        mulv<D>(F, x, xm);
-        mul<D>(F, P, T);
-        mul_Bt_sym_add<D>(T, F, Q, Pm);
-        if (!smoother_element<D>(x, P, T, xm, Pm, e)) bad = true;
-        if (!cholesky<D>(Pm, Lc, invd)) bad = true;
-        FixedPoint<D> fp;
-        fixed_point_load<D, BLOCK>(sSig, sV, smu, fp);
-        fixed_point_finish<D>(fp, F, xm, Lc, invd, sa);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          xm1[i] = sxm1[i * BLOCK];
+#pragma unroll
+          for (int j = 0; j < D; ++j) F1[i][j] = sSig[(i * D + j) * BLOCK];
+        }
+        load_sym_smem<D, BLOCK>(sPm1, Pm1);
+        if (!cholesky<D>(Pm1, Lc, invd)) bad = true;
+        fixed_point_finish<D>(fp, F1, xm1, Lc, invd, sa);
       } else {
-        FixedPoint<D> fp;
-        fixed_point_load<D, BLOCK>(sSig, sV, smu, fp);
+        SAgg<D> e;
         set_zero<D>(e.E);
 #pragma unroll
         for (int i = 0; i < D; ++i) e.g[i] = x[i];
         copy<D>(P, e.L);
+        store_egl<D>(a.rec_egl, k1 - 1, e);
         set_zero<D>(sa.E);
 #pragma unroll
         for (int i = 0; i < D; ++i) sa.g[i] = fp.mu[i];
         copy<D>(fp.V, sa.L);
       }
-      store_egl<D>(a.rec_egl, k1 - 1, e);
     } else {
       sagg_identity<D>(sa);
     }
@@ -992,6 +1101,25 @@ __global__ void __launch_bounds__(BLOCK) k_smoother_ks(const double* in, double*
   warp_sagg_combine<D>(sa, sb, work, out + i, P2, lane);
 }
 
+// smoother outputs of step k: f = H x = H D z = z_0 (the model is built with
+// H D = e_0^T), its variance, and optionally the state in SDE coordinates
+template <int D>
+__device__ __forceinline__ void smooth_out(const DevModel<D>& m, const ScanArgs& a, int64_t k, const Vec<D>& ms,
+                                           const Mat<D>& Ps) {
+  if (a.f_mean) a.f_mean[k] = ms[0];
+  if (a.f_var) a.f_var[k] = Ps[0][0];
+  if (a.xs) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) a.xs[i * a.ld + k] = ms[i] * m.Dsc[i];
+  }
+  if (a.Ps) {
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = i; j < D; ++j) a.Ps[pidx<D>(i, j) * a.ld + k] = Ps[i][j] * (m.Dsc[i] * m.Dsc[j]);
+  }
+}
+
 // smoother level 3: backward recursion through the chunk,
 // m^s_k = E_k m^s_{k+1} + g_k,  P^s_k = E_k P^s_{k+1} E_k^T + L_k
 template <int D>
@@ -1026,8 +1154,17 @@ __global__ void __launch_bounds__(BLOCK, 1) k_smoother_propagate(const DevModel<
     for (int i = 0; i < D; ++i) ms[i] = m2[i];
     copy<D>(P2, Ps);
   }
+  // With the fused filter pass a lane's smoother chunk is the elements
+  // k0-1 .. k1-2 (k0-1 .. n-1 in the lane with the last step), so the start
+  // above is the smoothed state of step k1-1 itself, which this lane writes;
+  // from pssgp_smooth the chunk is k0 .. k1-1 and the start is step k1's.
+  int64_t khi = k1 - 1;
+  if (a.fuse_smoother && k1 < a.n) {
+    smooth_out<D>(m, a, k1 - 1, ms, Ps);
+    khi = k1 - 2;
+  }
 #pragma unroll 1
-  for (int64_t k = k1 - 1; k >= k0; --k) {
+  for (int64_t k = khi; k >= k0; --k) {
     SAgg<D> e;
     load_egl<D>(a.rec_egl, k, e);
     Vec<D> m2;
@@ -1038,19 +1175,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_smoother_propagate(const DevModel<
 #pragma unroll
     for (int i = 0; i < D; ++i) ms[i] = m2[i];
     copy<D>(P2, Ps);
-    // f = H x = H D z = z_0 (the model is built with H D = e_0^T)
-    if (a.f_mean) a.f_mean[k] = ms[0];
-    if (a.f_var) a.f_var[k] = Ps[0][0];
-    if (a.xs) {
-#pragma unroll
-      for (int i = 0; i < D; ++i) a.xs[i * a.ld + k] = ms[i] * m.Dsc[i];
-    }
-    if (a.Ps) {
-#pragma unroll
-      for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int j = i; j < D; ++j) a.Ps[pidx<D>(i, j) * a.ld + k] = Ps[i][j] * (m.Dsc[i] * m.Dsc[j]);
-    }
+    smooth_out<D>(m, a, k, ms, Ps);
   }
 }
 
@@ -1490,6 +1615,9 @@ ScanArgs base_args(const Plan& p, void* ws) {
   a.wagg_f = reinterpret_cast<double*>(ws_ptr(ws, p.o_waggf));
   a.lagg_s = reinterpret_cast<double*>(ws_ptr(ws, p.o_laggs));
   a.lane_ll = a.lagg_s;   // [1 + d + d(d+1)/2][P0] fits in the smoother's [ns][P0], unused without a smoother
+  // [ns][P0]: written by k_filter_reduce, read by each k_filter_propagate thread
+  // from its own slot before it writes its smoother aggregate there
+  a.lane_fp = a.lagg_s;
   a.wagg_s = reinterpret_cast<double*>(ws_ptr(ws, p.o_waggs));
   a.llp = reinterpret_cast<double*>(ws_ptr(ws, p.o_llp));
   a.status = reinterpret_cast<int*>(ws_ptr(ws, p.o_status));
@@ -1568,7 +1696,8 @@ void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s
   }
   {
     constexpr int smem = reduce_smem_doubles<D>() * 8;
-    auto kern = ll_only ? k_filter_reduce<D, true> : k_filter_reduce<D, false>;
+    auto kern = ll_only ? k_filter_reduce<D, RED_LL>
+                        : a.fuse_smoother ? k_filter_reduce<D, RED_SMOOTH> : k_filter_reduce<D, RED_PLAIN>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     Timed tm(s, T_FRED);
     kern<<<grid, BLOCK, smem, s>>>(m, a);
