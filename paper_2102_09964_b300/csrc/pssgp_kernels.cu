@@ -532,7 +532,12 @@ template <int D> constexpr int reduce_smem_doubles() { return (2 * D * D + Sym<D
 //  RED_SMOOTH: also (A, eta, J) of the aggregate of the lane's steps but the
 //    last (of all its steps in the lane holding the series' last step) to
 //    lane_fp, from which k_filter_propagate forms the smoother chunk aggregate.
-enum { RED_PLAIN = 0, RED_LL = 1, RED_SMOOTH = 2 };
+//  RED_ADJ: the chunk's first step folded with its transition left out
+//    (F = I, Q = 0): the aggregate then takes the predicted state of the
+//    chunk's first step as input; its (A, eta, J) go to lane_fp (for the
+//    mean-adjoint chunk aggregate of k_filter_propagate), and the transition
+//    is put back in front (one operator application) for the scan.
+enum { RED_PLAIN = 0, RED_LL = 1, RED_SMOOTH = 2, RED_ADJ = 3 };
 
 template <int D>
 __device__ __forceinline__ void save_fold_state(const ScanArgs& a, int64_t g, const double* A, const double* eta,
@@ -598,6 +603,12 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
     }
     Mat<D> F, Q;
     load_fq<D>(a.rec_fq, k, F, Q);
+    if constexpr (RMODE == RED_ADJ) {
+      if (k == k0) {   // from the predicted state of step k0: no transition
+        set_eye<D>(F);
+        set_zero<D>(Q);
+      }
+    }
     const bool obs = a.mask[k] != 0;
     const double yk = a.y[k];
     const double Rk = a.R_per_step ? a.R[k] : R0;
@@ -615,6 +626,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
   }
   if constexpr (RMODE == RED_SMOOTH) {
     if (k1 == a.n && k1 > k0) save_fold_state<D>(a, g, Ain, seta, sJ);      // the lane with the last step
+  }
+  if constexpr (RMODE == RED_ADJ) {
+    if (k1 > k0) save_fold_state<D>(a, g, Ain, seta, sJ);
   }
   if constexpr (LL) {
     const double piece = ll_piece(nobs, lp, qsum);
@@ -636,6 +650,21 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
       ag.A[i][jj] = Ain[(i * D + jj) * BLOCK];
       ag.C[i][jj] = C[i][jj];
       ag.J[i][jj] = sJ[(i <= jj ? pidx<D>(i, jj) : pidx<D>(jj, i)) * BLOCK];
+    }
+  }
+  if constexpr (RMODE == RED_ADJ) {
+    if (k1 > k0) {   // the transition of step k0 in front: (F, 0, Q, 0, 0) x aggregate
+      FAgg<D> T, r;
+      load_fq<D>(a.rec_fq, k0, T.A, T.C);
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        T.b[i] = 0.0;
+        T.eta[i] = 0.0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) T.J[i][j] = 0.0;
+      }
+      if (!fagg_combine<D>(T, ag, r)) bad = true;
+      ag = r;
     }
   }
   if (a.dbg_agg) store_fagg<D>(a.dbg_agg + g, a.P0, ag);
@@ -909,13 +938,13 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
     lp.mul(obs ? S : 1.0);
     nobs += obs ? 1 : 0;
     if constexpr (fuse) store_sym_smem<D, BLOCK>(sP, P);
-    if constexpr (adj) {  // gradient: forward moments and the mean-adjoint chunk product
+    if constexpr (adj) {  // gradient: forward moments; the prediction of step k0 for the chunk aggregate
       store_adj<D>(a.rec_adj, k, xm, Pm, v, Si);
-      Vec<D> Kv;
+      if (k == k0) {
 #pragma unroll
-      for (int i = 0; i < D; ++i) Kv[i] = Pm[i][0] * Si;     // 0 on missing steps
-      if (k == k0) adj_fold_start<D, BLOCK>(sSig, smu);
-      adj_fold_step<D, BLOCK>(sSig, smu, F, k > k0, Kv, v * Si);
+        for (int i = 0; i < D; ++i) smu[i * BLOCK] = xm[i];
+        store_sym_smem<D, BLOCK>(sV, Pm);
+      }
     }
     if (a.xf) {
 #pragma unroll
@@ -931,20 +960,63 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
   a.llp[g] = ll_piece(nobs, lp, qsum);
   if (a.ll_step && k1 > k0) a.ll_step[lpos] = a.llp[g];
   if constexpr (adj) {
+    // The mean-adjoint chunk aggregate mb_{k0} = Pi mb_{k1} + gamma, with
+    // Pi^T = d m^-_{k1} / d m^-_{k0} and gamma the derivative of the chunk's
+    // log-likelihood by the predicted mean m^- of step k0, in closed form from
+    // the filter aggregate (A, eta, J) that takes the predicted state of step
+    // k0 as input (k_filter_reduce, RED_ADJ) and that prediction (m^-, P^-):
+    // the filtered mean of step k1-1 is A (I + P^- J)^{-1} (m^- + P^- eta) + b
+    // and the chunk's log-likelihood is Sec. 3's Gaussian integral, so with
+    // N = I + J P^-,
+    //   Pi = N^{-1} A^T F_{k1}^T,   gamma = N^{-1} (eta - J m^-)
+    // (F_{k1} = 0 after the last step; a series start inside the chunk gives
+    // A = 0 and freezes eta, J, as the recursion would).
     SAgg<D> sa;
     if (k1 > k0) {
-      // last factor: the transition into the next chunk's first step (none
-      // after the last step)
-      Mat<D> F1;
+      Mat<D> F1, J, N, Pm0;
+      Vec<D> eta;
       if (k1 < a.n) load_F<D>(a.rec_fq, k1, fqs_of<D>(), F1);
       else set_zero<D>(F1);
-      adj_fold_finish<D, BLOCK>(sSig, F1);
+      load_sym_smem<D, BLOCK>(sV, Pm0);
 #pragma unroll
       for (int i = 0; i < D; ++i) {
-        sa.g[i] = smu[i * BLOCK];
+        eta[i] = a.lane_fp[(D * D + i) * a.P0 + g];
+#pragma unroll
+        for (int j = i; j < D; ++j) {
+          J[i][j] = a.lane_fp[(D * D + D + pidx<D>(i, j)) * a.P0 + g];
+          J[j][i] = J[i][j];
+        }
+      }
+      constexpr int NR = D + 1;
+      double X[D][NR];
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        double gi = eta[i];
+#pragma unroll
+        for (int k = 0; k < D; ++k) gi = fma(-J[i][k], smu[k * BLOCK], gi);
+        X[i][0] = gi;
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-          sa.E[i][j] = sSig[(i * D + j) * BLOCK];
+          double t = (i == j) ? 1.0 : 0.0;   // N = I + J P^-
+#pragma unroll
+          for (int k = 0; k < D; ++k) t = fma(J[i][k], Pm0[k][j], t);
+          N[i][j] = t;
+          double u = 0.0;                    // (A^T F1^T)[i][j] = sum_k A[k][i] F1[j][k]
+#pragma unroll
+          for (int k = 0; k < D; ++k) u = fma(a.lane_fp[(k * D + i) * a.P0 + g], F1[j][k], u);
+          X[i][1 + j] = u;
+        }
+      }
+      int perm[D];
+      double invn[D];
+      if (!lu_factor<D>(N, perm, invn)) bad = true;
+      lu_solve<D, NR>(N, perm, invn, X);
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        sa.g[i] = X[i][0];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          sa.E[i][j] = X[i][1 + j];
           a.lane_pi[(i * D + j) * a.P0 + g] = sa.E[i][j];
           sa.L[i][j] = 0.0;
         }
@@ -1697,6 +1769,7 @@ void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s
   {
     constexpr int smem = reduce_smem_doubles<D>() * 8;
     auto kern = ll_only ? k_filter_reduce<D, RED_LL>
+                : a.adj ? k_filter_reduce<D, RED_ADJ>
                         : a.fuse_smoother ? k_filter_reduce<D, RED_SMOOTH> : k_filter_reduce<D, RED_PLAIN>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     Timed tm(s, T_FRED);
