@@ -127,7 +127,7 @@ struct Plan {
   int fqs, egs;      // per-step record strides (doubles, even)
   // byte offsets into the workspace
   int64_t o_status, o_fq, o_egl, o_laggf, o_waggf, o_laggs, o_waggs, o_llp, o_fmean, o_fvar, o_t, o_y, o_mask,
-      o_tpos, o_rstep, o_seg, o_llstep, o_adj, o_tauq, o_lpi, o_lmbar, o_gpart, o_gstep, total;
+      o_tpos, o_rstep, o_seg, o_llstep, o_adj, o_tauq, o_lpi, o_lmbar, o_lgj, o_gpart, o_gstep, total;
 };
 
 int warps_for(int d) {
@@ -171,13 +171,14 @@ Plan make_plan(int d, int64_t n, int64_t lanes_req, int warps = 0, bool grad = f
   p.o_rstep = o; o += align256(n * 8);     // batched: noise variance per step
   p.o_seg = o; o += align256(n);           // batched: 1 at each series' first step
   p.o_llstep = o; o += align256(n * 8);    // batched: log-likelihood pieces per step
-  p.o_adj = p.o_tauq = p.o_lpi = p.o_lmbar = p.o_gpart = p.o_gstep = -1;
+  p.o_adj = p.o_tauq = p.o_lpi = p.o_lmbar = p.o_lgj = p.o_gpart = p.o_gstep = -1;
   if (grad) {                                // gradient: forward moments, scan state
     const int adjs = (d + sym + 2 + 1) / 2 * 2;
     p.o_adj = o; o += align256(n * adjs * 8);
     p.o_tauq = o; o += align256(n * 16);       // (tau, q) per step
     p.o_lpi = o; o += align256(P0 * d * d * 8);
     p.o_lmbar = o; o += align256(P0 * d * 8);
+    p.o_lgj = o; o += align256(P0 * (d + sym) * 8);
     p.o_gpart = o; o += align256(3 * P0 * 8);
     p.o_gstep = o; o += align256(3 * n * 8);
   }
@@ -227,6 +228,7 @@ struct ScanArgs {
   double* tauq;              // [n][2] scaled step tau and variance ratio q
   double* lane_pi;           // [D*D][P0] raw chunk product of the mean-adjoint factors
   double* lane_mbar;         // [D][P0] mean adjoint at the chunk end
+  double* lane_gj;           // [D + D(D+1)/2][P0] gamma and N^{-1} J of the mean-adjoint chunk aggregate
   double* gpart;             // [3][P0] gradient partials per lane
   double* g_step;            // batched: [3][n] gradient pieces per step
   double* lagg_a;            // [ns][P0] covariance-adjoint lane aggregates
@@ -987,7 +989,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
           J[j][i] = J[i][j];
         }
       }
-      constexpr int NR = D + 1;
+      constexpr int NR = 2 * D + 1;   // [eta - J m^- | A^T F1^T | J]
       double X[D][NR];
 #pragma unroll
       for (int i = 0; i < D; ++i) {
@@ -995,6 +997,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
 #pragma unroll
         for (int k = 0; k < D; ++k) gi = fma(-J[i][k], smu[k * BLOCK], gi);
         X[i][0] = gi;
+#pragma unroll
+        for (int j = 0; j < D; ++j) X[i][1 + D + j] = J[i][j];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
           double t = (i == j) ? 1.0 : 0.0;   // N = I + J P^-
@@ -1014,17 +1018,23 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
 #pragma unroll
       for (int i = 0; i < D; ++i) {
         sa.g[i] = X[i][0];
+        a.lane_gj[i * a.P0 + g] = X[i][0];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
           sa.E[i][j] = X[i][1 + j];
           a.lane_pi[(i * D + j) * a.P0 + g] = sa.E[i][j];
           sa.L[i][j] = 0.0;
         }
+#pragma unroll
+        for (int j = i; j < D; ++j)    // N^{-1} J (symmetric)
+          a.lane_gj[(D + pidx<D>(i, j)) * a.P0 + g] = 0.5 * (X[i][1 + D + j] + X[j][1 + D + i]);
       }
     } else {
       sagg_identity<D>(sa);
 #pragma unroll
       for (int e = 0; e < D * D; ++e) a.lane_pi[e * a.P0 + g] = (e % (D + 1) == 0) ? 1.0 : 0.0;
+#pragma unroll
+      for (int e = 0; e < D + Sym<D>::N; ++e) a.lane_gj[e * a.P0 + g] = 0.0;
     }
     // level 1 of the mean-adjoint scan: inclusive suffix scan over the warp
 #pragma unroll 1
@@ -1333,18 +1343,14 @@ __global__ void __launch_bounds__(BLOCK, 1) k_smoother_elements(const DevModel<D
 // ---------------------------------------------------------------------------
 template <int D> constexpr int adjoint_smem_doubles() { return Sym<D>::N * BLOCK; }
 
-// mean-adjoint level 3 (backward through the chunk from the exclusive suffix)
-// fused with the covariance-adjoint levels 0/1 (backward Horner of
-// Mb <- E_k Mb E_k^T + B_k from zero, then a warp suffix scan)
+// per lane: the mean adjoint at the chunk end (level 3 of the mean-adjoint
+// scan, from the exclusive suffix) and the covariance-adjoint chunk aggregate
+// (levels 0/1: the closed form below, then a warp suffix scan)
 template <int D>
 __global__ void __launch_bounds__(BLOCK, 1) k_adjoint_mean(const DevModel<D> m, const ScanArgs a) {
-  extern __shared__ double adsm[];
-  double* sL = adsm + threadIdx.x;
   const int64_t g = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int64_t w = g >> 5;
-  const int64_t k0 = g * a.L;
-  const int64_t k1 = min(k0 + a.L, a.n);
   Vec<D> mb;
 #pragma unroll
   for (int i = 0; i < D; ++i) mb[i] = 0.0;
@@ -1364,42 +1370,40 @@ __global__ void __launch_bounds__(BLOCK, 1) k_adjoint_mean(const DevModel<D> m, 
   }
 #pragma unroll
   for (int i = 0; i < D; ++i) a.lane_mbar[i * a.P0 + g] = mb[i];
-#pragma unroll
-  for (int e = 0; e < Sym<D>::N; ++e) sL[e * BLOCK] = 0.0;
-#pragma unroll 1
-  for (int64_t k = k1 - 1; k >= k0; --k) {
-    Mat<D> F1;
-    if (k + 1 < a.n) load_F<D>(a.rec_fq, k + 1, fqs_of<D>(), F1);
-    else set_zero<D>(F1);
-    Vec<D> xb, xm, c0;
+  // The covariance adjoint's chunk term (Mb_{k0} = Pi Mb_{k1} Pi^T + L) in
+  // closed form: L is the derivative by the predicted covariance P^- of step
+  // k0 of the chunk's log-likelihood (the Gaussian integral of Sec. 3's
+  // aggregate: gamma gamma^T / 2 - N^{-1} J / 2) plus that of the predicted
+  // mean of step k1 through the filter gains (Pi mb_{k1} gamma^T,
+  // symmetrised):
+  //   L = (u gamma^T + gamma u^T) / 2 + gamma gamma^T / 2 - N^{-1} J / 2,
+  //   u = Pi mb_{k1},
+  // with gamma, N^{-1} J and Pi from the filter pass.  It equals the backward
+  // recursion L <- A (F^T L F) A^T + B through the chunk from L = 0.
+  SAgg<D> sa;
+  {
+    Vec<D> u, gam;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      double s = 0.0;
+      gam[i] = a.lane_gj[i * a.P0 + g];
+      double t = 0.0;
 #pragma unroll
-      for (int j = 0; j < D; ++j) s = fma(F1[j][i], mb[j], s);
-      xb[i] = s;
+      for (int j = 0; j < D; ++j) {
+        sa.E[i][j] = a.lane_pi[(i * D + j) * a.P0 + g];
+        t = fma(sa.E[i][j], mb[j], t);
+      }
+      u[i] = t;
+      sa.g[i] = 0.0;
     }
-    double v, Si;
-    load_adj_col0<D>(a.rec_adj, k, xm, c0, v, Si);
-    Vec<D> K;
-    double kx = 0.0;
 #pragma unroll
-    for (int i = 0; i < D; ++i) { K[i] = c0[i] * Si; kx = fma(K[i], xb[i], kx); }
-    const double vSi = v * Si;
-    const double c = -0.5 * fma(-vSi, vSi, Si);
-    adj_cov_step<D, BLOCK>(sL, F1, K, vSi, c, xb, kx);
+    for (int i = 0; i < D; ++i)
 #pragma unroll
-    for (int i = 0; i < D; ++i) mb[i] = xb[i];
-    mb[0] += vSi - kx;
-  }
-  SAgg<D> sa;
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    sa.g[i] = 0.0;
-#pragma unroll
-    for (int j = 0; j < D; ++j) sa.E[i][j] = a.lane_pi[(i * D + j) * a.P0 + g];
-#pragma unroll
-    for (int j = i; j < D; ++j) { sa.L[i][j] = sL[pidx<D>(i, j) * BLOCK]; sa.L[j][i] = sa.L[i][j]; }
+      for (int j = i; j < D; ++j) {
+        const double l = 0.5 * (fma(u[i], gam[j], u[j] * gam[i]) + gam[i] * gam[j] -
+                                a.lane_gj[(D + pidx<D>(i, j)) * a.P0 + g]);
+        sa.L[i][j] = l;
+        sa.L[j][i] = l;
+      }
   }
 #pragma unroll 1
   for (int off = 1; off < 32; off <<= 1) {
@@ -1698,6 +1702,7 @@ ScanArgs base_args(const Plan& p, void* ws) {
     a.tauq = reinterpret_cast<double*>(ws_ptr(ws, p.o_tauq));
     a.lane_pi = reinterpret_cast<double*>(ws_ptr(ws, p.o_lpi));
     a.lane_mbar = reinterpret_cast<double*>(ws_ptr(ws, p.o_lmbar));
+    a.lane_gj = reinterpret_cast<double*>(ws_ptr(ws, p.o_lgj));
     a.gpart = reinterpret_cast<double*>(ws_ptr(ws, p.o_gpart));
     a.lagg_a = a.lagg_f;     // the filter aggregates are dead once the filter pass is done
     a.wagg_a = a.wagg_f;
@@ -1823,9 +1828,8 @@ void run_grad(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s, 
   }
   constexpr int asmem = adjoint_smem_doubles<D>() * 8;
   {
-    cudaFuncSetAttribute(k_adjoint_mean<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, asmem);
     Timed tm(s, T_AMEAN);
-    k_adjoint_mean<D><<<grid, BLOCK, asmem, s>>>(m, a);
+    k_adjoint_mean<D><<<grid, BLOCK, 0, s>>>(m, a);
     after_launch();
   }
   {
