@@ -81,70 +81,6 @@ __device__ __forceinline__ void load_F(const double* rec, int64_t k, int fqs, Ma
 }
 
 // ---------------------------------------------------------------------------
-// Forward fold of the mean-adjoint chunk aggregate (E, g) over a chunk
-// [k0, k1): E = E_{k0} ... E_{k1-1}, g = sum_k E_{k0} ... E_{k-1} g_k, kept as
-// Pi (row-major D x D at sPi[e * ST]) and gamma (sg[i * ST]).  Step k first
-// completes the previous factor (Pi <- Pi F_k^T), then adds Pi g_k and applies
-// A_k (Pi <- Pi - Pi[:,0] K^T); row i of Pi needs only row i.
-// ---------------------------------------------------------------------------
-template <int D, int ST>
-__device__ __forceinline__ void adj_fold_start(double* sPi, double* sg) {
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    sg[i * ST] = 0.0;
-#pragma unroll
-    for (int j = 0; j < D; ++j) sPi[(i * D + j) * ST] = (i == j) ? 1.0 : 0.0;
-  }
-}
-
-// with_F: apply F^T first (every step but the chunk's first)
-template <int D, int ST>
-__device__ __forceinline__ void adj_fold_step(double* sPi, double* sg, const Mat<D>& F, bool with_F,
-                                              const Vec<D>& K, double vSi) {
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    double r[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) r[j] = sPi[(i * D + j) * ST];
-    if (with_F) {
-      double s[D];
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        double a = r[0] * F[j][0];
-#pragma unroll
-        for (int l = 1; l < D; ++l) a = fma(r[l], F[j][l], a);
-        s[j] = a;
-      }
-#pragma unroll
-      for (int j = 0; j < D; ++j) r[j] = s[j];
-    }
-    const double c = r[0];
-    sg[i * ST] = fma(c, vSi, sg[i * ST]);
-#pragma unroll
-    for (int j = 0; j < D; ++j) sPi[(i * D + j) * ST] = fma(-c, K[j], r[j]);
-  }
-}
-
-// chunk end: the last factor's F^T (the transition into the next chunk's
-// first step; F = 0 at the end of the data or of a series)
-template <int D, int ST>
-__device__ __forceinline__ void adj_fold_finish(double* sPi, const Mat<D>& F) {
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    double r[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) r[j] = sPi[(i * D + j) * ST];
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      double a = r[0] * F[j][0];
-#pragma unroll
-      for (int l = 1; l < D; ++l) a = fma(r[l], F[j][l], a);
-      sPi[(i * D + j) * ST] = a;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // One backward step of the covariance adjoint, in place on a symmetric
 // matrix in shared memory (packed upper, sL[e * ST]):
 //   L <- A (F^T L F) A^T + B,  A = I - e0 K^T,

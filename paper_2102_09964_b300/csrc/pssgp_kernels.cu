@@ -825,11 +825,12 @@ __global__ void __launch_bounds__(BLOCK) k_filter_llfinish(const DevModel<D> m, 
 }
 
 // filter level 3 (+ smoother levels 0/1 when fused)
-// shared memory of k_filter_propagate: the fixed-point state Sig, V (packed),
-// mu per thread, entry-major with stride BLOCK
-// The fused mode uses them for the start state (x0 in mu, P0 in V) and F of
-// the lane's last step (in Sig), plus the filter covariance P_k (packed) and
-// the prediction (x^-, P^-) of the last step.
+// shared memory of k_filter_propagate, per thread, entry-major with stride
+// BLOCK: a d x d matrix (Sig), a packed symmetric one (V) and a vector (mu).
+// The adjoint mode keeps the prediction of the chunk's first step in (mu, V);
+// the fused mode keeps the start state (x0 in mu, P0 in V) and F of the
+// lane's last step (in Sig), plus the filter covariance P_k (packed) and the
+// prediction (x^-, P^-) of the last step.
 template <int D, int MODE> constexpr int propagate_smem_doubles() {
   return (D * D + Sym<D>::N + D + (MODE == 1 ? 2 * Sym<D>::N + D : 0)) * BLOCK;
 }

@@ -698,20 +698,15 @@ __device__ __forceinline__ bool smoother_element(const Vec<D>& x, const Mat<D>& 
   return ok;
 }
 
-// Chunk aggregate of the smoothing operator by forward recursion.
-// The product of the smoothing elements of steps s..e-1 is the conditional
-// p(x_s | x_e, y_{1:e-1}) = N(E x_e + g, L) (each element is
+// Chunk aggregate of the smoothing operator from the joint of its first and
+// last states.  The product of the smoothing elements of steps s..e-1 is the
+// conditional p(x_s | x_e, y_{1:e-1}) = N(E x_e + g, L) (each element is
 // p(x_k | x_{k+1}, y_{1:k}), supplement Prop. 2, and the chain is Markov).
-// It follows from the joint of (x_s, x_k) given y_{1:k}, carried forward with
-// the Kalman filter as in fixed-point smoothing:
-//   mu = E[x_s | y_1:k], V = Cov(x_s | y_1:k), Sig = Cov(x_s, x_k | y_1:k),
-//   predict  Sig <- Sig F^T;
-//   update   c = Sig[:,0] (Cov(x_s, y)), mu += c v / S, V -= c c^T / S,
-//            Sig -= c K^T   (K = P^-[:,0] / S, the filter gain);
-// and at the chunk end, with the prediction (x^-, P^-) of step e,
+// Given mu = E[x_s | y_{1:e-1}], V = Cov(x_s | y_{1:e-1}) and
+// Sig = Cov(x_s, x_{e-1} | y_{1:e-1}) (k_filter_propagate forms them in closed
+// form from the filter aggregate of steps s+1..e-1), the prediction
+// (x^-, P^-) of step e closes it:
 //   E = Sig F_e^T (P^-)^{-1}, g = mu - E x^-, L = V - E (Sig F_e^T)^T.
-// Cost per step: one d x d product and rank-one updates, instead of the two
-// products of an explicit fold of the operator.
 template <int D>
 struct FixedPoint {
   Vec<D> mu;
@@ -719,49 +714,8 @@ struct FixedPoint {
   Mat<D> Sig;
 };
 
-template <int D>
-__device__ __forceinline__ void fixed_point_start(FixedPoint<D>& f, const Vec<D>& x, const Mat<D>& P) {
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    f.mu[i] = x[i];
-#pragma unroll
-    for (int j = 0; j < D; ++j) { f.V[i][j] = P[i][j]; f.Sig[i][j] = P[i][j]; }
-  }
-}
-
-// Sig <- Sig F^T ; then, if observed, the rank-one update with gain K = Pm[:,0]/S
-template <int D>
-__device__ __forceinline__ void fixed_point_step(FixedPoint<D>& f, const Mat<D>& F, bool observed, const Mat<D>& Pm,
-                                                 double Si, double v) {
-  Mat<D> Sm;
-#pragma unroll
-  for (int i = 0; i < D; ++i)
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      double s = f.Sig[i][0] * F[j][0];
-#pragma unroll
-      for (int k = 1; k < D; ++k) s = fma(f.Sig[i][k], F[j][k], s);
-      Sm[i][j] = s;
-    }
-  if (observed) {
-    Vec<D> c, cs, K;
-#pragma unroll
-    for (int i = 0; i < D; ++i) { c[i] = Sm[i][0]; cs[i] = c[i] * Si; K[i] = Pm[i][0] * Si; }
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      f.mu[i] = fma(cs[i], v, f.mu[i]);
-#pragma unroll
-      for (int j = i; j < D; ++j) { f.V[i][j] = fma(-cs[i], c[j], f.V[i][j]); f.V[j][i] = f.V[i][j]; }
-#pragma unroll
-      for (int j = 0; j < D; ++j) f.Sig[i][j] = fma(-c[i], K[j], Sm[i][j]);
-    }
-  } else {
-    copy<D>(Sm, f.Sig);
-  }
-}
-
-// chunk end: aggregate (E, g, L) from the fixed-point state and the
-// prediction (xm, Pm) of the step after the chunk, Pm = Lc Lc^T given.
+// chunk end: aggregate (E, g, L) from (mu, V, Sig) and the prediction
+// (xm, Pm) of the step after the chunk, Pm = Lc Lc^T given.
 template <int D>
 __device__ __forceinline__ void fixed_point_finish(const FixedPoint<D>& f, const Mat<D>& F, const Vec<D>& xm,
                                                    const Mat<D>& Lc, const double (&invd)[D], SAgg<D>& a) {
@@ -811,73 +765,6 @@ __device__ __forceinline__ void fixed_point_finish(const FixedPoint<D>& f, const
       a.L[i][j] = s;
       a.L[j][i] = s;
     }
-}
-
-// The same recursion with its state in shared memory (element e of a
-// thread's Sig / V(packed) / mu at ptr[e * SST]); each row of Sig is updated
-// in place (row i of Sig F^T needs only row i of Sig), so only a row and the
-// vector c = Sig[:,0] are held in registers.
-template <int D, int SST>
-__device__ __forceinline__ void fixed_point_start_smem(double* Sig, double* V, double* mu, const Vec<D>& x,
-                                                       const Mat<D>& P) {
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    mu[i * SST] = x[i];
-#pragma unroll
-    for (int j = 0; j < D; ++j) Sig[(i * D + j) * SST] = P[i][j];
-#pragma unroll
-    for (int j = i; j < D; ++j) V[pidx<D>(i, j) * SST] = P[i][j];
-  }
-}
-
-template <int D, int SST>
-__device__ __forceinline__ void fixed_point_step_smem(double* Sig, double* V, double* mu, const Mat<D>& F,
-                                                      bool observed, const Mat<D>& Pm, double Si, double v) {
-  Vec<D> c;
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    double row[D], sm[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) row[k] = Sig[(i * D + k) * SST];
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      double s = row[0] * F[j][0];
-#pragma unroll
-      for (int k = 1; k < D; ++k) s = fma(row[k], F[j][k], s);
-      sm[j] = s;
-    }
-    c[i] = sm[0];
-    if (observed) {
-      const double ci = sm[0];
-#pragma unroll
-      for (int j = 0; j < D; ++j) Sig[(i * D + j) * SST] = fma(-ci, Pm[j][0] * Si, sm[j]);
-    } else {
-#pragma unroll
-      for (int j = 0; j < D; ++j) Sig[(i * D + j) * SST] = sm[j];
-    }
-  }
-  if (observed) {
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      const double cs = c[i] * Si;
-      mu[i * SST] = fma(cs, v, mu[i * SST]);
-#pragma unroll
-      for (int j = i; j < D; ++j) V[pidx<D>(i, j) * SST] = fma(-cs, c[j], V[pidx<D>(i, j) * SST]);
-    }
-  }
-}
-
-template <int D, int SST>
-__device__ __forceinline__ void fixed_point_load(const double* Sig, const double* V, const double* mu,
-                                                 FixedPoint<D>& f) {
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    f.mu[i] = mu[i * SST];
-#pragma unroll
-    for (int j = 0; j < D; ++j) f.Sig[i][j] = Sig[(i * D + j) * SST];
-#pragma unroll
-    for (int j = i; j < D; ++j) { f.V[i][j] = V[pidx<D>(i, j) * SST]; f.V[j][i] = f.V[i][j]; }
-  }
 }
 
 // ---------------------------------------------------------------------------
