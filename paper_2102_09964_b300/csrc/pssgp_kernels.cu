@@ -415,12 +415,29 @@ __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_rec(const DevModel<D>
 // writes the F/Q record, the step's noise variance and whether it starts a
 // series.  params[3s..3s+2] = lengthscale, variance, noise variance.  The
 // grid covers max(n, B + 1) threads so that every offset is checked.
+// per-series scales of the unit model, once per series: uscale = l0 / l and
+// qscale = s2 / s2_0 and the noise variance, stored at the series' first step
+// (a non-empty series' first step is unique and < n); checks the parameters
+__global__ void __launch_bounds__(128) k_series_scales(double ell0, double var0, const int64_t* offsets, int B,
+                                                      const double* params, int64_t n, double* su, double* sq,
+                                                      double* sr, int* status) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  const int64_t a = offsets[s], b = offsets[s + 1];
+  if (!(b > a) || a < 0 || a >= n) return;      // empty (or invalid: flagged by k_discretize_batched)
+  const double ell = params[3 * s], s2 = params[3 * s + 1], R = params[3 * s + 2];
+  if (bad_pos(ell) || bad_pos(s2) || bad_pos(R)) flag(status, PSSGP_EBATCH);
+  su[a] = ell0 / ell;
+  sq[a] = s2 / var0;
+  sr[a] = R;
+}
+
 template <int D>
-__global__ void __launch_bounds__(DISC_BLOCK) k_discretize_batched(const DevModel<D> m, double ell0, double var0,
-                                                                 const int64_t* offsets, int B, const double* params,
-                                                                 const double* t, int64_t n, double* rec,
-                                                                 double* Rstep, uint8_t* seg, double* tauq,
-                                                                 int* status) {
+__global__ void __launch_bounds__(DISC_BLOCK) k_discretize_batched(const DevModel<D> m, const int64_t* offsets,
+                                                                 int B, const double* su, const double* sq,
+                                                                 const double* sr, const double* t, int64_t n,
+                                                                 double* rec, double* Rstep, uint8_t* seg,
+                                                                 double* tauq, int* status) {
   constexpr int FQS = fqs_of<D>();
   extern __shared__ double stage[];
   const int64_t k0 = (int64_t)blockIdx.x * DISC_BLOCK;
@@ -441,12 +458,12 @@ __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_batched(const DevMode
       if (offsets[mid] <= k) lo = mid; else hi = mid;
     }
     sid = lo;
-    first = (k == 0) || (k == offsets[sid]);
-    const double ell = params[3 * sid], s2 = params[3 * sid + 1];
-    R = params[3 * sid + 2];
-    if (bad_pos(ell) || bad_pos(s2) || bad_pos(R)) bits |= PSSGP_EBATCH;
-    uscale = ell0 / ell;
-    qscale = s2 / var0;
+    const int64_t a0 = offsets[sid];
+    first = (k == 0) || (k == a0);
+    const int64_t ia = min(max(a0, (int64_t)0), n - 1);   // in range even for invalid offsets (flagged)
+    uscale = su[ia];
+    qscale = sq[ia];
+    R = sr[ia];
     const double t1 = t[k];
     if (nonfinite(t1)) bits |= PSSGP_ENAN;
     if (!first) {
@@ -1747,6 +1764,9 @@ struct BatchArgs {
   const double* params;     // [B][3]
   double* Rstep;
   uint8_t* seg;
+  double* su;               // [n] each: (uscale, qscale, R) of every series at its first step
+  double* sq;
+  double* sr;
 };
 
 // ll_only: the log-likelihood alone (reduce with the zero-start terms, level
@@ -1755,6 +1775,13 @@ template <int D>
 void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s, const BatchArgs* bt = nullptr,
                 bool ll_only = false) {
   const int grid = (int)(p.P0 / BLOCK);
+  if (bt) {
+    Timed tm(s, T_DISC);
+    k_series_scales<<<(unsigned)((bt->B + 127) / 128), 128, 0, s>>>(bt->ell0, bt->var0, bt->offsets, bt->B,
+                                                                     bt->params, p.n, bt->su, bt->sq, bt->sr,
+                                                                     a.status);
+    after_launch();
+  }
   {
     Timed tm(s, T_DISC);
     constexpr int dsmem = DISC_BLOCK * fqs_of<D>() * 8;
@@ -1767,7 +1794,7 @@ void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s
       cudaFuncSetAttribute(k_discretize_batched<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem);
       const int64_t thr = std::max<int64_t>(p.n, (int64_t)bt->B + 1);
       k_discretize_batched<D><<<(unsigned)((thr + DISC_BLOCK - 1) / DISC_BLOCK), DISC_BLOCK, dsmem, s>>>(
-          m, bt->ell0, bt->var0, bt->offsets, bt->B, bt->params, a.t, p.n, a.rec_fq, bt->Rstep, bt->seg, a.tauq,
+          m, bt->offsets, bt->B, bt->su, bt->sq, bt->sr, a.t, p.n, a.rec_fq, bt->Rstep, bt->seg, a.tauq,
           a.status);
     }
     after_launch();
@@ -1991,6 +2018,11 @@ extern "C" int pssgp_loglik_batched(const pssgp_model* model, const int64_t* off
   bt.ell0 = ell0; bt.var0 = var0; bt.offsets = offsets; bt.B = B; bt.params = params;
   bt.Rstep = reinterpret_cast<double*>(ws_ptr(ws, p.o_rstep));
   bt.seg = reinterpret_cast<uint8_t*>(ws_ptr(ws, p.o_seg));
+  // the smoother outputs and prediction positions are unused by the batched
+  // paths: 3n doubles for the per-series table (indexed by a series' first step)
+  bt.su = reinterpret_cast<double*>(ws_ptr(ws, p.o_fmean));
+  bt.sq = reinterpret_cast<double*>(ws_ptr(ws, p.o_fvar));
+  bt.sr = reinterpret_cast<double*>(ws_ptr(ws, p.o_tpos));
   a.t = t; a.y = y; a.mask = mask; a.R = bt.Rstep; a.R_per_step = 1;
   a.fuse_smoother = 0;
   a.seg_start = bt.seg;
@@ -2061,6 +2093,11 @@ extern "C" int pssgp_loglik_grad_batched(const pssgp_model* model, const int64_t
   bt.ell0 = ell0; bt.var0 = var0; bt.offsets = offsets; bt.B = B; bt.params = params;
   bt.Rstep = reinterpret_cast<double*>(ws_ptr(ws, p.o_rstep));
   bt.seg = reinterpret_cast<uint8_t*>(ws_ptr(ws, p.o_seg));
+  // the smoother outputs and prediction positions are unused by the batched
+  // paths: 3n doubles for the per-series table (indexed by a series' first step)
+  bt.su = reinterpret_cast<double*>(ws_ptr(ws, p.o_fmean));
+  bt.sq = reinterpret_cast<double*>(ws_ptr(ws, p.o_fvar));
+  bt.sr = reinterpret_cast<double*>(ws_ptr(ws, p.o_tpos));
   a.t = t; a.y = y; a.mask = mask; a.R = bt.Rstep; a.R_per_step = 1;
   a.seg_start = bt.seg;
   a.ll_step = reinterpret_cast<double*>(ws_ptr(ws, p.o_llstep));
