@@ -331,6 +331,9 @@ def batched_bench(args, P, wl, dev, barrier, world, rank):
         call(d)
     torch.cuda.synchronize()
     assert all(P.status(d["ws"]) == 0 for d in parts), "device status error (batched)"
+    # one family after the other in one graph: as two parallel branches (fork
+    # onto a second stream and join) an evaluation took 24.6 ms against 24.0,
+    # the lane counts being tuned for the whole GPU
     g = P.Graph()
     with g:
         for d in parts:
@@ -546,9 +549,9 @@ def run_ours(args, wl_params):
             dist.barrier()
 
     # --- device-timed region (inputs resident in HBM) ---
-    sampler = ClockSampler(dev.index)
-    sampler.start()
-    time.sleep(0.3)
+    # one stream first (reported as ms_per_step_one_stream), then the timed
+    # value: steps alternate between two streams with a workspace each, so
+    # one step's low-occupancy scan rounds overlap the next step's kernels
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -557,12 +560,42 @@ def run_ours(args, wl_params):
         step()
     e1.record(stream)
     e1.synchronize()
+    ms_one = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+
+    dstreams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    wsbs = [wsb, P.workspace(m.d, n, dev)]
+    outs = [out, tuple(torch.empty_like(o) for o in out)]
+
+    def dstep(i):
+        j = i % 2
+        with torch.cuda.stream(dstreams[j]):
+            P.predict(m, tt, yy, ts, R, ws=wsbs[j], out=outs[j])
+
+    for i in range(max(args.warmup, 3) + 1):
+        dstep(i)
+    torch.cuda.synchronize()
+    assert P.status(wsbs[1]) == 0, "device status error"
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for st in dstreams:
+        st.wait_stream(stream)
+    for i in range(args.steps):
+        dstep(i)
+    for st in dstreams:
+        stream.wait_stream(st)
+    e1.record(stream)
+    e1.synchronize()
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms, world, dev)
     value = job_throughput(n, world, ms)
+    del wsbs[1]
 
     # --- end to end through the C ABI from pinned host buffers ---
     # pssgp_predict_host: every step copies its inputs host -> device and its
@@ -642,7 +675,8 @@ def run_ours(args, wl_params):
     whole = sum(alg.values()) / (ms * 1e-3) / 1e12
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_one_stream": round(ms_one, 4),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args.workload, d, n),
             "e2e": e2e, "gpu_launches": int(gpu_launches), "clocks": clocks, "roofline": roofline,
