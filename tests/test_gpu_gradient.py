@@ -113,6 +113,29 @@ def test_batched_grad_matches_forward_mode(kind):
         check_grad(g[s], rg, b - a, TOL[kind], (kind, s))
 
 
+@pytest.mark.parametrize("kind", ["matern32", "matern52"])
+def test_batched_grad_short_series_at_and_inside_chunk_starts(kind):
+    """6,000 series of 1 to 3 steps with a quarter of the steps missing: at
+    the default tuning every chunk holds a few steps, so series start at
+    chunk starts and inside chunks, where the adjoint chunk aggregates reset
+    (A = 0 after a series start)."""
+    rng = np.random.default_rng(39)
+    bt = wl.series_batch(seed=40, lengths=rng.integers(1, 4, size=6000), kinds=(kind,))
+    m = P.build_model(kind, 1.0, 1.0)
+    mask = (rng.uniform(size=bt.t.size) >= 0.25).astype(np.uint8)
+    ll, g, ws = P.loglik_grad_batched(m, dev(bt.offsets, torch.int64), dev(bt.params()), dev(bt.t), dev(bt.y),
+                                      dev(mask, torch.uint8))
+    assert P.status(ws) == 0
+    ll, g = ll.cpu().numpy(), g.cpu().numpy()
+    for s in rng.choice(bt.B, 400, replace=False):
+        a, b = bt.offsets[s], bt.offsets[s + 1]
+        nobs = max(int(mask[a:b].sum()), 1)
+        rll, rg = oracle.loglik_grad_fwd(kind, bt.lengthscale[s], bt.variance[s], bt.t[a:b], bt.y[a:b],
+                                         mask[a:b], bt.noise[s])
+        assert abs(ll[s] - rll) <= TOL[kind] * max(abs(rll), nobs)
+        check_grad(g[s], rg, nobs, TOL[kind], (kind, s))
+
+
 def test_batched_grad_full_size_sampled():
     """The 4,096-series workload, one call per family; sampled series against
     the oracle's forward-mode gradient."""
