@@ -263,7 +263,7 @@ int pssgp_loglik_grad_batched(const pssgp_model* model, const int64_t* offsets,
  *  - Scratch: a fixed 32 MiB array inside the library's device image, held on
  *    every GPU that loads the library until the process exits.  That bounds
  *    the problem size: n up to about 28,000 merged steps at d = 6 and about
- *    160,000 at d = 2 (exactly: the workspace of the current scan tuning,
+ *    147,000 at d = 2 (exactly: the workspace of the current scan tuning,
  *    at most pssgp_workspace_size(d, n), must fit in 32 MiB).  Larger
  *    problems are rejected with PSSGP_ESCRATCH before anything is launched.
  *  - The first call on a device looks up the scratch's device address
