@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--timing-steps", type=int, default=3)
     ap.add_argument("--warps-per-sm", type=int, default=0, help="scan lanes per SM / 32 (0 = library default)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 4,096-series batched measurement")
+    ap.add_argument("--streams", type=int, default=4,
+                    help="streams (each with its own workspace) that the timed steps alternate over "
+                         "(measured at 2^20 RBF-6: 2 -> 196, 3 -> 204, 4 -> 206, 6 -> 206 M steps/s)")
     ap.add_argument("--no-fit", action="store_true", help="skip the learned-vs-plain fit and Table-1 measurements")
     ap.add_argument("--no-gradient", action="store_true", help="skip the log-likelihood gradient measurement")
     ap.add_argument("--fit-adam", action="store_true", help="also time the Adam fits (about a minute)")
@@ -550,7 +553,7 @@ def run_ours(args, wl_params):
 
     # --- device-timed region (inputs resident in HBM) ---
     # one stream first (reported as ms_per_step_one_stream), then the timed
-    # value: steps alternate between two streams with a workspace each, so
+    # value: steps alternate between --streams streams (4) with a workspace each, so
     # one step's low-occupancy scan rounds overlap the next step's kernels
     barrier()
     torch.cuda.synchronize()
@@ -562,19 +565,20 @@ def run_ours(args, wl_params):
     e1.synchronize()
     ms_one = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
 
-    dstreams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    wsbs = [wsb, P.workspace(m.d, n, dev)]
-    outs = [out, tuple(torch.empty_like(o) for o in out)]
+    ns = max(1, args.streams)
+    dstreams = [torch.cuda.Stream() for _ in range(ns)]
+    wsbs = [wsb] + [P.workspace(m.d, n, dev) for _ in range(ns - 1)]
+    outs = [out] + [tuple(torch.empty_like(o) for o in out) for _ in range(ns - 1)]
 
     def dstep(i):
-        j = i % 2
+        j = i % ns
         with torch.cuda.stream(dstreams[j]):
             P.predict(m, tt, yy, ts, R, ws=wsbs[j], out=outs[j])
 
-    for i in range(max(args.warmup, 3) + 1):
+    for i in range(max(args.warmup, 3) + ns - 1):
         dstep(i)
     torch.cuda.synchronize()
-    assert P.status(wsbs[1]) == 0, "device status error"
+    assert all(P.status(w) == 0 for w in wsbs), "device status error"
     sampler = ClockSampler(dev.index)
     sampler.start()
     time.sleep(0.3)
@@ -595,25 +599,25 @@ def run_ours(args, wl_params):
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms, world, dev)
     value = job_throughput(n, world, ms)
-    del wsbs[1]
+    del wsbs[1:]
 
     # --- end to end through the C ABI from pinned host buffers ---
     # pssgp_predict_host: every step copies its inputs host -> device and its
-    # results device -> host inside the call; two streams with two workspaces
+    # results device -> host inside the call; --streams streams with a workspace each
     # let one step's copies overlap the other's kernels
     h_tt = torch.as_tensor(s.t_train, dtype=torch.float64).pin_memory()
     h_yy = torch.as_tensor(s.y_train, dtype=torch.float64).pin_memory()
     h_ts = torch.as_tensor(s.t_test, dtype=torch.float64).pin_memory()
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    streams = [torch.cuda.Stream() for _ in range(ns)]
     houts = [(torch.empty(M, dtype=torch.float64).pin_memory(), torch.empty(M, dtype=torch.float64).pin_memory(),
               torch.empty(1, dtype=torch.float64).pin_memory()) for _ in streams]
-    hws = [None, None]
+    hws = [None] * ns
 
     def e2e_step(i):
-        j = i % 2
+        j = i % ns
         hws[j] = P.predict_host(m, h_tt, h_yy, h_ts, R, houts[j], ws=hws[j], stream=streams[j])
 
-    for i in range(4):
+    for i in range(2 * ns):
         e2e_step(i)
     torch.cuda.synchronize()
     barrier()
