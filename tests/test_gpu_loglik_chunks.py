@@ -135,3 +135,26 @@ def test_batched_long_series_equal_single_calls():
         assert P.status(w1) == 0
         one = float(one.cpu()[0])
         assert abs(ll[s] - one) <= 1e-10 * max(abs(one), b - a)
+
+
+@pytest.mark.parametrize("kind", ["matern32", "matern52", "rbf"])
+@pytest.mark.parametrize("R", [1e-6, 1e-9])
+def test_tiny_noise_prediction_and_loglik(kind, R):
+    """Nearly noise-free data: J grows like 1/R in the chunk aggregates, and
+    the closed forms solve with I + P J.  Prediction (closed-form smoother
+    chunk aggregates) and both log-likelihood paths against the oracle at the
+    usual tolerances (measured errors up to about 5e-11 at R = 1e-9)."""
+    s = wl.prefix(wl.sinusoid_large(N=1 << 16, M=1000), 8_000)
+    m = P.build_model(kind, 1.0, 1.0)
+    mean, var, ll, ws = P.predict(m, dev(s.t_train), dev(s.y_train), dev(s.t_test), R)
+    assert P.status(ws) == 0
+    fm, fv, res, _ = oracle.predict(om.make_model(kind, 1.0, 1.0), s.t_train, s.y_train, s.t_test, R)
+    mean, var, ll = mean.cpu().numpy(), var.cpu().numpy(), float(ll.cpu()[0])
+    tol = TOL[kind]
+    assert np.max(np.abs(mean - fm) / np.maximum(np.abs(fm), np.sqrt(fv))) <= tol
+    assert np.max(np.abs(var - fv) / fv) <= tol
+    assert abs(ll - res.loglik) <= tol * max(abs(res.loglik), s.N)
+    t, y, mask, _ = oracle.merge(s.t_train, s.y_train, s.t_test)
+    l2, w2 = P.loglik(m, dev(t), dev(y), dev(mask, torch.uint8), R)
+    assert P.status(w2) == 0
+    assert abs(float(l2.cpu()[0]) - res.loglik) <= tol * max(abs(res.loglik), s.N)
