@@ -136,6 +136,20 @@ def test_batched_grad_short_series_at_and_inside_chunk_starts(kind):
         check_grad(g[s], rg, nobs, TOL[kind], (kind, s))
 
 
+@pytest.mark.parametrize("kind", ["matern32", "matern52", "rbf"])
+@pytest.mark.parametrize("R", [1e-6, 1e-9])
+def test_grad_tiny_noise(kind, R):
+    """Nearly noise-free data: J grows like 1/R in the chunk aggregates from
+    which the adjoint chunk aggregates are formed (N = I + J P^-)."""
+    s = wl.prefix(wl.sinusoid_large(N=1 << 16, M=0), 3_000)
+    mask = np.ones(s.N, np.uint8)
+    ll, g, st = gpu_grad(kind, 1.0, 1.0, s.t_train, s.y_train, mask, R)
+    assert st == 0
+    rll, rg = oracle.loglik_grad_fwd(kind, 1.0, 1.0, s.t_train, s.y_train, mask, R)
+    assert abs(ll - rll) <= TOL[kind] * max(abs(rll), s.N)
+    check_grad(g, rg, s.N, TOL[kind], (kind, R))
+
+
 def test_batched_grad_full_size_sampled():
     """The 4,096-series workload, one call per family; sampled series against
     the oracle's forward-mode gradient."""
