@@ -35,8 +35,8 @@ sys.path.insert(0, ROOT)
 METRIC = "filter+smoother time steps/s at N=2^20,d=6 FP64"
 # DRAM bytes per merged step of each kernel, from a one-pass ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels at the
-# 2^20 workload itself (profiles/dram_traffic_rbf6_2p20.md); a launch's traffic
-# is this x n.  Reset an entry to None whenever its kernel changes.
+# 2^20 workload itself; a launch's traffic is this x n.  Reset an entry to None
+# whenever its kernel changes.
 PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1088.4, "filter_reduce": 767.3, "discretize": 477.9,
                                 "smoother_propagate": 524.0}
 UNIT = "steps/s"
