@@ -152,7 +152,7 @@ Plan make_plan(int d, int64_t n, int64_t lanes_req, int warps = 0, bool grad = f
   p.nf = d * d + 2 * d + 2 * sym;
   p.ns = d * d + d + sym;
   p.fqs = (int)round_up(d * d + sym, 2);
-  p.egs = (int)round_up(d * d + d + sym, 2);
+  p.egs = (int)round_up(d * d + d + 2 * sym, 2);
   int64_t o = 0;
   p.o_status = o; o += 256;
   p.o_fq = o; o += align256(n * p.fqs * 8);
@@ -241,7 +241,9 @@ __device__ __forceinline__ void flag(int* status, int bits) {
 }
 
 template <int D> __host__ __device__ constexpr int fqs_of() { return (D * D + Sym<D>::N + 1) / 2 * 2; }
-template <int D> __host__ __device__ constexpr int egs_of() { return (D * D + D + Sym<D>::N + 1) / 2 * 2; }
+// per-step RTS record: E (d*d), g (d), the filtered covariance P_k and the
+// predicted covariance P^-_{k+1} (both packed)
+template <int D> __host__ __device__ constexpr int egs_of() { return (D * D + D + 2 * Sym<D>::N + 1) / 2 * 2; }
 
 template <int D>
 __device__ __forceinline__ void load_fq(const double* rec, int64_t k, Mat<D>& F, Mat<D>& Q) {
@@ -267,8 +269,10 @@ __device__ __forceinline__ void store_fq(double* rec, int64_t k, const Mat<D>& F
 #pragma unroll
     for (int j = i; j < D; ++j) p[D * D + pidx<D>(i, j)] = Q[i][j];
 }
+// the RTS record of step k: (E, g) of element e, P_k and P^-_{k+1}
 template <int D>
-__device__ __forceinline__ void store_egl(double* rec, int64_t k, const SAgg<D>& e) {
+__device__ __forceinline__ void store_rts(double* rec, int64_t k, const SAgg<D>& e, const Mat<D>& P,
+                                          const Mat<D>& Pm) {
   double* p = rec + k * egs_of<D>();
 #pragma unroll
   for (int i = 0; i < D; ++i)
@@ -279,7 +283,10 @@ __device__ __forceinline__ void store_egl(double* rec, int64_t k, const SAgg<D>&
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
-    for (int j = i; j < D; ++j) p[D * D + D + pidx<D>(i, j)] = e.L[i][j];
+    for (int j = i; j < D; ++j) {
+      p[D * D + D + pidx<D>(i, j)] = P[i][j];
+      p[D * D + D + Sym<D>::N + pidx<D>(i, j)] = Pm[i][j];
+    }
 }
 // a symmetric matrix, packed upper, in shared memory (entry e at p[e * SST])
 template <int D, int SST>
@@ -297,11 +304,13 @@ __device__ __forceinline__ void load_sym_smem(const double* p, Mat<D>& M) {
     for (int j = i; j < D; ++j) { M[i][j] = p[pidx<D>(i, j) * SST]; M[j][i] = M[i][j]; }
 }
 
-// smoother_element() written to the record of step k as it is formed:
-// W = Lu^{-1} T in place of T, L = P - W^T V with V = diag(rd) W (V replaces
-// W row by row), then E row by row with g (row j of E = Lu^{-T} applied to column j of V), so that at
-// most one row of E is held.  P_k (packed) is read from shared memory (entry
-// e at sP[e * SST]), so that its registers are free once T = F P_k is formed.
+// The RTS record of step k written as it is formed: E and g of
+// smoother_element() (W = Lu^{-1} T in place of T, V = diag(rd) W row by row,
+// then E row by row with g: row j of E = Lu^{-T} applied to column j of V, so
+// that at most one row of E is held), P_k (packed, read from shared memory at
+// sP[e * SST]) and P^- (the prediction of step k+1).  The smoother pass uses
+// P^s_k = P_k + E (P^s_{k+1} - P^-) E^T, identical to E P^s_{k+1} E^T + L with
+// L = P_k - E P^- E^T, so L is not formed.
 template <int D, int SST>
 __device__ __forceinline__ bool smoother_element_store(double* rec, int64_t k, const Vec<D>& x, const double* sP,
                                                        Mat<D>& T, const Vec<D>& xm, const Mat<D>& Pm) {
@@ -318,24 +327,18 @@ __device__ __forceinline__ bool smoother_element_store(double* rec, int64_t k, c
       for (int q = 0; q < i; ++q) s = fma(-Lu[i][q], T[q][j], s);
       T[i][j] = s;
     }
-  // L = P - sum_q W_q^T V_q over the rows q; row q of T becomes V_q once used
-  double Ls[Sym<D>::N];
 #pragma unroll
-  for (int e = 0; e < Sym<D>::N; ++e) Ls[e] = sP[e * SST];
+  for (int q = 0; q < D; ++q)
 #pragma unroll
-  for (int q = 0; q < D; ++q) {
-    double vq[D];
+    for (int j = 0; j < D; ++j) T[q][j] *= rd[q];
 #pragma unroll
-    for (int j = 0; j < D; ++j) vq[j] = T[q][j] * rd[q];
-#pragma unroll
-    for (int i = 0; i < D; ++i)
-#pragma unroll
-      for (int j = i; j < D; ++j) Ls[pidx<D>(i, j)] = fma(-T[q][i], vq[j], Ls[pidx<D>(i, j)]);
-#pragma unroll
-    for (int j = 0; j < D; ++j) T[q][j] = vq[j];
+  for (int e = 0; e < Sym<D>::N; ++e) {
+    p[D * D + D + e] = sP[e * SST];
   }
 #pragma unroll
-  for (int e = 0; e < Sym<D>::N; ++e) p[D * D + D + e] = Ls[e];
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) p[D * D + D + Sym<D>::N + pidx<D>(i, j)] = Pm[i][j];
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     double r[D];
@@ -357,18 +360,24 @@ __device__ __forceinline__ bool smoother_element_store(double* rec, int64_t k, c
 }
 
 template <int D>
-__device__ __forceinline__ void load_egl(const double* rec, int64_t k, SAgg<D>& e) {
+__device__ __forceinline__ void load_rts(const double* rec, int64_t k, Mat<D>& E, Vec<D>& g, Mat<D>& P,
+                                         Mat<D>& Pm) {
   const double* p = rec + k * egs_of<D>();
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
-    for (int j = 0; j < D; ++j) e.E[i][j] = p[i * D + j];
+    for (int j = 0; j < D; ++j) E[i][j] = p[i * D + j];
 #pragma unroll
-  for (int i = 0; i < D; ++i) e.g[i] = p[D * D + i];
+  for (int i = 0; i < D; ++i) g[i] = p[D * D + i];
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
-    for (int j = i; j < D; ++j) { e.L[i][j] = p[D * D + D + pidx<D>(i, j)]; e.L[j][i] = e.L[i][j]; }
+    for (int j = i; j < D; ++j) {
+      P[i][j] = p[D * D + D + pidx<D>(i, j)];
+      P[j][i] = P[i][j];
+      Pm[i][j] = p[D * D + D + Sym<D>::N + pidx<D>(i, j)];
+      Pm[j][i] = Pm[i][j];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1148,12 +1157,13 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
         if (!cholesky<D>(Pm1, Lc, invd)) bad = true;
         fixed_point_finish<D>(fp, F1, xm1, Lc, invd, sa);
       } else {
-        SAgg<D> e;
+        SAgg<D> e;   // the series' last element: E = 0, g = x_{n-1}, P^s = P_{n-1}
+        Mat<D> Z;
         set_zero<D>(e.E);
+        set_zero<D>(Z);
 #pragma unroll
         for (int i = 0; i < D; ++i) e.g[i] = x[i];
-        copy<D>(P, e.L);
-        store_egl<D>(a.rec_egl, k1 - 1, e);
+        store_rts<D>(a.rec_egl, k1 - 1, e, P, Z);
         set_zero<D>(sa.E);
 #pragma unroll
         for (int i = 0; i < D; ++i) sa.g[i] = fp.mu[i];
@@ -1265,13 +1275,19 @@ __global__ void __launch_bounds__(BLOCK, 1) k_smoother_propagate(const DevModel<
   }
 #pragma unroll 1
   for (int64_t k = khi; k >= k0; --k) {
-    SAgg<D> e;
-    load_egl<D>(a.rec_egl, k, e);
+    Mat<D> E, Pk, Pm;
+    Vec<D> g;
+    load_rts<D>(a.rec_egl, k, E, g, Pk, Pm);
     Vec<D> m2;
     Mat<D> T, P2;
-    mulv_add<D>(e.E, ms, e.g, m2);
-    mul<D>(e.E, Ps, T);
-    mul_Bt_sym_add<D>(T, e.E, e.L, P2);
+    mulv_add<D>(E, ms, g, m2);
+    // P^s_k = P_k + E (P^s_{k+1} - P^-_{k+1}) E^T
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = i; j < D; ++j) { Ps[i][j] -= Pm[i][j]; Ps[j][i] = Ps[i][j]; }
+    mul<D>(E, Ps, T);
+    mul_Bt_sym_add<D>(T, E, Pk, P2);
 #pragma unroll
     for (int i = 0; i < D; ++i) ms[i] = m2[i];
     copy<D>(P2, Ps);
@@ -1321,8 +1337,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_smoother_elements(const DevModel<D
           P[jj][i] = P[i][jj];
         }
       SAgg<D> e, r;
+      Mat<D> Pm;
       if (!last) {
-        Mat<D> T, Pm;
+        Mat<D> T;
         Vec<D> xm;
         mulv<D>(F, x, xm);
         mul<D>(F, P, T);
@@ -1330,11 +1347,12 @@ __global__ void __launch_bounds__(BLOCK, 1) k_smoother_elements(const DevModel<D
         if (!smoother_element<D>(x, P, T, xm, Pm, e)) bad = true;
       } else {
         set_zero<D>(e.E);
+        set_zero<D>(Pm);
 #pragma unroll
         for (int i = 0; i < D; ++i) e.g[i] = x[i];
         copy<D>(P, e.L);
       }
-      store_egl<D>(a.rec_egl, k, e);
+      store_rts<D>(a.rec_egl, k, e, P, Pm);
       sagg_combine<D>(sa, e, r);
       sa = r;
     }
