@@ -37,8 +37,8 @@ METRIC = "filter+smoother time steps/s at N=2^20,d=6 FP64"
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels at the
 # 2^20 workload itself; a launch's traffic is this x n.  Reset an entry to None
 # whenever its kernel changes.
-PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": None, "filter_reduce": 767.3, "discretize": 477.9,
-                                "smoother_propagate": None}
+PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1344.9, "filter_reduce": 799.8, "discretize": 477.6,
+                                "smoother_propagate": 682.2}
 UNIT = "steps/s"
 WORKLOADS = {
     "rbf6": dict(kind="rbf", order=6, lengthscale=1.0, variance=1.0, noise=0.01),
@@ -98,12 +98,11 @@ def flops_kf_step(d, observed_frac):
 
 
 def flops_smoother_element(d):
-    """E, g, L from P^- = Lu diag(dd) Lu^T (square-root free; one reciprocal
-    per pivot): W = Lu^{-1} T, V = diag(1/dd) W, L = P - W^T V,
-    E^T = Lu^{-T} V, g = x - E x^-."""
-    s = d * (d + 1) // 2
+    """E and g from P^- = Lu diag(dd) Lu^T (square-root free; one reciprocal
+    per pivot): W = Lu^{-1} T, V = diag(1/dd) W, E^T = Lu^{-T} V,
+    g = x - E x^- (the record keeps P_k and P^- instead of L)."""
     ldl = sum(2 * j + 1 + (d - 1 - j) * (2 * j + 1) for j in range(d))
-    return ldl + 2 * d * d * (d - 1) + d * d + 2 * s * d + 2 * d * d
+    return ldl + 2 * d * d * (d - 1) + d * d + 2 * d * d
 
 
 def flops_smoother_fold(d):
@@ -112,8 +111,9 @@ def flops_smoother_fold(d):
 
 
 def flops_rts_step(d):
+    """m = E m' + g; P^s = P + E (P^s' - P^-) E^T."""
     s = d * (d + 1) // 2
-    return 2 * d * d + (2 * d ** 3 - d * d) + 2 * s * d
+    return 2 * d * d + s + (2 * d ** 3 - d * d) + 2 * s * d
 
 
 def flops_adjoint_fold(d, observed_frac):
