@@ -198,7 +198,7 @@ struct ScanArgs {
   int R_per_step;
   int64_t n, L, P0, P2;
   double* rec_fq;        // per step: F (d*d), Q packed
-  double* rec_egl;       // per step: E (d*d), g (d), L packed
+  double* rec_egl;       // per step: the RTS record E (d*d), g (d), P_k and P^-_{k+1} (packed)
   double* lagg_f;        // [nf][P0] level-1 inclusive lane aggregates
   double* wagg_f;        // [nf][P2] warp totals (level-2 input)
   const double* wfin_f;  // [nf][P2] level-2 inclusive results
