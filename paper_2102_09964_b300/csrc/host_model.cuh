@@ -40,6 +40,12 @@ inline DevModel<D> dev_model(const pssgp_model* pm) {
   m.companion = pm->companion;
   for (int i = 0; i < D; ++i)
     for (int j = 0; j < D; ++j) { m.rsup[i][j] = pm->rsup[i * D + j]; m.rlast[i][j] = pm->rlast[i * D + j]; }
+  // rows 1..d-1 of Q from row 0 (companion_q_rows): companion drift and a
+  // diffusion with the single entry W[d-1][d-1]
+  bool rank1 = true;
+  for (int e = 0; e + 1 < D * D; ++e) rank1 = rank1 && pm->W[e] == 0.0;
+  m.qrows = (pm->companion && rank1 && pm->W[D * D - 1] > 0.0) ? 1 : 0;
+  for (int i = 0; i + 1 < D; ++i) m.wg[i] = m.qrows ? pm->W[D * D - 1] / pm->G[i * D + i + 1] : 0.0;
   return m;
 }
 

@@ -30,6 +30,8 @@ struct DevModel {
   double qc[Sym<D>::N][NT];
   double rsup[D][D];            // companion row recursion (see pssgp.h)
   double rlast[D][D];
+  double wg[D];                 // W[d-1][d-1] / G[i][i+1] (companion Q rows)
+  int qrows;                    // companion drift and W = w e_{d-1} e_{d-1}^T
   float hthr_f[NT + 1];
   float hthr_q[NT + 1];
   float hmax;
@@ -48,7 +50,9 @@ struct DevModel {
 // host-precomputed coefficients.  The term counts are chosen per warp from the
 // warp's longest step against bounds built from the exact norms ||G^m||, ||W_m||
 // (float arithmetic, off the FP64 pipe).  For a companion-form drift only row 0
-// of F is summed; row i+1 is row i times G scaled (2 FP64 ops per entry).
+// of F is summed; row i+1 is row i times G scaled (2 FP64 ops per entry); with
+// a rank-one diffusion on the last state also only row 0 of Q is summed and
+// the other rows follow from the Lyapunov identity (companion_q_rows).
 // Steps longer than hmax are halved s times and doubled back with
 // F(2h) = F(h)^2, Q(2h) = F(h) Q(h) F(h)^T + Q(h).
 // first = true gives the prior at a series' first time: F = 0, Q = P_inf.
@@ -67,6 +71,37 @@ __device__ __noinline__ void double_steps(Mat<D>& F, Mat<D>& Q, int s, int smax)
       copy<D>(Q2, Q);
       copy<D>(F2, F);
     }
+  }
+}
+
+// Rows 1..d-1 of Q from its row 0 and the last column f of F, for a
+// companion drift (rows 0..d-2 of G hold only g_i = G[i][i+1]) and a rank-one
+// diffusion W = w e_{d-1} e_{d-1}^T.  Differentiating
+// Q(h) = int_0^h e^{sG} W e^{sG}^T ds gives G Q + Q G^T = F W F^T - W, whose
+// entries (i, j), i < d-1, read
+//   g_i Q[i+1][j] + g_j Q[i][j+1]               = w f_i f_j    (j < d-1)
+//   g_i Q[i+1][d-1] + sum_k G[d-1][k] Q[i][k]   = w f_i f_{d-1}
+// so row i+1 follows from row i in O(d) operations per entry instead of a
+// Taylor sum.  For steps short against the model's scale the two sides of
+// each line are of the same order in h and every entry keeps its relative
+// accuracy; for long steps the error is small against sqrt(Q_ii Q_jj).
+// qscale multiplies w (Q is linear in W).  Row 0 must be complete on entry.
+template <int D>
+__device__ __forceinline__ void companion_q_rows(const DevModel<D>& m, const Mat<D>& F, Mat<D>& Q,
+                                                 double qscale) {
+#pragma unroll
+  for (int j = 1; j < D; ++j) Q[j][0] = Q[0][j];
+#pragma unroll
+  for (int i = 0; i + 1 < D; ++i) {
+    const double wf = (qscale * m.wg[i]) * F[i][D - 1];
+#pragma unroll
+    for (int j = i + 1; j + 1 < D; ++j) Q[i + 1][j] = fma(wf, F[j][D - 1], -m.rsup[i][j + 1] * Q[i][j + 1]);
+    double s = wf * F[D - 1][D - 1];
+#pragma unroll
+    for (int k = 0; k < D; ++k) s = fma(-m.rlast[i][k], Q[i][k], s);
+    Q[i + 1][D - 1] = s;
+#pragma unroll
+    for (int j = i + 2; j < D; ++j) Q[j][i + 1] = Q[i + 1][j];
   }
 }
 
@@ -131,22 +166,36 @@ __device__ __forceinline__ void discretize_fp64(const DevModel<D>& m, double h, 
         for (int j = 0; j < D; ++j) F[i][j] = fma(F[i][j], hs, m.fc[i * D + j][t]);
     }
   }
+  const double hq = hs * qscale;
+  if (m.qrows && !all_terms) {
+    // row 0 by Horner, the other rows from the Lyapunov identity
 #pragma unroll
-  for (int i = 0; i < D; ++i)
-#pragma unroll
-    for (int j = i; j < D; ++j) Q[i][j] = m.qc[pidx<D>(i, j)][kq - 1];
+    for (int j = 0; j < D; ++j) Q[0][j] = m.qc[j][kq - 1];
 #pragma unroll 1
-  for (int t = kq - 2; t >= 0; --t) {
+    for (int t = kq - 2; t >= 0; --t) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) Q[0][j] = fma(Q[0][j], hs, m.qc[j][t]);
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) Q[0][j] *= hq;
+    companion_q_rows<D>(m, F, Q, qscale);
+  } else {
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
-      for (int j = i; j < D; ++j) Q[i][j] = fma(Q[i][j], hs, m.qc[pidx<D>(i, j)][t]);
+      for (int j = i; j < D; ++j) Q[i][j] = m.qc[pidx<D>(i, j)][kq - 1];
+#pragma unroll 1
+    for (int t = kq - 2; t >= 0; --t) {
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = i; j < D; ++j) Q[i][j] = fma(Q[i][j], hs, m.qc[pidx<D>(i, j)][t]);
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = i; j < D; ++j) { Q[i][j] *= hq; Q[j][i] = Q[i][j]; }
   }
-  const double hq = hs * qscale;
-#pragma unroll
-  for (int i = 0; i < D; ++i)
-#pragma unroll
-    for (int j = i; j < D; ++j) { Q[i][j] *= hq; Q[j][i] = Q[i][j]; }
   // doubling for long steps (rare; each lane applies its own count)
   if (smax > 0) double_steps<D>(F, Q, s, smax);
   if (first) {
@@ -258,7 +307,36 @@ __device__ __forceinline__ void discretize_split(const DevModel<D>& m, double h,
         for (int j = 0; j < D; ++j) F[i][j] = fma(F[i][j], hs, m.fc[i * D + j][t]);
     }
   }
-  {
+  const double hq = hs * qscale;
+  if (m.qrows && !all_terms) {
+    // row 0 by Horner (FP32 tail, FP64 head), the other rows from the
+    // Lyapunov identity
+    int t0 = kq - 2;
+    if (mq < kq) {
+      float a[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) a[j] = m.qc32[j][kq - 1];
+#pragma unroll 1
+      for (int t = kq - 2; t >= mq; --t) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) a[j] = fmaf(a[j], h32, m.qc32[j][t]);
+      }
+#pragma unroll
+      for (int j = 0; j < D; ++j) Q[0][j] = (double)a[j];
+      t0 = mq - 1;
+    } else {
+#pragma unroll
+      for (int j = 0; j < D; ++j) Q[0][j] = m.qc[j][kq - 1];
+    }
+#pragma unroll 1
+    for (int t = t0; t >= 0; --t) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) Q[0][j] = fma(Q[0][j], hs, m.qc[j][t]);
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) Q[0][j] *= hq;
+    companion_q_rows<D>(m, F, Q, qscale);
+  } else {
     int t0 = kq - 2;
     if (mq < kq) {
       float a[Sym<D>::N];
@@ -287,12 +365,11 @@ __device__ __forceinline__ void discretize_split(const DevModel<D>& m, double h,
 #pragma unroll
         for (int j = i; j < D; ++j) Q[i][j] = fma(Q[i][j], hs, m.qc[pidx<D>(i, j)][t]);
     }
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = i; j < D; ++j) { Q[i][j] *= hq; Q[j][i] = Q[i][j]; }
   }
-  const double hq = hs * qscale;
-#pragma unroll
-  for (int i = 0; i < D; ++i)
-#pragma unroll
-    for (int j = i; j < D; ++j) { Q[i][j] *= hq; Q[j][i] = Q[i][j]; }
   // doubling for long steps (rare; each lane applies its own count)
   if (smax > 0) double_steps<D>(F, Q, s, smax);
   if (first) {
