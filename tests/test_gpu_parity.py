@@ -336,6 +336,25 @@ def test_predict_rbf_orders_up_to_the_largest_state(order):
     check_marginals(host(mean), host(var), float(host(ll)[0]), fm, fv, res.loglik, s.N, 1e-6, f"rbf{order}")
 
 
+def test_companion_drift_with_full_diffusion():
+    """A companion drift whose white noise also drives the first states
+    (L = (0.4, -0.3, 1)): F still takes the companion recursion, but Q has no
+    rank-one structure on the last state, so every entry of Q is summed by
+    its Taylor series instead of rows 1..d-1 following from row 0."""
+    s = wl.prefix(wl.sinusoid_large(N=1 << 15, M=400), 8000)
+    o = om.make_model("matern52", 0.8, 1.0)
+    o.L = np.array([[0.4], [-0.3], [1.0]])
+    o.Pinf = om.lyapunov(o.G, o.W)
+    m = P.model_from_sde(o.G, o.L, o.q, o.H)
+    assert m.raw.companion == 1
+    W = np.ctypeslib.as_array(m.raw.W)[:9].reshape(3, 3)
+    assert np.count_nonzero(W) > 1
+    mean, var, ll, ws = P.predict(m, dev(s.t_train), dev(s.y_train), dev(s.t_test), 0.02)
+    assert P.status(ws) == 0
+    fm, fv, res, _ = oracle.predict(o, s.t_train, s.y_train, s.t_test, 0.02)
+    check_marginals(host(mean), host(var), float(host(ll)[0]), fm, fv, res.loglik, s.N, 1e-9, "full W")
+
+
 def _non_companion_sde():
     """Matern-5/2 in coordinates z = T^-1 x with T's first row e_0 (so
     H T = e_0^T) and the rest mixing: G' = T^-1 G T is not in companion form,
