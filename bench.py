@@ -74,13 +74,27 @@ def parse():
 # algorithmic FP64 flop counts per merged step (FMA = 2 flops; a reciprocal,
 # square root or comparison counts 1), from the formulas each kernel evaluates
 # ---------------------------------------------------------------------------
-def flops_discretize(d, kf, kq, companion=True):
+def flops_discretize(d, kf, kq, companion=True, qrows=True):
     s = d * (d + 1) // 2
     if companion:   # row 0 of F by Horner, rows 1..d-1 by the companion recursion
         f = 2 * d * (kf - 1) + (d - 1) * (1 + 3 * (d - 1))
     else:
         f = 2 * d * d * (kf - 1)
-    return f + 2 * s * (kq - 1) + s
+    if companion and qrows:
+        # row 0 of Q by Horner and its scaling; row i+1 from row i by the
+        # Lyapunov identity: w f_i, 3 flops per inner entry, 1 + 2d for the
+        # last column
+        q = 2 * d * (kq - 1) + d + (d - 1) * (2 + 2 * d) + 3 * (d - 2) * (d - 1) // 2
+    else:
+        q = 2 * s * (kq - 1) + s
+    return f + q
+
+
+def diffusion_on_last_state(model):
+    """True when W = w e_{d-1} e_{d-1}^T (rows 1..d-1 of Q follow from row 0)."""
+    d = model.d
+    W = np.ctypeslib.as_array(model.raw.W)[:d * d]
+    return bool(W[-1] > 0.0 and np.count_nonzero(W[:-1]) == 0)
 
 
 def flops_filter_fold(d, observed_frac):
@@ -655,7 +669,7 @@ def run_ours(args, wl_params):
     d = m.d
     obs = N / n
     alg = {
-        "discretize": n * flops_discretize(d, kf, kq, bool(m.raw.companion)),
+        "discretize": n * flops_discretize(d, kf, kq, bool(m.raw.companion), diffusion_on_last_state(m)),
         "filter_reduce": n * flops_filter_fold(d, obs),
         # the smoother chunk aggregate is formed once per lane (not per step)
         "filter_propagate": n * (flops_kf_step(d, obs) + flops_smoother_element(d)),
