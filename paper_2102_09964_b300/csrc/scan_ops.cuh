@@ -408,15 +408,6 @@ struct FAgg {
 };
 template <int D> struct FAggSize { static constexpr int N = D * D + 2 * D + 2 * Sym<D>::N; };
 
-template <int D>
-__device__ __forceinline__ void fagg_identity(FAgg<D>& a) {
-  set_eye<D>(a.A);
-  set_zero<D>(a.C);
-  set_zero<D>(a.J);
-#pragma unroll
-  for (int i = 0; i < D; ++i) { a.b[i] = 0.0; a.eta[i] = 0.0; }
-}
-
 // Aggregate of a run of consecutive elements, folded one raw element at a
 // time.  The tuple (A, b, C, eta, J) of elements s+1..k encodes the affine
 // conditional p(x_k | x_s, y_{s+1:k}) = N(A x_s + b, C) and the likelihood
@@ -428,50 +419,9 @@ __device__ __forceinline__ void fagg_identity(FAgg<D>& a) {
 // w w^T / S to J and w r / S to eta.  An unobserved step keeps only the
 // prediction (the missing-element case of Sec. 3).  A series' first step has
 // F = 0, Q = P_inf, giving A = 0, eta = 0, J = 0 as for the k = 1 elements.
-template <int D>
-__device__ __forceinline__ void fagg_fold_step(FAgg<D>& a, const Mat<D>& F, const Mat<D>& Q,
-                                               bool observed, double y, double R, bool& bad) {
-  Mat<D> Am, T, Pm;
-  Vec<D> bm;
-  mul<D>(F, a.A, Am);
-  mulv<D>(F, a.b, bm);
-  mul<D>(F, a.C, T);
-  mul_Bt_sym_add<D>(T, F, Q, Pm);
-  if (observed) {
-    const double S = Pm[0][0] + R;
-    if (bad_pos(S)) bad = true;
-    const double Si = __drcp_rn(S);
-    const double r = y - bm[0];
-    Vec<D> ws, K;
-#pragma unroll
-    for (int i = 0; i < D; ++i) ws[i] = Am[0][i] * Si;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-#pragma unroll
-      for (int j = i; j < D; ++j) { a.J[i][j] = fma(ws[i], Am[0][j], a.J[i][j]); a.J[j][i] = a.J[i][j]; }
-      a.eta[i] = fma(ws[i], r, a.eta[i]);
-    }
-#pragma unroll
-    for (int i = 0; i < D; ++i) K[i] = Pm[i][0] * Si;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-#pragma unroll
-      for (int j = 0; j < D; ++j) a.A[i][j] = fma(-K[i], Am[0][j], Am[i][j]);
-      a.b[i] = fma(K[i], r, bm[i]);
-#pragma unroll
-      for (int j = i; j < D; ++j) { a.C[i][j] = fma(-K[i], Pm[0][j], Pm[i][j]); a.C[j][i] = a.C[i][j]; }
-    }
-  } else {
-    copy<D>(Am, a.A);
-    copy<D>(Pm, a.C);
-#pragma unroll
-    for (int i = 0; i < D; ++i) a.b[i] = bm[i];
-  }
-}
-
-// The same fold with the chunk aggregate split between registers (b, C) and
-// shared memory (A double-buffered, J and eta; element e of a thread's
-// matrix at ptr[e * SST], so a warp's accesses hit 32 consecutive banks).
+// The chunk aggregate is split between registers (b, C) and shared memory
+// (A double-buffered, J and eta; element e of a thread's matrix at
+// ptr[e * SST], so a warp's accesses hit 32 consecutive banks).
 // P^- = F C F^T + Q is built one row of F C at a time, and A' = F A row by
 // row.  Returns the step's S = H P^- H^T + R, 1/S and innovation r = y - H F b
 // (1/S = r = 0 on a missing step): the terms of the chunk's log-likelihood
