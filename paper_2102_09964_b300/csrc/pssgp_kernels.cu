@@ -245,6 +245,17 @@ template <int D> __host__ __device__ constexpr int fqs_of() { return (D * D + Sy
 // predicted covariance P^-_{k+1} (both packed)
 template <int D> __host__ __device__ constexpr int egs_of() { return (D * D + D + 2 * Sym<D>::N + 1) / 2 * 2; }
 
+// Ask for a per-step record of N doubles (the next step's) in L1 while the
+// current step computes: a lane spends microseconds on a step at d = 6, far
+// longer than a DRAM access, but its loads are issued only when the step
+// starts.  One prefetch per 128-byte line, every address inside the record.
+template <int N>
+__device__ __forceinline__ void prefetch_record(const double* p) {
+#pragma unroll
+  for (int o = 0; o < N; o += 16) asm volatile("prefetch.global.L1 [%0];" ::"l"(p + o));
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p + N - 1));
+}
+
 template <int D>
 __device__ __forceinline__ void load_fq(const double* rec, int64_t k, Mat<D>& F, Mat<D>& Q) {
   const double* p = rec + k * fqs_of<D>();
@@ -928,6 +939,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
         lp = LogProd();
       }
     }
+    if (k + 1 < k1) prefetch_record<fqs_of<D>()>(a.rec_fq + (k + 1) * fqs_of<D>());
     Mat<D> F, Q, T, Pm;
     Vec<D> xm;
     load_fq<D>(a.rec_fq, k, F, Q);
@@ -1275,6 +1287,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_smoother_propagate(const DevModel<
   }
 #pragma unroll 1
   for (int64_t k = khi; k >= k0; --k) {
+    if (k > k0) prefetch_record<egs_of<D>()>(a.rec_egl + (k - 1) * egs_of<D>());
     Mat<D> E, Pk, Pm;
     Vec<D> g;
     load_rts<D>(a.rec_egl, k, E, g, Pk, Pm);
