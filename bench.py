@@ -37,8 +37,8 @@ METRIC = "filter+smoother time steps/s at N=2^20,d=6 FP64"
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels at the
 # 2^20 workload itself; a launch's traffic is this x n.  Reset an entry to None
 # whenever its kernel changes.
-PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1343.4, "filter_reduce": 797.6, "discretize": 472.5,
-                                "smoother_propagate": 682.2}
+PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1338.0, "filter_reduce": 798.1, "discretize": 471.9,
+                                "smoother_propagate": 682.3}
 UNIT = "steps/s"
 WORKLOADS = {
     "rbf6": dict(kind="rbf", order=6, lengthscale=1.0, variance=1.0, noise=0.01),
