@@ -165,6 +165,41 @@ def test_discretize(kind):
     assert np.all(np.abs(Q - Qr).max(axis=(1, 2))[~nz] == 0)
 
 
+@pytest.mark.parametrize("kind", ["matern32", "matern52", "rbf"])
+def test_discretize_entrywise_short_steps(kind):
+    """Short steps (1e-6 to 3e-3 lengthscales) in warps that also hold a
+    step of 17 lengthscales, so that every warp sums all stored Taylor terms
+    of row 0: then every entry of Q at least 1e-12 of the step's largest
+    agrees with the oracle (pinned entrywise against a 50-digit evaluation)
+    to 1e-12 relative.  Rows 1..d-1 of Q come from row 0 through the
+    Lyapunov identity on the device; this checks that they keep the relative
+    accuracy of the small entries, which a normwise check does not see.  (With
+    only short steps in a warp, its normwise term count leaves entries of
+    order h^{2d-1} truncated: normwise negligible, not entrywise.)"""
+    hk = np.zeros(64)                                   # two warps of steps k = 0..63
+    long_k = [1, 33]
+    rest = [k for k in range(1, 64) if k not in long_k]
+    hk[long_k] = 17.0
+    hk[rest] = np.logspace(-6, np.log10(3e-3), len(rest))
+    t = np.cumsum(hk)
+    o = om.make_model(kind, 1.0, 1.0)
+    Fr, Qr = oracle.discretize(o, t)
+    m = P.build_model(kind, 1.0, 1.0)
+    d = m.d
+    F, Q, ws = P.discretize(m, dev(t))
+    assert P.status(ws) == 0
+    Q = unpack(host(Q), d)
+    worst = 0.0
+    for k in range(1, t.size):
+        if k in long_k:
+            continue
+        qmax = np.abs(Qr[k]).max()
+        big = np.abs(Qr[k]) >= 1e-12 * qmax
+        rel = np.abs(Q[k][big] - Qr[k][big]) / np.abs(Qr[k][big])
+        worst = max(worst, rel.max())
+    assert worst <= 1e-12, worst
+
+
 @pytest.mark.parametrize("seed", [0, 1])
 def test_merge_bit_exact(seed):
     rng = np.random.default_rng(seed)
