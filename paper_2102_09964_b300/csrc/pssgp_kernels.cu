@@ -400,8 +400,11 @@ __device__ __forceinline__ void load_rts(const double* rec, int64_t k, Mat<D>& E
 // shared memory and written out with consecutive threads on consecutive
 // addresses.
 constexpr int DISC_BLOCK = 128;
+// Three blocks per SM up to d = 6 (at most 170 registers; d = 6 spills
+// 24 bytes): the kernel alternates FP64 work with staging and coalesced
+// stores, and the third block fills the FP64 pipe during another's stores.
 template <int D>
-__global__ void __launch_bounds__(DISC_BLOCK) k_discretize_rec(const DevModel<D> m, const double* t, int64_t n,
+__global__ void __launch_bounds__(DISC_BLOCK, (D <= 6 ? 3 : 1)) k_discretize_rec(const DevModel<D> m, const double* t, int64_t n,
                                                              double* rec, double* tauq, int* status) {
   constexpr int FQS = fqs_of<D>();
   extern __shared__ double stage[];           // DISC_BLOCK * FQS doubles
