@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(DISC_BLOCK, (D <= 6 ? 3 : 1)) k_discretize_rec
     }
   }
   Mat<D> F, Q;
-  discretize<D>(m, h, first, act, F, Q);
+  discretize<D, false, true>(m, h, first, act, F, Q);
   store_fq<D>(stage, threadIdx.x, F, Q);     // record threadIdx.x of the block
   if (tauq && act) { tauq[2 * k] = h; tauq[2 * k + 1] = 1.0; }
   __syncthreads();
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_batched(const DevMode
     }
   }
   Mat<D> F, Q;
-  discretize<D, true>(m, h, first, act, F, Q, uscale, qscale);
+  discretize<D, true, true>(m, h, first, act, F, Q, uscale, qscale);
   store_fq<D>(stage, threadIdx.x, F, Q);
   if (act) {
     Rstep[k] = R;

@@ -58,9 +58,9 @@ struct DevModel {
 // first = true gives the prior at a series' first time: F = 0, Q = P_inf.
 // Must be called by all 32 lanes of a warp (warp reductions inside).
 // ---------------------------------------------------------------------------
-// s doublings F <- F F, Q <- F Q F^T + Q (kept out of line: rare path)
+// s doublings F <- F F, Q <- F Q F^T + Q
 template <int D>
-__device__ __noinline__ void double_steps(Mat<D>& F, Mat<D>& Q, int s, int smax) {
+__device__ __forceinline__ void double_steps_body(Mat<D>& F, Mat<D>& Q, int s, int smax) {
 #pragma unroll 1
   for (int r = 0; r < smax; ++r) {
     if (r < s) {
@@ -72,6 +72,13 @@ __device__ __noinline__ void double_steps(Mat<D>& F, Mat<D>& Q, int s, int smax)
       copy<D>(F2, F);
     }
   }
+}
+// out of line (rare path) for kernels whose registers are needed elsewhere;
+// the call keeps F and Q in a stack frame.  Kernels that only discretise
+// take the inline body (INL below) and need no frame.
+template <int D>
+__device__ __noinline__ void double_steps(Mat<D>& F, Mat<D>& Q, int s, int smax) {
+  double_steps_body<D>(F, Q, s, smax);
 }
 
 // Rows 1..d-1 of Q from its row 0 and the last column f of F, for a
@@ -113,7 +120,7 @@ __device__ __forceinline__ void companion_q_rows(const DevModel<D>& m, const Mat
 // all_terms: sum every stored Taylor term (entrywise accuracy of the small
 // entries of Q for short steps, which the per-warp normwise term count does
 // not give; needed where Q is factorised, as in the prior simulation).
-template <int D>
+template <int D, bool INL = false>
 __device__ __forceinline__ void discretize_fp64(const DevModel<D>& m, double h, bool first, bool active,
                                            Mat<D>& F, Mat<D>& Q, double uscale = 1.0, double qscale = 1.0,
                                            bool all_terms = false) {
@@ -197,7 +204,10 @@ __device__ __forceinline__ void discretize_fp64(const DevModel<D>& m, double h, 
       for (int j = i; j < D; ++j) { Q[i][j] *= hq; Q[j][i] = Q[i][j]; }
   }
   // doubling for long steps (rare; each lane applies its own count)
-  if (smax > 0) double_steps<D>(F, Q, s, smax);
+  if (smax > 0) {
+    if constexpr (INL) double_steps_body<D>(F, Q, s, smax);
+    else double_steps<D>(F, Q, s, smax);
+  }
   if (first) {
 #pragma unroll
     for (int i = 0; i < D; ++i)
@@ -209,7 +219,7 @@ __device__ __forceinline__ void discretize_fp64(const DevModel<D>& m, double h, 
   }
 }
 
-template <int D>
+template <int D, bool INL = false>
 __device__ __forceinline__ void discretize_split(const DevModel<D>& m, double h, bool first, bool active,
                                            Mat<D>& F, Mat<D>& Q, double uscale = 1.0, double qscale = 1.0,
                                            bool all_terms = false) {
@@ -371,7 +381,10 @@ __device__ __forceinline__ void discretize_split(const DevModel<D>& m, double h,
       for (int j = i; j < D; ++j) { Q[i][j] *= hq; Q[j][i] = Q[i][j]; }
   }
   // doubling for long steps (rare; each lane applies its own count)
-  if (smax > 0) double_steps<D>(F, Q, s, smax);
+  if (smax > 0) {
+    if constexpr (INL) double_steps_body<D>(F, Q, s, smax);
+    else double_steps<D>(F, Q, s, smax);
+  }
   if (first) {
 #pragma unroll
     for (int i = 0; i < D; ++i)
@@ -386,13 +399,14 @@ __device__ __forceinline__ void discretize_split(const DevModel<D>& m, double h,
 // SPLIT = true: mixed precision (the terms below 2^-36 of the series summed in
 // FP32), for kernels where steps are long relative to the model's scale (the
 // batched path); SPLIT = false keeps every term in FP64 and the term counts
-// warp-uniform through the uniform datapath.
-template <int D, bool SPLIT = false>
+// warp-uniform through the uniform datapath.  INL = true inlines the doubling
+// of long steps (kernels that do nothing but discretise).
+template <int D, bool SPLIT = false, bool INL = false>
 __device__ __forceinline__ void discretize(const DevModel<D>& m, double h, bool first, bool active,
                                            Mat<D>& F, Mat<D>& Q, double uscale = 1.0, double qscale = 1.0,
                                            bool all_terms = false) {
-  if constexpr (SPLIT) discretize_split<D>(m, h, first, active, F, Q, uscale, qscale, all_terms);
-  else discretize_fp64<D>(m, h, first, active, F, Q, uscale, qscale, all_terms);
+  if constexpr (SPLIT) discretize_split<D, INL>(m, h, first, active, F, Q, uscale, qscale, all_terms);
+  else discretize_fp64<D, INL>(m, h, first, active, F, Q, uscale, qscale, all_terms);
 }
 
 // ---------------------------------------------------------------------------
