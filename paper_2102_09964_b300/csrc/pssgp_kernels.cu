@@ -256,17 +256,39 @@ __device__ __forceinline__ void prefetch_record(const double* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p + N - 1));
 }
 
-template <int D>
+// A per-step record of N doubles (N even) by 16-byte loads: every record
+// starts on a 16-byte boundary (the workspace regions are 256-byte aligned
+// and the record lengths even), and half as many load instructions queue in
+// the load/store unit.
+template <int N>
+__device__ __forceinline__ void load_record(const double* p, double (&r)[N]) {
+  static_assert(N % 2 == 0, "records have an even number of doubles");
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) {
+    const double2 v = q[i];
+    r[2 * i] = v.x;
+    r[2 * i + 1] = v.y;
+  }
+}
+
+template <int D, bool VEC = true>
 __device__ __forceinline__ void load_fq(const double* rec, int64_t k, Mat<D>& F, Mat<D>& Q) {
-  const double* p = rec + k * fqs_of<D>();
+  double r[fqs_of<D>()];
+  if constexpr (VEC) {
+    load_record(rec + k * fqs_of<D>(), r);
+  } else {
+#pragma unroll
+    for (int e = 0; e < fqs_of<D>(); ++e) r[e] = rec[k * fqs_of<D>() + e];
+  }
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
-    for (int j = 0; j < D; ++j) F[i][j] = p[i * D + j];
+    for (int j = 0; j < D; ++j) F[i][j] = r[i * D + j];
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
-    for (int j = i; j < D; ++j) { Q[i][j] = p[D * D + pidx<D>(i, j)]; Q[j][i] = Q[i][j]; }
+    for (int j = i; j < D; ++j) { Q[i][j] = r[D * D + pidx<D>(i, j)]; Q[j][i] = Q[i][j]; }
 }
 template <int D>
 __device__ __forceinline__ void store_fq(double* rec, int64_t k, const Mat<D>& F, const Mat<D>& Q) {
@@ -373,7 +395,8 @@ __device__ __forceinline__ bool smoother_element_store(double* rec, int64_t k, c
 template <int D>
 __device__ __forceinline__ void load_rts(const double* rec, int64_t k, Mat<D>& E, Vec<D>& g, Mat<D>& P,
                                          Mat<D>& Pm) {
-  const double* p = rec + k * egs_of<D>();
+  double p[egs_of<D>()];
+  load_record(rec + k * egs_of<D>(), p);
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -595,6 +618,7 @@ __device__ __forceinline__ void save_fold_state(const ScanArgs& a, int64_t g, co
 template <int D, int RMODE>
 __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m, const ScanArgs a) {
   constexpr bool LL = RMODE == RED_LL;
+  constexpr bool VECMODE = RMODE == RED_ADJ;   // 16-byte record loads: measured faster only here
   extern __shared__ double smem[];
   double* sA0 = smem + threadIdx.x;
   double* sA1 = sA0 + D * D * BLOCK;
@@ -644,7 +668,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
       if (k == k1 - 1 && k1 < a.n) save_fold_state<D>(a, g, Ain, seta, sJ);   // steps k0 .. k1-2
     }
     Mat<D> F, Q;
-    load_fq<D>(a.rec_fq, k, F, Q);
+    load_fq<D, VECMODE>(a.rec_fq, k, F, Q);
     if constexpr (RMODE == RED_ADJ) {
       if (k == k0) {   // from the predicted state of step k0: no transition
         set_eye<D>(F);
