@@ -1,7 +1,8 @@
 """Pins for the oracle's discretisation, supplement Eq. (ss-gp-formation).
 
 Checked against: the Ornstein-Uhlenbeck (Matern-1/2) closed form, a library
-matrix exponential, stationarity F P_inf F^T + Q = P_inf (Sec. 4.1), and a
+matrix exponential, stationarity F P_inf F^T + Q = P_inf (Sec. 4.1), the
+Lyapunov identity G Q + Q G^T = F W F^T - W of the integral, and a
 50-digit evaluation of Q by mpmath quadrature-free Van Loan (entrywise,
 including entries that are many orders smaller than P_inf).
 """
@@ -46,6 +47,25 @@ def test_stationarity_and_expm(oracle_lib, kind, balanced):
     # h = 0 (duplicate time): F = I, Q = 0 exactly
     np.testing.assert_array_equal(F[6], np.eye(m.d))
     np.testing.assert_array_equal(Q[6], np.zeros((m.d, m.d)))
+
+
+@pytest.mark.parametrize("kind", ["matern32", "matern52", "rbf"])
+@pytest.mark.parametrize("balanced", [False, True])
+def test_lyapunov_identity_of_the_integral(oracle_lib, kind, balanced):
+    """d/dh of Q(h) = int_0^h e^{sG} W e^{sG}^T ds is G Q + Q G^T + W and also
+    F W F^T, so G Q + Q G^T = F W F^T - W at every step (the identity from
+    which the device forms rows 1..d-1 of Q).  Checked against the scale of
+    its terms, over steps from 1e-4 to 10 lengthscales."""
+    m = om.make_model(kind, 1.0, 1.0, balanced=balanced)
+    h = np.array([1e-4, 3e-3, 0.05, 0.4, 2.0, 10.0])
+    t = np.cumsum(np.concatenate([[0.0], h]))
+    F, Q = oracle.discretize(m, t)
+    W = m.W
+    for k in range(1, t.size):
+        lhs = m.G @ Q[k] + Q[k] @ m.G.T
+        rhs = F[k] @ W @ F[k].T - W
+        scale = np.abs(m.G).max() * np.abs(Q[k]).max() + np.abs(W).max()
+        assert np.abs(lhs - rhs).max() <= 1e-13 * scale, (k, np.abs(lhs - rhs).max() / scale)
 
 
 def _mp_vanloan(G, W, h, dps=50):
