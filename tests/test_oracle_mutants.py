@@ -34,13 +34,15 @@ MUTANTS = [
     ("element_J_no_S", "J[i * d + j] = HF[i] * HF[j] / S;", "J[i * d + j] = HF[i] * HF[j];"),
     ("element_C_no_update", "mm(d, d, d, IKH, Q, C);", "memcpy(C, Q, sizeof(real) * dd);"),
     ("smoother_g_sign", "g[i] = m[i] - EFm[i];", "g[i] = m[i] + EFm[i];"),
+    ("vanloan_Q_order", "mm(d, d, d, F, E12, Q);", "mm(d, d, d, E12, F, Q);"),
     ("smoother_combine_transposed", "mm(d, d, d, Ei, Lj, T);\n  tr(d, d, Ei, Eit);\n  mm(d, d, d, T, Eit, L);",
      "tr(d, d, Ei, Eit);\n  mm(d, d, d, Eit, Lj, T);\n  mm(d, d, d, T, Ei, L);"),
 ]
 
 
 def _battery():
-    """The pins in miniature: dense GP (Lemma), stationarity, Props. 1 and 2."""
+    """The pins in miniature: dense GP (Lemma), stationarity, the Lyapunov
+    identity of Q, Props. 1 and 2."""
     rng = np.random.default_rng(21)
     n = 120
     t = np.sort(rng.uniform(0, 12, n))
@@ -55,6 +57,10 @@ def _battery():
         assert abs(res.loglik - ll) < 1e-9 * max(abs(ll), n)
         for k in (1, 50, 100):
             assert np.abs(res.F[k] @ m.Pinf @ res.F[k].T + res.Q[k] - m.Pinf).max() < 1e-12 * np.abs(m.Pinf).max()
+            # the Lyapunov identity of the integral, G Q + Q G^T = F W F^T - W
+            lhs = m.G @ res.Q[k] + res.Q[k] @ m.G.T
+            rhs = res.F[k] @ m.W @ res.F[k].T - m.W
+            assert np.abs(lhs - rhs).max() < 1e-12 * (np.abs(m.G).max() * np.abs(res.Q[k]).max() + np.abs(m.W).max())
         tl = np.array([0.0, 40.0])        # a long step exercises the doubling
         F, Q = oracle.discretize(m, tl)
         assert np.abs(F[1] @ m.Pinf @ F[1].T + Q[1] - m.Pinf).max() < 1e-12 * np.abs(m.Pinf).max()
