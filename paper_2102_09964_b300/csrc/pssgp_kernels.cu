@@ -618,7 +618,9 @@ __device__ __forceinline__ void save_fold_state(const ScanArgs& a, int64_t g, co
 template <int D, int RMODE>
 __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m, const ScanArgs a) {
   constexpr bool LL = RMODE == RED_LL;
-  constexpr bool VECMODE = RMODE == RED_ADJ;   // 16-byte record loads: measured faster only here
+  // 16-byte record loads (load_record) made the gradient's instance faster;
+  // in the others they cost more register spills than they saved
+  constexpr bool VECMODE = RMODE == RED_ADJ;
   extern __shared__ double smem[];
   double* sA0 = smem + threadIdx.x;
   double* sA1 = sA0 + D * D * BLOCK;
