@@ -43,10 +43,13 @@ extern "C" {
 #endif
 
 #define PSSGP_DMAX 8
+/* Largest step count any entry point accepts (PSSGP_EINVAL above it): keeps
+ * every workspace size n x record x 8 bytes far from int64 overflow. */
+#define PSSGP_NMAX ((int64_t)1 << 40)
 
 /* ---- status codes ------------------------------------------------------ */
 #define PSSGP_OK 0
-#define PSSGP_EINVAL (-1)      /* null pointer, n < 1, ld < n, bad flag       */
+#define PSSGP_EINVAL (-1)      /* null pointer, n < 1 or > PSSGP_NMAX, ld < n, bad flag */
 #define PSSGP_EDIM (-2)        /* d outside 1..PSSGP_DMAX                      */
 #define PSSGP_EKERNEL (-3)     /* unknown kernel kind or invalid hyperparameter */
 #define PSSGP_EWORKSPACE (-4)  /* workspace too small or misaligned            */
@@ -262,20 +265,24 @@ int pssgp_loglik_grad_batched(const pssgp_model* model, const int64_t* offsets,
  * counterpart; this is a deployment convenience.
  *  - Scratch: a fixed 32 MiB array inside the library's device image, held on
  *    every GPU that loads the library until the process exits.  That bounds
- *    the problem size: n up to about 28,000 merged steps at d = 6 and about
- *    147,000 at d = 2 (exactly: the workspace of the current scan tuning,
- *    at most pssgp_workspace_size(d, n), must fit in 32 MiB).  Larger
- *    problems are rejected with PSSGP_ESCRATCH before anything is launched.
- *  - The first call on a device looks up the scratch's device address
- *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture.
+ *    the problem size: the workspace of the current scan tuning must fit in
+ *    32 MiB, which allows n (merged steps) up to 290,464 at d = 1, 137,781
+ *    at d = 2, 78,584 at d = 3, 24,594 at d = 6 and 14,574 at d = 8 (the
+ *    largest n with pssgp_workspace_size(d, n) <= 32 MiB; per-step records
+ *    plus the per-chunk aggregates).  Larger problems are rejected with PSSGP_ESCRATCH
+ *    before anything is launched.
+ *  - Every call looks up the scratch's device address in the current device's
+ *    context (cudaGetSymbolAddress, with that device current); the first call
+ *    on a device also loads the library's device code there, so make that
+ *    first call before any stream capture.
  *  - All calls share the one scratch array per device, so calls that overlap
  *    on the GPU (different streams or threads) race and give wrong results;
  *    serialise them.  Nothing from a previous call is reused: the status word
  *    is cleared at the start, everything else is written before it is read.
  *  - Arguments as pssgp_loglik; `status` (device pointer to one int32,
  *    nullable) receives the device status bits of this call.  The per-kernel
- *    timing diagnostic (pssgp_timing) must be off. */
+ *    timing diagnostic (pssgp_timing) creates CUDA events, so while it is on
+ *    this call returns PSSGP_EINVAL without launching anything. */
 int pssgp_loglik_noalloc(const pssgp_model* model, const double* t, const double* y,
                          const uint8_t* mask, const double* R, int32_t R_per_step,
                          int64_t n, double* loglik, int32_t* status, void* stream);
@@ -496,9 +503,12 @@ int pssgp_graph_destroy(pssgp_graph* graph);
 size_t pssgp_model_bytes(void);
 
 /* Measured FP64 fused-multiply-add rate of this device (lane FMAs per
- * second) from a short kernel with independent FMA chains on all SMs: the
- * denominator of the FP64 roofline.  Synchronous; allocates a small probe
- * buffer of its own. */
+ * second): the fastest of three timed launches (after a warm-up) of a kernel
+ * with eight independent FMA chains per thread at each of 4, 8 and 16 warps
+ * per SM, about 10 ms each.  The denominator of the FP64 roofline (the nominal
+ * rate is SMs x 128 lanes / 64 cycles per warp instruction x the SM clock).
+ * Synchronous on the legacy default stream; allocates a small probe buffer of
+ * its own. */
 int pssgp_fp64_fma_rate(double* fma_per_s);
 
 #ifdef __cplusplus

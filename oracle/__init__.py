@@ -228,11 +228,12 @@ def predict(m, t_train, y_train, t_test, R):
 GRAD_PARAMS = ("log_lengthscale", "log_variance", "log_noise")
 
 
-def loglik_tangent(m, t, y, mask, R, param):
+def loglik_tangent(m, t, y, mask, R, param, with_scale=False):
     """(loglik, d loglik / d param) by forward mode through the discretisation
     (Frechet derivative of the Van Loan exponential) and the sequential
     Kalman filter, with the model's tangent from ``model.model_tangent``.
-    ``m`` must be the unbalanced model; R scalar or per step."""
+    ``m`` must be the unbalanced model; R scalar or per step.  With
+    ``with_scale`` also the sum of |per-step term| of the derivative."""
     from . import model as _model
     lib = _load()
     d = m.d
@@ -253,22 +254,32 @@ def loglik_tangent(m, t, y, mask, R, param):
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
     ll = ctypes.c_double(0.0)
     dll = ctypes.c_double(0.0)
+    dabs = ctypes.c_double(0.0)
     rc = lib.orc_loglik_tangent(d, _p(_c(m.H).ravel()), _p(Ra), _p(dRa), per, _p(F), _p(Q), _p(dF), _p(dQ),
-                                _p(y), _u8(mask), ctypes.c_long(n), ctypes.byref(ll), ctypes.byref(dll))
+                                _p(y), _u8(mask), ctypes.c_long(n), ctypes.byref(ll), ctypes.byref(dll),
+                                ctypes.byref(dabs))
     _check(rc, "loglik_tangent")
+    if with_scale:
+        return ll.value, dll.value, dabs.value
     return ll.value, dll.value
 
 
-def loglik_grad_fwd(kind, lengthscale, variance, t, y, mask, R, order=6):
+def loglik_grad_fwd(kind, lengthscale, variance, t, y, mask, R, order=6, with_scale=False):
     """(loglik, gradient over GRAD_PARAMS) by forward mode, one direction at a
-    time (R scalar or per step; d/d log noise scales every R_k)."""
+    time (R scalar or per step; d/d log noise scales every R_k).  With
+    ``with_scale`` also, per component, the sum over steps of the absolute
+    per-step terms (``loglik_tangent``)."""
     from . import model as _model
     m = _model.make_model(kind, lengthscale, variance, order=order)
     g = []
+    sc = []
     ll = None
     for p in GRAD_PARAMS:
-        ll, dl = loglik_tangent(m, t, y, mask, R, p)
+        ll, dl, ds = loglik_tangent(m, t, y, mask, R, p, with_scale=True)
         g.append(dl)
+        sc.append(ds)
+    if with_scale:
+        return ll, np.array(g), np.array(sc)
     return ll, np.array(g)
 
 
@@ -280,14 +291,14 @@ def loglik_at(kind, lengthscale, variance, t, y, mask, R, order=6):
     return kalman_filter(m, F, Q, y, mask, R)[4]
 
 
-def loglik_grad_fd(kind, lengthscale, variance, t, y, mask, R, h=1e-6, order=6):
+def loglik_grad_fd(kind, lengthscale, variance, t, y, mask, R, h=1e-6, order=6, threads=1):
     """Central finite differences of the oracle log-likelihood in
-    (log lengthscale, log variance, log noise), step h in each log parameter."""
+    (log lengthscale, log variance, log noise), step h in each log parameter
+    (the six evaluations in ``threads`` threads)."""
     base = np.log([lengthscale, variance])
     R = np.asarray(R, dtype=np.float64)
-    g = []
+    points = []
     for i in range(3):
-        vals = []
         for sgn in (1.0, -1.0):
             th = base.copy()
             Rp = R
@@ -295,9 +306,15 @@ def loglik_grad_fd(kind, lengthscale, variance, t, y, mask, R, h=1e-6, order=6):
                 th[i] += sgn * h
             else:
                 Rp = R * math.exp(sgn * h)
-            vals.append(loglik_at(kind, math.exp(th[0]), math.exp(th[1]), t, y, mask, Rp, order=order))
-        g.append((vals[0] - vals[1]) / (2.0 * h))
-    return np.array(g)
+            points.append((math.exp(th[0]), math.exp(th[1]), Rp))
+    run = lambda p: loglik_at(kind, p[0], p[1], t, y, mask, p[2], order=order)
+    if threads > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(threads) as ex:
+            vals = list(ex.map(run, points))
+    else:
+        vals = [run(p) for p in points]
+    return np.array([(vals[2 * i] - vals[2 * i + 1]) / (2.0 * h) for i in range(3)])
 
 
 # ---------------------------------------------------------------------------

@@ -716,17 +716,21 @@ int orc_discretize_tangent(int d, const double *G_, const double *W_, const doub
  *   m = m^- + K v             dm = dm^- + dK v + K dv
  *   P = P^- - K S K^T         dP = dP^- - dK S K^T - K dS K^T - K S dK^T
  *   l += -1/2 [log(2 pi S) + v^2 / S]
- *                             dl += -1/2 [dS / S + 2 v dv / S - v^2 dS / S^2] */
+ *                             dl += -1/2 [dS / S + 2 v dv / S - v^2 dS / S^2]
+ * dloglik_abs (nullable) receives the sum of the absolute values of the
+ * per-step terms of dl: the scale against which the rounding of any order of
+ * summing those terms is measured (a gradient near 0 is a cancellation). */
 int orc_loglik_tangent(int d, const double *H_, const double *R, const double *dR, int R_per_step,
                        const double *F_, const double *Q_, const double *dF_, const double *dQ_,
-                       const double *y, const unsigned char *mask, long n, double *loglik, double *dloglik) {
+                       const double *y, const unsigned char *mask, long n, double *loglik, double *dloglik,
+                       double *dloglik_abs) {
   if (d < 1 || d > DMAX || n < 1) return 3;
   const real twopi = 6.283185307179586476925286766559L;
   int dd = d * d;
   real H[DMAX];
   load(1, d, H_, H);
   real m[DMAX] = {0}, P[DMAX * DMAX] = {0}, dm[DMAX] = {0}, dP[DMAX * DMAX] = {0};
-  real ll = 0.0L, dll = 0.0L;
+  real ll = 0.0L, dll = 0.0L, dabs = 0.0L;
   for (long k = 0; k < n; ++k) {
     real F[DMAX * DMAX], Q[DMAX * DMAX], dF[DMAX * DMAX], dQ[DMAX * DMAX], Ft[DMAX * DMAX], dFt[DMAX * DMAX];
     load(d, d, F_ + k * dd, F); load(d, d, Q_ + k * dd, Q);
@@ -778,7 +782,9 @@ int orc_loglik_tangent(int d, const double *H_, const double *R, const double *d
       symmetrize(d, P);
       symmetrize(d, dP);
       ll += -0.5L * (logl(twopi * S) + v * v / S);
-      dll += -0.5L * (dS / S + 2.0L * v * dv / S - v * v * dS / (S * S));
+      const real dterm = -0.5L * (dS / S + 2.0L * v * dv / S - v * v * dS / (S * S));
+      dll += dterm;
+      dabs += fabsl(dterm);
     } else {
       memcpy(m, mp, sizeof(real) * d); memcpy(dm, dmp, sizeof(real) * d);
       memcpy(P, Pp, sizeof(real) * dd); memcpy(dP, dPp, sizeof(real) * dd);
@@ -786,6 +792,7 @@ int orc_loglik_tangent(int d, const double *H_, const double *R, const double *d
   }
   if (loglik) *loglik = (double)ll;
   if (dloglik) *dloglik = (double)dll;
+  if (dloglik_abs) *dloglik_abs = (double)dabs;
   return 0;
 }
 

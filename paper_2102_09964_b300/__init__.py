@@ -140,6 +140,19 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+# PSSGP_NAN_FILL=1: every output and workspace the binding allocates is filled
+# with 0xFF bytes (NaN for floating point, -1 for integers) before the call,
+# so that an entry the library should write but does not is visible.
+_NAN_FILL = os.environ.get("PSSGP_NAN_FILL", "0") not in ("", "0")
+
+
+def _empty(*size, dtype, device):
+    t = torch.empty(*size, dtype=dtype, device=device)
+    if _NAN_FILL and t.numel() > 0:
+        t.view(torch.uint8).fill_(0xFF)
+    return t
+
+
 @dataclass
 class Model:
     """A built state-space model (host struct handed to every call)."""
@@ -187,12 +200,12 @@ def workspace_size(d: int, n: int) -> int:
 def workspace(d: int, n: int, device="cuda", extra: int = 0) -> torch.Tensor:
     """A device workspace of the size the library asks for (torch allocations
     are 256-byte aligned)."""
-    return torch.empty(workspace_size(d, n) + int(extra), dtype=torch.uint8, device=device)
+    return _empty(workspace_size(d, n) + int(extra), dtype=torch.uint8, device=device)
 
 
 def workspace_grad(d: int, n: int, device="cuda") -> torch.Tensor:
     """A device workspace for the gradient entry points."""
-    return torch.empty(int(lib().pssgp_workspace_size_grad(int(d), int(n))), dtype=torch.uint8, device=device)
+    return _empty(int(lib().pssgp_workspace_size_grad(int(d), int(n))), dtype=torch.uint8, device=device)
 
 
 def status(ws: torch.Tensor) -> int:
@@ -210,11 +223,11 @@ def merge(t_train, y_train, t_test, ws=None):
     dev = t_train.device
     N, M = t_train.numel(), t_test.numel()
     n = N + M
-    t = torch.empty(n, dtype=torch.float64, device=dev)
-    y = torch.empty(n, dtype=torch.float64, device=dev)
-    mask = torch.empty(n, dtype=torch.uint8, device=dev)
-    tpos = torch.empty(max(M, 1), dtype=torch.int64, device=dev)
-    ws = ws if ws is not None else torch.empty(256, dtype=torch.uint8, device=dev)
+    t = _empty(n, dtype=torch.float64, device=dev)
+    y = _empty(n, dtype=torch.float64, device=dev)
+    mask = _empty(n, dtype=torch.uint8, device=dev)
+    tpos = _empty(max(M, 1), dtype=torch.int64, device=dev)
+    ws = ws if ws is not None else _empty(256, dtype=torch.uint8, device=dev)
     rc = lib().pssgp_merge(_ptr(t_train), _ptr(y_train), N, _ptr(t_test), M, _ptr(t), _ptr(y), _ptr(mask),
                            _ptr(tpos), _ptr(ws), ws.numel(), _stream())
     _check(rc, "pssgp_merge")
@@ -224,9 +237,9 @@ def merge(t_train, y_train, t_test, ws=None):
 def discretize(model: Model, t, ws=None):
     """F (d*d x n, entry-major) and Q (packed x n)."""
     d, n = model.d, t.numel()
-    F = torch.empty(d * d, n, dtype=torch.float64, device=t.device)
-    Q = torch.empty(d * (d + 1) // 2, n, dtype=torch.float64, device=t.device)
-    ws = ws if ws is not None else torch.empty(256, dtype=torch.uint8, device=t.device)
+    F = _empty(d * d, n, dtype=torch.float64, device=t.device)
+    Q = _empty(d * (d + 1) // 2, n, dtype=torch.float64, device=t.device)
+    ws = ws if ws is not None else _empty(256, dtype=torch.uint8, device=t.device)
     rc = lib().pssgp_discretize(ctypes.byref(model.raw), _ptr(t), n, _ptr(F), _ptr(Q), n, _ptr(ws), ws.numel(),
                                 _stream())
     _check(rc, "pssgp_discretize")
@@ -240,9 +253,9 @@ def filter(model: Model, t, y, mask, R, ws=None, outputs=True, loglik=True):
     R = _f64(R, dev).reshape(-1)
     per = 1 if R.numel() == n and n > 1 else 0
     ws = ws if ws is not None else workspace(d, n, dev)
-    xf = torch.empty(d, n, dtype=torch.float64, device=dev) if outputs else None
-    Pf = torch.empty(d * (d + 1) // 2, n, dtype=torch.float64, device=dev) if outputs else None
-    ll = torch.empty(1, dtype=torch.float64, device=dev) if loglik else None
+    xf = _empty(d, n, dtype=torch.float64, device=dev) if outputs else None
+    Pf = _empty(d * (d + 1) // 2, n, dtype=torch.float64, device=dev) if outputs else None
+    ll = _empty(1, dtype=torch.float64, device=dev) if loglik else None
     rc = lib().pssgp_filter(ctypes.byref(model.raw), _ptr(t), _ptr(y), _ptr(mask), _ptr(R), per, n, _ptr(xf),
                             _ptr(Pf), n, _ptr(ll), _ptr(ws), ws.numel(), _stream())
     _check(rc, "pssgp_filter")
@@ -254,10 +267,10 @@ def smooth(model: Model, t, xf, Pf, ws=None, states=False):
     d, n = model.d, t.numel()
     dev = t.device
     ws = ws if ws is not None else workspace(d, n, dev)
-    fm = torch.empty(n, dtype=torch.float64, device=dev)
-    fv = torch.empty(n, dtype=torch.float64, device=dev)
-    xs = torch.empty(d, n, dtype=torch.float64, device=dev) if states else None
-    Ps = torch.empty(d * (d + 1) // 2, n, dtype=torch.float64, device=dev) if states else None
+    fm = _empty(n, dtype=torch.float64, device=dev)
+    fv = _empty(n, dtype=torch.float64, device=dev)
+    xs = _empty(d, n, dtype=torch.float64, device=dev) if states else None
+    Ps = _empty(d * (d + 1) // 2, n, dtype=torch.float64, device=dev) if states else None
     rc = lib().pssgp_smooth(ctypes.byref(model.raw), _ptr(t), _ptr(xf), _ptr(Pf), n, n, _ptr(fm), _ptr(fv),
                             _ptr(xs), _ptr(Ps), _ptr(ws), ws.numel(), _stream())
     _check(rc, "pssgp_smooth")
@@ -270,7 +283,7 @@ def loglik(model: Model, t, y, mask, R, ws=None):
     R = _f64(R, dev).reshape(-1)
     per = 1 if R.numel() == n and n > 1 else 0
     ws = ws if ws is not None else workspace(d, n, dev)
-    ll = torch.empty(1, dtype=torch.float64, device=dev)
+    ll = _empty(1, dtype=torch.float64, device=dev)
     rc = lib().pssgp_loglik(ctypes.byref(model.raw), _ptr(t), _ptr(y), _ptr(mask), _ptr(R), per, n, _ptr(ll),
                             _ptr(ws), ws.numel(), _stream())
     _check(rc, "pssgp_loglik")
@@ -291,7 +304,7 @@ def loglik_batched(model: Model, offsets, params, t, y, mask, ws=None, out=None)
     if params.numel() != 3 * B:
         raise ValueError("params must hold 3 values per series")
     ws = ws if ws is not None else workspace(d, n, dev)
-    ll = out if out is not None else torch.empty(B, dtype=torch.float64, device=dev)
+    ll = out if out is not None else _empty(B, dtype=torch.float64, device=dev)
     rc = lib().pssgp_loglik_batched(ctypes.byref(model.raw), _ptr(offsets), B, _ptr(params), _ptr(t), _ptr(y),
                                     _ptr(mask), n, _ptr(ll), _ptr(ws), ws.numel(), _stream())
     _check(rc, "pssgp_loglik_batched")
@@ -308,8 +321,8 @@ def loglik_grad(model: Model, t, y, mask, R, ws=None):
     R = _f64(R, dev).reshape(-1)
     per = 1 if R.numel() == n and n > 1 else 0
     ws = ws if ws is not None else workspace_grad(d, n, dev)
-    ll = torch.empty(1, dtype=torch.float64, device=dev)
-    g = torch.empty(3, dtype=torch.float64, device=dev)
+    ll = _empty(1, dtype=torch.float64, device=dev)
+    g = _empty(3, dtype=torch.float64, device=dev)
     rc = lib().pssgp_loglik_grad(ctypes.byref(model.raw), _ptr(t), _ptr(y), _ptr(mask), _ptr(R), per, n, _ptr(ll),
                                  _ptr(g), _ptr(ws), ws.numel(), _stream())
     _check(rc, "pssgp_loglik_grad")
@@ -330,7 +343,7 @@ def loglik_grad_batched(model: Model, offsets, params, t, y, mask, ws=None, out=
         raise ValueError("params must hold 3 values per series")
     ws = ws if ws is not None else workspace_grad(d, n, dev)
     if out is None:
-        out = (torch.empty(B, dtype=torch.float64, device=dev), torch.empty(B, 3, dtype=torch.float64, device=dev))
+        out = (_empty(B, dtype=torch.float64, device=dev), _empty(B, 3, dtype=torch.float64, device=dev))
     ll, g = out
     rc = lib().pssgp_loglik_grad_batched(ctypes.byref(model.raw), _ptr(offsets), B, _ptr(params), _ptr(t), _ptr(y),
                                          _ptr(mask), n, _ptr(ll), _ptr(g), _ptr(ws), ws.numel(), _stream())
@@ -360,10 +373,10 @@ def fit_batched(model: Model, offsets, t, y, mask, theta0, max_iter=2000, patien
     n = t.numel()
     dev = t.device
     theta = _f64(theta0, dev).reshape(B, 3).clone()
-    ll = torch.empty(B, dtype=torch.float64, device=dev)
-    it = torch.empty(B, dtype=torch.int32, device=dev)
+    ll = _empty(B, dtype=torch.float64, device=dev)
+    it = _empty(B, dtype=torch.int32, device=dev)
     if ws is None:
-        ws = torch.empty(int(lib().pssgp_fit_workspace_size(model.d, n, B)), dtype=torch.uint8, device=dev)
+        ws = _empty(int(lib().pssgp_fit_workspace_size(model.d, n, B)), dtype=torch.uint8, device=dev)
     o = FitOptions(int(max_iter), int(patience), float(tol), float(lr), float(beta1), float(beta2), float(eps),
                    int(check_every), {"adam": FIT_ADAM, "lbfgs": FIT_LBFGS}[method])
     nrun = ctypes.c_int32(0)
@@ -406,8 +419,8 @@ def predict(model: Model, t_train, y_train, t_test, R: float, ws=None, out=None,
     dev = t_train.device
     ws = ws if ws is not None else workspace(model.d, N + M, dev)
     if out is None:
-        out = (torch.empty(M, dtype=torch.float64, device=dev), torch.empty(M, dtype=torch.float64, device=dev),
-               torch.empty(1, dtype=torch.float64, device=dev))
+        out = (_empty(M, dtype=torch.float64, device=dev), _empty(M, dtype=torch.float64, device=dev),
+               _empty(1, dtype=torch.float64, device=dev))
     mean, var, ll = out
     rc = lib().pssgp_predict(ctypes.byref(model.raw), _ptr(t_train), _ptr(y_train), N, _ptr(t_test), M, float(R),
                              _ptr(mean), _ptr(var), _ptr(ll) if with_loglik else None, _ptr(ws), ws.numel(),
@@ -422,7 +435,7 @@ def predict_host(model: Model, t_train, y_train, t_test, R: float, out, ws=None,
     `stream` (default: the current stream); returns the workspace."""
     N, M = t_train.numel(), t_test.numel()
     if ws is None:
-        ws = torch.empty(int(lib().pssgp_predict_host_workspace_size(model.d, N, M)), dtype=torch.uint8,
+        ws = _empty(int(lib().pssgp_predict_host_workspace_size(model.d, N, M)), dtype=torch.uint8,
                          device="cuda")
     st = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
     mean, var, ll = out
@@ -525,7 +538,7 @@ def autotune_loglik_batched(model: Model, offsets, params, t, y, mask, ws=None, 
             tune_set(d, int(table[key]["warps_per_sm"]))
             return int(table[key]["warps_per_sm"]), None
     ws = ws if ws is not None else workspace(d, n, t.device)
-    ll = out if out is not None else torch.empty(B, dtype=torch.float64, device=t.device)
+    ll = out if out is not None else _empty(B, dtype=torch.float64, device=t.device)
     params = _f64(params, t.device).reshape(-1)
     w = ctypes.c_int32(0)
     ms = ctypes.c_float(0.0)
@@ -601,8 +614,8 @@ def simulate_prior(model: Model, offsets, params, seed: int, spacing: float = 0.
     B = offsets.numel() - 1
     n = int(offsets[-1].item())
     params = _f64(params, dev).reshape(-1)
-    t = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
-    y = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+    t = _empty(max(n, 1), dtype=torch.float64, device=dev)
+    y = _empty(max(n, 1), dtype=torch.float64, device=dev)
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     rc = lib().pssgp_simulate_prior(ctypes.byref(model.raw), _ptr(offsets), B, _ptr(params), int(seed),
                                     float(spacing), _ptr(t), _ptr(y), _ptr(st), _stream())
@@ -613,7 +626,7 @@ def simulate_prior(model: Model, offsets, params, seed: int, spacing: float = 0.
 def features(offsets, t, y, out=None):
     """The 65 log-periodogram features of every series (device float32[B, 65])."""
     B = offsets.numel() - 1
-    f = out if out is not None else torch.empty(B, NFEAT, dtype=torch.float32, device=t.device)
+    f = out if out is not None else _empty(B, NFEAT, dtype=torch.float32, device=t.device)
     _check(lib().pssgp_features(_ptr(offsets), B, _ptr(t), _ptr(y), _ptr(f), _stream()), "pssgp_features")
     return f
 
@@ -630,7 +643,7 @@ class MLP:
 
     def ws(self, rows: int):
         if rows not in self._ws:
-            self._ws[rows] = torch.empty(int(lib().pssgp_mlp_workspace_size(int(rows))), dtype=torch.uint8,
+            self._ws[rows] = _empty(int(lib().pssgp_mlp_workspace_size(int(rows))), dtype=torch.uint8,
                                          device=self.device)
         return self._ws[rows]
 
@@ -648,8 +661,8 @@ class MLP:
 
     def grad(self, feat, theta, grad=None, loss=None, out=None):
         rows = feat.shape[0]
-        g = grad if grad is not None else torch.empty(self.nparam, dtype=torch.float32, device=self.device)
-        ls = loss if loss is not None else torch.empty(1, dtype=torch.float32, device=self.device)
+        g = grad if grad is not None else _empty(self.nparam, dtype=torch.float32, device=self.device)
+        ls = loss if loss is not None else _empty(1, dtype=torch.float32, device=self.device)
         ws = self.ws(rows)
         _check(lib().pssgp_mlp_grad(_ptr(self.state), _ptr(feat), _ptr(theta), rows, _ptr(g), _ptr(ls), _ptr(out),
                                     _ptr(ws), ws.numel(), _stream()), "pssgp_mlp_grad")
@@ -665,8 +678,8 @@ class MLP:
         from lr to lr_final.  Returns the loss of every step (device)."""
         rows = feat.shape[0]
         nb = rows // batch
-        g = torch.empty(self.nparam, dtype=torch.float32, device=self.device)
-        losses = torch.empty(max(epochs * nb, 1), dtype=torch.float32, device=self.device)
+        g = _empty(self.nparam, dtype=torch.float32, device=self.device)
+        losses = _empty(max(epochs * nb, 1), dtype=torch.float32, device=self.device)
         total = epochs * nb
         for e in range(epochs):
             for b in range(nb):
@@ -678,7 +691,7 @@ class MLP:
 
     def predict(self, feat):
         rows = feat.shape[0]
-        th = torch.empty(rows, 3, dtype=torch.float64, device=self.device)
+        th = _empty(rows, 3, dtype=torch.float64, device=self.device)
         ws = self.ws(rows)
         _check(lib().pssgp_mlp_predict(_ptr(self.state), _ptr(feat), rows, _ptr(th), _ptr(ws), ws.numel(),
                                        _stream()), "pssgp_mlp_predict")

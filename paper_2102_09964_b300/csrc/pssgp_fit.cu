@@ -265,7 +265,7 @@ __global__ void k_fit_lbfgs(int Ba, const int* idx, const int64_t* ooff, const d
 }  // namespace
 
 extern "C" size_t pssgp_fit_workspace_size(int32_t d, int64_t n, int32_t B) {
-  if (d < 1 || d > PSSGP_DMAX || n < 1 || B < 1) return 0;
+  if (d < 1 || d > PSSGP_DMAX || n < 1 || n > PSSGP_NMAX || B < 1) return 0;
   return (size_t)fit_layout(d, n, B).total;
 }
 
@@ -273,7 +273,7 @@ extern "C" int pssgp_fit_batched(const pssgp_model* model, const int64_t* offset
                                  const double* y, const uint8_t* mask, int64_t n, double* theta, double* loglik,
                                  int32_t* iters, const pssgp_fit_options* opt, void* ws, size_t ws_bytes,
                                  void* stream, int32_t* iterations_run) {
-  if (!model || !offsets_host || !t || !y || !mask || !theta || !loglik || !iters || !opt || !ws || B < 1 || n < 1)
+  if (!model || !offsets_host || !t || !y || !mask || !theta || !loglik || !iters || !opt || !ws || B < 1 || n < 1 || n > PSSGP_NMAX)
     return PSSGP_EINVAL;
   if (opt->max_iter < 1 || opt->patience < 1 || opt->check_every < 1 || !(opt->lr > 0.0) || !(opt->tol >= 0.0) ||
       (opt->method != PSSGP_FIT_ADAM && opt->method != PSSGP_FIT_LBFGS))

@@ -1741,12 +1741,18 @@ __global__ void k_gather(const double* src_m, const double* src_v, const int64_t
 
 // FP64 FMA rate probe: four independent dependent chains per thread
 __global__ void k_dfma_probe(double* out, int iters) {
-  double a0 = threadIdx.x * 1e-3, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
+  double a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = threadIdx.x * 1e-3 + j;
   const double c = 0.999999, dd = 1e-9;
   for (int i = 0; i < iters; ++i) {
-    a0 = fma(a0, c, dd); a1 = fma(a1, c, dd); a2 = fma(a2, c, dd); a3 = fma(a3, c, dd);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = fma(a[j], c, dd);
   }
-  out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3;
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += a[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -1969,7 +1975,7 @@ int filter_common(const pssgp_model* model, const double* t, const double* y, co
                   int32_t R_per_step, int64_t n, double* xf, double* Pf, int64_t ld, double* loglik, void* ws,
                   size_t ws_bytes, void* stream, int64_t lanes, double* dbg) {
   begin_call();
-  if (!model_ok(model) || !t || !y || !mask || !R || n < 1) return PSSGP_EINVAL;
+  if (!model_ok(model) || !t || !y || !mask || !R || n < 1 || n > PSSGP_NMAX) return PSSGP_EINVAL;
   if ((xf || Pf) && ld < n) return PSSGP_EINVAL;
   const Plan p = make_plan(model->d, n, lanes);
   const int rc = check_ws(p, ws, ws_bytes);
@@ -2001,7 +2007,7 @@ int filter_common(const pssgp_model* model, const double* t, const double* y, co
 // C ABI
 // ===========================================================================
 extern "C" size_t pssgp_workspace_size(int32_t d, int64_t n) {
-  if (d < 1 || d > PSSGP_DMAX || n < 1) return 0;
+  if (d < 1 || d > PSSGP_DMAX || n < 1 || n > PSSGP_NMAX) return 0;
   return (size_t)make_plan(d, n, 0, WARPS_MAX).total;   // enough for every tuning
 }
 
@@ -2019,7 +2025,7 @@ extern "C" int pssgp_merge(const double* t_train, const double* y_train, int64_t
                            double* t, double* y, uint8_t* mask, int64_t* test_pos, void* ws, size_t ws_bytes,
                            void* stream) {
   begin_call();
-  if (!t_train || !y_train || !t || !y || !mask || N < 0 || M < 0 || N + M < 1) return PSSGP_EINVAL;
+  if (!t_train || !y_train || !t || !y || !mask || N < 0 || M < 0 || N + M < 1 || N > PSSGP_NMAX || M > PSSGP_NMAX) return PSSGP_EINVAL;
   if (M > 0 && (!t_test || !test_pos)) return PSSGP_EINVAL;
   int rc = check_small_ws(ws, ws_bytes);
   if (rc) return rc;
@@ -2036,7 +2042,7 @@ extern "C" int pssgp_merge(const double* t_train, const double* y_train, int64_t
 extern "C" int pssgp_discretize(const pssgp_model* model, const double* t, int64_t n, double* F, double* Q,
                                 int64_t ld, void* ws, size_t ws_bytes, void* stream) {
   begin_call();
-  if (!model_ok(model) || !t || !F || !Q || n < 1 || ld < n) return PSSGP_EINVAL;
+  if (!model_ok(model) || !t || !F || !Q || n < 1 || n > PSSGP_NMAX || ld < n) return PSSGP_EINVAL;
   int rc = check_small_ws(ws, ws_bytes);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -2065,7 +2071,7 @@ extern "C" int pssgp_loglik_batched(const pssgp_model* model, const int64_t* off
                                     const double* params, const double* t, const double* y, const uint8_t* mask,
                                     int64_t n, double* loglik, void* ws, size_t ws_bytes, void* stream) {
   begin_call();
-  if (!model_ok(model) || !offsets || !params || !t || !y || !mask || !loglik || B < 1 || n < 1)
+  if (!model_ok(model) || !offsets || !params || !t || !y || !mask || !loglik || B < 1 || n < 1 || n > PSSGP_NMAX)
     return PSSGP_EINVAL;
   const double ell0 = model->lengthscale, var0 = model->variance;
   if (!(ell0 > 0.0) || !(var0 > 0.0) || !std::isfinite(ell0) || !std::isfinite(var0)) return PSSGP_EMODEL;
@@ -2101,7 +2107,7 @@ extern "C" int pssgp_loglik_batched(const pssgp_model* model, const int64_t* off
 }
 
 extern "C" size_t pssgp_workspace_size_grad(int32_t d, int64_t n) {
-  if (d < 1 || d > PSSGP_DMAX || n < 1) return 0;
+  if (d < 1 || d > PSSGP_DMAX || n < 1 || n > PSSGP_NMAX) return 0;
   return (size_t)make_plan(d, n, 0, WARPS_MAX, true).total;
 }
 
@@ -2109,7 +2115,7 @@ extern "C" int pssgp_loglik_grad(const pssgp_model* model, const double* t, cons
                                  const double* R, int32_t R_per_step, int64_t n, double* loglik, double* grad,
                                  void* ws, size_t ws_bytes, void* stream) {
   begin_call();
-  if (!model_ok(model) || !t || !y || !mask || !R || !grad || n < 1) return PSSGP_EINVAL;
+  if (!model_ok(model) || !t || !y || !mask || !R || !grad || n < 1 || n > PSSGP_NMAX) return PSSGP_EINVAL;
   const Plan p = make_plan(model->d, n, 0, 0, true);
   const int rc = check_ws(p, ws, ws_bytes);
   if (rc) return rc;
@@ -2140,7 +2146,7 @@ extern "C" int pssgp_loglik_grad_batched(const pssgp_model* model, const int64_t
                                          const uint8_t* mask, int64_t n, double* loglik, double* grad, void* ws,
                                          size_t ws_bytes, void* stream) {
   begin_call();
-  if (!model_ok(model) || !offsets || !params || !t || !y || !mask || !grad || B < 1 || n < 1)
+  if (!model_ok(model) || !offsets || !params || !t || !y || !mask || !grad || B < 1 || n < 1 || n > PSSGP_NMAX)
     return PSSGP_EINVAL;
   const double ell0 = model->lengthscale, var0 = model->variance;
   if (!(ell0 > 0.0) || !(var0 > 0.0) || !std::isfinite(ell0) || !std::isfinite(var0)) return PSSGP_EMODEL;
@@ -2184,7 +2190,7 @@ extern "C" int pssgp_smooth(const pssgp_model* model, const double* t, const dou
                             int64_t ld, double* f_mean, double* f_var, double* xs, double* Ps, void* ws,
                             size_t ws_bytes, void* stream) {
   begin_call();
-  if (!model_ok(model) || !t || !xf || !Pf || n < 1 || ld < n) return PSSGP_EINVAL;
+  if (!model_ok(model) || !t || !xf || !Pf || n < 1 || n > PSSGP_NMAX || ld < n) return PSSGP_EINVAL;
   const Plan p = make_plan(model->d, n, 0);
   const int rc = check_ws(p, ws, ws_bytes);
   if (rc) return rc;
@@ -2222,7 +2228,7 @@ HostStage host_stage(int d, int64_t N, int64_t M) {
 }  // namespace
 
 extern "C" size_t pssgp_predict_host_workspace_size(int32_t d, int64_t N, int64_t M) {
-  if (d < 1 || d > PSSGP_DMAX || N < 1 || M < 0) return 0;
+  if (d < 1 || d > PSSGP_DMAX || N < 1 || M < 0 || N > PSSGP_NMAX || M > PSSGP_NMAX) return 0;
   return (size_t)host_stage(d, N, M).total;
 }
 
@@ -2233,7 +2239,7 @@ extern "C" int pssgp_predict(const pssgp_model* model, const double* t_train, co
 extern "C" int pssgp_predict_host(const pssgp_model* model, const double* t_train, const double* y_train, int64_t N,
                                   const double* t_test, int64_t M, double R, double* mean_test, double* var_test,
                                   double* loglik, void* ws, size_t ws_bytes, void* stream) {
-  if (!model_ok(model) || !t_train || !y_train || N < 1 || M < 0 || !ws) return PSSGP_EINVAL;
+  if (!model_ok(model) || !t_train || !y_train || N < 1 || M < 0 || N > PSSGP_NMAX || M > PSSGP_NMAX || !ws) return PSSGP_EINVAL;
   if (M > 0 && (!t_test || !mean_test || !var_test)) return PSSGP_EINVAL;
   const HostStage h = host_stage(model->d, N, M);
   if ((int64_t)ws_bytes < h.total || (reinterpret_cast<uintptr_t>(ws) & 255) != 0) return PSSGP_EWORKSPACE;
@@ -2263,7 +2269,7 @@ extern "C" int pssgp_predict(const pssgp_model* model, const double* t_train, co
                              const double* t_test, int64_t M, double R, double* mean_test, double* var_test,
                              double* loglik, void* ws, size_t ws_bytes, void* stream) {
   begin_call();
-  if (!model_ok(model) || !t_train || !y_train || N < 1 || M < 0) return PSSGP_EINVAL;
+  if (!model_ok(model) || !t_train || !y_train || N < 1 || M < 0 || N > PSSGP_NMAX || M > PSSGP_NMAX) return PSSGP_EINVAL;
   if (M > 0 && (!t_test || !mean_test || !var_test)) return PSSGP_EINVAL;
   if (!(R > 0.0) || !std::isfinite(R)) return PSSGP_EINVAL;
   const int64_t n = N + M;
@@ -2312,7 +2318,7 @@ extern "C" int pssgp_debug_filter_aggregates(const pssgp_model* model, const dou
                                              const uint8_t* mask, const double* R, int64_t n, int32_t lanes,
                                              double* agg, int64_t* first, int32_t* lanes_out, void* ws,
                                              size_t ws_bytes, void* stream) {
-  if (!model_ok(model) || !agg || !first || !lanes_out || n < 1) return PSSGP_EINVAL;
+  if (!model_ok(model) || !agg || !first || !lanes_out || n < 1 || n > PSSGP_NMAX) return PSSGP_EINVAL;
   if (lanes < 0 || lanes % BLOCK) return PSSGP_EINVAL;
   const Plan p = make_plan(model->d, n, lanes);
   int rc = check_ws(p, ws, ws_bytes);
@@ -2357,26 +2363,39 @@ extern "C" int pssgp_debug_filter_aggregates(const pssgp_model* model, const dou
   return PSSGP_OK;
 }
 
+// Best of three timed launches (after one warm-up) at each of 4, 8 and 16
+// warps per SM: eight independent FMA chains per thread keep the pipe fed at
+// every occupancy, and the fastest launch is the rate the FP64 pipe sustains.
 extern "C" int pssgp_fp64_fma_rate(double* fma_per_s) {
   if (!fma_per_s) return PSSGP_EINVAL;
-  const int blocks = num_sms() * 2, threads = 256, iters = 1 << 14;
+  const int sms = num_sms(), iters = 1 << 13, threads = 128;
+  const int max_blocks = sms * 4;
   double* out = nullptr;
-  if (cudaMalloc(&out, sizeof(double) * blocks * threads) != cudaSuccess) return PSSGP_ECUDA;
+  if (cudaMalloc(&out, sizeof(double) * max_blocks * threads) != cudaSuccess) return PSSGP_ECUDA;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  k_dfma_probe<<<blocks, threads>>>(out, iters);
-  cudaEventRecord(e0);
-  k_dfma_probe<<<blocks, threads>>>(out, iters);
-  cudaEventRecord(e1);
-  const cudaError_t e = cudaEventSynchronize(e1);
-  float ms = 0.0f;
-  cudaEventElapsedTime(&ms, e0, e1);
+  double best = 0.0;
+  cudaError_t e = cudaSuccess;
+  for (int bps = 1; bps <= 4 && e == cudaSuccess; bps *= 2) {
+    const int blocks = sms * bps;
+    k_dfma_probe<<<blocks, threads>>>(out, iters);
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      cudaEventRecord(e0);
+      k_dfma_probe<<<blocks, threads>>>(out, iters * (4 / bps));
+      cudaEventRecord(e1);
+      e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms > 0.0f)
+        best = std::max(best, (double)blocks * threads * (double)iters * (4 / bps) * 8 / (ms * 1e-3));
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(out);
-  if (e != cudaSuccess || ms <= 0.0f) return PSSGP_ECUDA;
-  *fma_per_s = (double)blocks * threads * iters * 4 / (ms * 1e-3);
+  if (e != cudaSuccess || best <= 0.0) return PSSGP_ECUDA;
+  *fma_per_s = best;
   return PSSGP_OK;
 }
 
@@ -2427,29 +2446,23 @@ extern "C" const char* pssgp_timing_name(int32_t slot) {
 // ===========================================================================
 namespace {
 constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;   // 32 MiB per device, held until exit
-constexpr int kMaxDevices = 64;
-void* g_noalloc_ptr[kMaxDevices] = {};
-std::mutex g_noalloc_mu;
 }  // namespace
 
 // The scratch itself.  Host code must not use this name as a device address
-// (on the host it is only a stand-in); its device address is looked up once
-// per device with cudaGetSymbolAddress below.
+// (on the host it is only a stand-in); its device address is looked up with
+// cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 namespace {
-// Device address of the scratch on the current device (looked up on the
-// first call per device, with that device current).
+// Device address of the scratch in the current device's context, looked up
+// on every call with that device current (a cheap host call once the module
+// is loaded; the first call on a device loads it).  Not cached, so a context
+// that was torn down and created again (cudaDeviceReset) cannot leave a stale
+// address behind.
 int noalloc_scratch(void** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PSSGP_ECUDA;
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return PSSGP_ECUDA;
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return PSSGP_ECUDA;
+  *out = p;
   return PSSGP_OK;
 }
 }  // namespace
@@ -2457,7 +2470,12 @@ int noalloc_scratch(void** out) {
 extern "C" int pssgp_loglik_noalloc(const pssgp_model* model, const double* t, const double* y, const uint8_t* mask,
                                     const double* R, int32_t R_per_step, int64_t n, double* loglik,
                                     int32_t* status, void* stream) {
-  if (!model_ok(model) || !t || !y || !mask || !R || !loglik || n < 1) return PSSGP_EINVAL;
+  if (!model_ok(model) || !t || !y || !mask || !R || !loglik || n < 1 || n > PSSGP_NMAX) return PSSGP_EINVAL;
+  {
+    // the timing diagnostic creates CUDA events around every launch
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_timing) return PSSGP_EINVAL;
+  }
   if ((size_t)make_plan(model->d, n, 0).total > kNoAllocScratchBytes) return PSSGP_ESCRATCH;
   void* ws = nullptr;
   int rc = noalloc_scratch(&ws);

@@ -13,7 +13,7 @@ import time
 import numpy as np
 import torch
 
-from . import MLP, NFEAT, features, fit_batched, simulate_prior
+from . import MLP, NFEAT, _empty, features, fit_batched, simulate_prior
 
 
 def prior_features(model, offsets: np.ndarray, params: np.ndarray, seed: int, chunk: int = 65_536,
@@ -22,7 +22,7 @@ def prior_features(model, offsets: np.ndarray, params: np.ndarray, seed: int, ch
     prior, simulated `chunk` series at a time (chunk c uses key seed + c, so
     the chunks draw independent numbers); the series themselves are not kept."""
     B = offsets.size - 1
-    feat = torch.empty(B, NFEAT, dtype=torch.float32, device=device)
+    feat = _empty(B, NFEAT, dtype=torch.float32, device=device)
     for c, a in enumerate(range(0, B, chunk)):
         b = min(a + chunk, B)
         off = torch.as_tensor(offsets[a:b + 1] - offsets[a], dtype=torch.int64, device=device)

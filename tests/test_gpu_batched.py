@@ -208,7 +208,7 @@ def test_graph_replay_with_new_parameters():
         d = dict(m=m, sub=sub, off=dev(sub.offsets, torch.int64), par=dev(sub.params()), t=dev(sub.t),
                  y=dev(sub.y), mask=dev(np.ones(sub.t.size, np.uint8), torch.uint8))
         d["ws"] = P.workspace(m.d, sub.t.size, torch.device("cuda"))
-        d["ll"] = torch.empty(sub.B, dtype=torch.float64, device="cuda")
+        d["ll"] = torch.full((sub.B,), float("nan"), dtype=torch.float64, device="cuda")
         P.loglik_batched(d["m"], d["off"], d["par"], d["t"], d["y"], d["mask"], ws=d["ws"], out=d["ll"])  # warm-up
         parts.append((kind, d))
     torch.cuda.synchronize()

@@ -1,11 +1,19 @@
 """GPU parity of the adjoint gradient of the log marginal likelihood with
 respect to (log lengthscale, log variance, log noise variance) against the
-oracle's forward-mode gradient (and, at the full 2^20-step size, against
+oracle's forward-mode gradient (and, at the full 2^20-step size, also against
 central differences of the oracle's log-likelihood).
 
-Tolerance semantics: |dg| <= tol * max(|g|, n_obs) per component, tol 1e-9
-for Matern kernels and 1e-6 for the order-6 RBF Taylor model (the same
-scale as the log-likelihood's own tolerance: both are sums of n_obs terms).
+Tolerance semantics, per component i: relative error
+    |g_i - ref_i| / max(|ref_i|, s_i / sqrt(n_obs)) <= tol,
+tol 1e-8 for Matern kernels and 1e-6 for the order-6 RBF Taylor model.
+s_i is the sum over steps of |per-step term| of the forward-mode derivative
+(the oracle returns it): a component is a sum of n_obs such terms, and
+s_i / sqrt(n_obs) is the size of a sum of n_obs terms of that magnitude with
+random signs.  A component below it (near an optimum, where the terms cancel)
+is judged against that scale instead of its own value.  Against central
+differences (h = 1e-6): |g_i - fd_i| <= 1e-5 |fd_i| + 4 eps |loglik| / h, the
+second term the rounding of the two log-likelihood values the difference
+divides by 2h.
 """
 import numpy as np
 import pytest
@@ -13,11 +21,14 @@ import torch
 
 import oracle
 import paper_2102_09964_b300 as P
+from oracle import model as om
 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"matern12": 1e-9, "matern32": 1e-9, "matern52": 1e-9, "rbf": 1e-6}
+TOL = {"matern12": 1e-8, "matern32": 1e-8, "matern52": 1e-8, "rbf": 1e-6}
+# the log-likelihood itself: |d loglik| <= tol * max(|loglik|, n_obs) (reading r13)
+LLTOL = {"matern12": 1e-9, "matern32": 1e-9, "matern52": 1e-9, "rbf": 1e-6}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -34,10 +45,28 @@ def dev(x, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
 
 
-def check_grad(g, ref, nobs, tol, what=""):
-    err = np.max(np.abs(np.asarray(g) - ref) / np.maximum(np.abs(ref), max(nobs, 1)))
-    assert err <= tol, (what, g, ref, err)
+@pytest.fixture(autouse=True)
+def _rep(report):
+    global REPORT
+    REPORT = report
+
+
+REPORT = None
+
+
+def check_grad(g, ref, scale, nobs, tol, what=""):
+    """Relative error per component, floored at scale / sqrt(n_obs)."""
+    g = np.asarray(g, dtype=np.float64)
+    floor = np.asarray(scale) / np.sqrt(max(nobs, 1))
+    err = np.max(np.abs(g - ref) / np.maximum(np.maximum(np.abs(ref), floor), 1e-300))
+    if REPORT is not None:
+        REPORT(f"gradient vs forward mode, {what[0] if isinstance(what, tuple) else what}".split("/")[0], err, tol)
+    assert err <= tol, (what, g, ref, scale, err)
     return err
+
+
+def fwd(kind, ell, s2, t, y, mask, R):
+    return oracle.loglik_grad_fwd(kind, ell, s2, t, y, mask, R, with_scale=True)
 
 
 def gpu_grad(kind, ell, s2, t, y, mask, R):
@@ -55,10 +84,10 @@ def test_grad_matches_forward_mode(kind, n):
     mask = (rng.uniform(size=n) > 0.1).astype(np.uint8)
     ll, g, st = gpu_grad(kind, 0.7, 1.3, t, y, mask, 0.02)
     assert st == 0
-    rll, rg = oracle.loglik_grad_fwd(kind, 0.7, 1.3, t, y, mask, 0.02)
+    rll, rg, sc = fwd(kind, 0.7, 1.3, t, y, mask, 0.02)
     nobs = int(mask.sum())
-    assert abs(ll - rll) <= TOL[kind] * max(abs(rll), nobs, 1)
-    check_grad(g, rg, nobs, TOL[kind], f"{kind}/{n}")
+    assert abs(ll - rll) <= LLTOL[kind] * max(abs(rll), nobs, 1)
+    check_grad(g, rg, sc, nobs, TOL[kind], f"{kind}/{n}")
 
 
 @pytest.mark.parametrize("kind", ["matern32", "matern52", "rbf"])
@@ -72,8 +101,8 @@ def test_grad_long_gaps_ties_missing_runs(kind):
     mask[3000:3500] = 0                     # a run of missing steps
     ll, g, st = gpu_grad(kind, 1.1, 0.9, t, y, mask, 0.05)
     assert st == 0
-    rll, rg = oracle.loglik_grad_fwd(kind, 1.1, 0.9, t, y, mask, 0.05)
-    check_grad(g, rg, int(mask.sum()), TOL[kind], kind)
+    rll, rg, sc = fwd(kind, 1.1, 0.9, t, y, mask, 0.05)
+    check_grad(g, rg, sc, int(mask.sum()), TOL[kind], kind)
 
 
 def test_grad_per_step_noise():
@@ -83,8 +112,8 @@ def test_grad_per_step_noise():
     m = P.build_model("matern52", 0.8, 1.0)
     ll, g, ws = P.loglik_grad(m, dev(s.t_train), dev(s.y_train), dev(mask, torch.uint8), dev(R))
     assert P.status(ws) == 0
-    rll, rg = oracle.loglik_grad_fwd("matern52", 0.8, 1.0, s.t_train, s.y_train, mask, R)
-    check_grad(g.cpu().numpy(), rg, 5000, 1e-9)
+    rll, rg, sc = fwd("matern52", 0.8, 1.0, s.t_train, s.y_train, mask, R)
+    check_grad(g.cpu().numpy(), rg, sc, 5000, TOL["matern52"], "matern52 per-step noise")
 
 
 def test_grad_all_missing_is_zero():
@@ -107,10 +136,10 @@ def test_batched_grad_matches_forward_mode(kind):
         if b == a:
             assert ll[s] == 0.0 and np.all(g[s] == 0.0)
             continue
-        rll, rg = oracle.loglik_grad_fwd(kind, bt.lengthscale[s], bt.variance[s], bt.t[a:b], bt.y[a:b],
-                                         mask[a:b], bt.noise[s])
-        assert abs(ll[s] - rll) <= TOL[kind] * max(abs(rll), b - a)
-        check_grad(g[s], rg, b - a, TOL[kind], (kind, s))
+        rll, rg, sc = fwd(kind, bt.lengthscale[s], bt.variance[s], bt.t[a:b], bt.y[a:b], mask[a:b],
+                          bt.noise[s])
+        assert abs(ll[s] - rll) <= LLTOL[kind] * max(abs(rll), b - a)
+        check_grad(g[s], rg, sc, b - a, TOL[kind], (f"{kind} batched", s))
 
 
 @pytest.mark.parametrize("kind", ["matern32", "matern52"])
@@ -130,10 +159,10 @@ def test_batched_grad_short_series_at_and_inside_chunk_starts(kind):
     for s in rng.choice(bt.B, 400, replace=False):
         a, b = bt.offsets[s], bt.offsets[s + 1]
         nobs = max(int(mask[a:b].sum()), 1)
-        rll, rg = oracle.loglik_grad_fwd(kind, bt.lengthscale[s], bt.variance[s], bt.t[a:b], bt.y[a:b],
-                                         mask[a:b], bt.noise[s])
-        assert abs(ll[s] - rll) <= TOL[kind] * max(abs(rll), nobs)
-        check_grad(g[s], rg, nobs, TOL[kind], (kind, s))
+        rll, rg, sc = fwd(kind, bt.lengthscale[s], bt.variance[s], bt.t[a:b], bt.y[a:b], mask[a:b],
+                          bt.noise[s])
+        assert abs(ll[s] - rll) <= LLTOL[kind] * max(abs(rll), nobs)
+        check_grad(g[s], rg, sc, nobs, TOL[kind], (f"{kind} batched short series", s))
 
 
 @pytest.mark.parametrize("kind", ["matern32", "matern52", "rbf"])
@@ -145,9 +174,9 @@ def test_grad_tiny_noise(kind, R):
     mask = np.ones(s.N, np.uint8)
     ll, g, st = gpu_grad(kind, 1.0, 1.0, s.t_train, s.y_train, mask, R)
     assert st == 0
-    rll, rg = oracle.loglik_grad_fwd(kind, 1.0, 1.0, s.t_train, s.y_train, mask, R)
-    assert abs(ll - rll) <= TOL[kind] * max(abs(rll), s.N)
-    check_grad(g, rg, s.N, TOL[kind], (kind, R))
+    rll, rg, sc = fwd(kind, 1.0, 1.0, s.t_train, s.y_train, mask, R)
+    assert abs(ll - rll) <= LLTOL[kind] * max(abs(rll), s.N)
+    check_grad(g, rg, sc, s.N, TOL[kind], (f"{kind} tiny noise", R))
 
 
 def test_batched_grad_full_size_sampled():
@@ -170,21 +199,38 @@ def test_batched_grad_full_size_sampled():
         pick = sorted({int(np.argmin(sl)), int(np.argmax(sl)), *rng.choice(idx.size, 2, replace=False).tolist()})
         for s in pick:
             a, b = sub.offsets[s], sub.offsets[s + 1]
-            rll, rg = oracle.loglik_grad_fwd(kind, sub.lengthscale[s], 1.0, sub.t[a:b], sub.y[a:b],
-                                             np.ones(b - a, np.uint8), sub.noise[s])
-            check_grad(g[s], rg, b - a, TOL[kind], (kind, s))
+            rll, rg, sc = fwd(kind, sub.lengthscale[s], 1.0, sub.t[a:b], sub.y[a:b], np.ones(b - a, np.uint8),
+                              sub.noise[s])
+            check_grad(g[s], rg, sc, b - a, TOL[kind], (f"{kind} 4096-series batch", s))
 
 
-def test_grad_full_size_rbf_vs_central_differences():
+def test_grad_full_size_rbf_vs_forward_mode_and_central_differences(report):
     """RBF-6 on the 2^20 training points, in the launch configuration of the
-    benchmark, against central differences (h = 1e-6) of the oracle."""
+    benchmark, against the oracle's forward mode (relative 1e-6) and central
+    differences (h = 1e-6) of its log-likelihood (relative 1e-5 plus the
+    differences' rounding)."""
+    from concurrent.futures import ThreadPoolExecutor
     s = wl.sinusoid_large()
     t, y = s.t_train, s.y_train
     mask = np.ones(t.size, np.uint8)
     ll, g, st = gpu_grad("rbf", 1.0, 1.0, t, y, mask, 0.01)
     assert st == 0
-    gfd = oracle.loglik_grad_fd("rbf", 1.0, 1.0, t, y, mask, 0.01)
-    check_grad(g, gfd, t.size, 1e-6, "rbf 2^20")
+    # the oracle's three directions and the six difference points run in
+    # threads (its C routines release the interpreter lock)
+    m = om.make_model("rbf", 1.0, 1.0)
+    with ThreadPoolExecutor(3) as ex:
+        fw = list(ex.map(lambda p: oracle.loglik_tangent(m, t, y, mask, 0.01, p, with_scale=True),
+                         oracle.GRAD_PARAMS))
+    rll = fw[0][0]
+    rg = np.array([f[1] for f in fw])
+    sc = np.array([f[2] for f in fw])
+    assert abs(ll - rll) <= LLTOL["rbf"] * max(abs(rll), t.size)
+    check_grad(g, rg, sc, t.size, TOL["rbf"], "rbf 2^20")
+    gfd = oracle.loglik_grad_fd("rbf", 1.0, 1.0, t, y, mask, 0.01, threads=6)
+    noise = 4.0 * np.finfo(np.float64).eps * abs(rll) / 1e-6
+    err = np.max(np.abs(g - gfd) / (1e-5 * np.abs(gfd) + noise))
+    report("gradient vs central differences, rbf 2^20 (|d| / (1e-5|fd| + fd rounding))", err, 1.0)
+    assert err <= 1.0, (g, gfd, noise)
 
 
 def test_autograd_function_and_a_descent_step():

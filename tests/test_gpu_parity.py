@@ -40,10 +40,29 @@ def host(x):
     return x.detach().cpu().numpy()
 
 
+REPORT = None
+
+
+@pytest.fixture(autouse=True)
+def _rep(report):
+    global REPORT
+    REPORT = report
+
+
+def _rep_key(what):
+    return str(what).split("/")[0]
+
+
 def check_marginals(fm, fv, ll, rm, rv, rll, n_obs, tol, what=""):
     em = np.max(np.abs(fm - rm) / np.maximum(np.abs(rm), np.sqrt(rv)))
     ev = np.max(np.abs(fv - rv) / rv)
     el = abs(ll - rll) / max(abs(rll), n_obs) if ll is not None else 0.0
+    if REPORT is not None:
+        REPORT(f"posterior mean, {_rep_key(what)} (tol {tol:g})", em, tol)
+        REPORT(f"posterior variance, {_rep_key(what)} (tol {tol:g})", ev, tol)
+        if ll is not None:
+            REPORT(f"log-likelihood, {_rep_key(what)} (tol {tol:g})", el, tol)
+    assert np.isfinite(em) and np.isfinite(ev) and np.isfinite(el), (what, em, ev, el)
     assert em <= tol and ev <= tol and el <= tol, (what, em, ev, el)
     return em, ev, el
 
@@ -53,6 +72,10 @@ def check_states(x, Pk, rx, rP, tol, what=""):
     sd = np.sqrt(np.maximum(np.einsum("kii->ki", rP), 1e-300))
     ex = np.max(np.abs(x - rx) / np.maximum(np.abs(rx), sd))
     eP = np.max(np.abs(Pk - rP) / (sd[:, :, None] * sd[:, None, :]))
+    if REPORT is not None:
+        REPORT(f"state mean, {_rep_key(what)} (tol {tol:g})", ex, tol)
+        REPORT(f"state covariance, {_rep_key(what)} (tol {tol:g})", eP, tol)
+    assert np.isfinite(ex) and np.isfinite(eP), (what, ex, eP)
     assert ex <= tol and eP <= tol, (what, ex, eP)
 
 
@@ -132,12 +155,12 @@ def test_filter_and_smoother_states(kind, n):
     tg, yg, mg = dev(t), dev(y), dev(mask, torch.uint8)
     xf, Pf, ll, ws = P.filter(m, tg, yg, mg, 0.01)
     assert P.status(ws) == 0
-    check_states(host(xf).T, unpack(host(Pf), d), res.m, res.P, TOL[kind], "filter")
+    check_states(host(xf).T, unpack(host(Pf), d), res.m, res.P, TOL[kind], f"filter {kind}")
     assert abs(float(host(ll)[0]) - res.loglik) <= TOL[kind] * max(abs(res.loglik), s.N)
     fm, fv, xs, Ps, ws2 = P.smooth(m, tg, xf, Pf, states=True)
     assert P.status(ws2) == 0
-    check_marginals(host(fm), host(fv), None, res.f_mean, res.f_var, None, s.N, TOL[kind], "smooth")
-    check_states(host(xs).T, unpack(host(Ps), d), res.ms, res.Ps, 10 * TOL[kind], "smooth states")
+    check_marginals(host(fm), host(fv), None, res.f_mean, res.f_var, None, s.N, TOL[kind], f"smooth {kind}")
+    check_states(host(xs).T, unpack(host(Ps), d), res.ms, res.Ps, 10 * TOL[kind], f"smooth states {kind}")
     # the log-likelihood entry point sums per chunk from the fold's zero-start
     # terms (no propagate pass): the same value up to the summation order
     ll2, _ = P.loglik(m, tg, yg, mg, 0.01)
@@ -350,7 +373,8 @@ def test_predict_from_host_buffers_equals_device_call():
     ref = (host(mean), host(var), host(ll))
     ht = [torch.as_tensor(x).pin_memory() for x in (s.t_train, s.y_train, s.t_test)]
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    outs = [tuple(torch.empty(k, dtype=torch.float64).pin_memory() for k in (s.M, s.M, 1)) for _ in streams]
+    outs = [tuple(torch.full((k,), float("nan"), dtype=torch.float64).pin_memory() for k in (s.M, s.M, 1))
+            for _ in streams]
     keep = [P.predict_host(m, *ht, 0.01, o, stream=st) for st, o in zip(streams, outs)]   # workspaces stay alive
     torch.cuda.synchronize()
     del keep

@@ -239,3 +239,28 @@ def test_host_argument_errors_of_the_newer_entry_points(lib):
     assert lib.pssgp_workspace_size_grad(3, 1000) > lib.pssgp_workspace_size(3, 1000)
     assert lib.pssgp_fit_workspace_size(3, 1000, 4) > lib.pssgp_workspace_size_grad(3, 1000)
     assert lib.pssgp_tune_set(0, 8) == -2 and lib.pssgp_tune_set(3, 5) == EINVAL and lib.pssgp_tune_get(9) == -2
+
+
+def test_noalloc_size_limits_stated_in_the_header(lib):
+    """The allocation-free log-likelihood accepts n while the workspace of the
+    scan plan fits its 32 MiB scratch; the header states the resulting limits
+    per state dimension, which must be the largest n with
+    pssgp_workspace_size(d, n) <= 32 MiB (sizes are non-decreasing in n)."""
+    text = " ".join(open(os.path.join(ROOT, "include", "pssgp.h")).read().replace("*", " ").split())
+    for d in (1, 2, 3, 6, 8):
+        lo, hi = 1, 1 << 22
+        while lo < hi:
+            mid = (lo + hi + 1) // 2
+            if lib.pssgp_workspace_size(d, mid) <= 32 << 20:
+                lo = mid
+            else:
+                hi = mid - 1
+        assert f"{lo:,} at d = {d}" in text, (d, lo)
+
+
+def test_step_count_bound(lib):
+    """n above 2^40 is rejected (keeps every workspace size far from int64
+    overflow)."""
+    assert lib.pssgp_workspace_size(6, 1 << 40) > 0
+    assert lib.pssgp_workspace_size(6, (1 << 40) + 1) == 0
+    assert lib.pssgp_workspace_size_grad(6, (1 << 41)) == 0
