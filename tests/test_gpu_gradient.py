@@ -4,13 +4,18 @@ oracle's forward-mode gradient (and, at the full 2^20-step size, also against
 central differences of the oracle's log-likelihood).
 
 Tolerance semantics, per component i: relative error
-    |g_i - ref_i| / max(|ref_i|, s_i / sqrt(n_obs)) <= tol,
+    |g_i - ref_i| / max(|ref_i|, s_i / sqrt(n_obs), 1e-5 sqrt(n_obs)) <= tol,
 tol 1e-8 for Matern kernels and 1e-6 for the order-6 RBF Taylor model.
 s_i is the sum over steps of |per-step term| of the forward-mode derivative
 (the oracle returns it): a component is a sum of n_obs such terms, and
 s_i / sqrt(n_obs) is the size of a sum of n_obs terms of that magnitude with
 random signs.  A component below it (near an optimum, where the terms cancel)
-is judged against that scale instead of its own value.  Against central
+is judged against that scale instead of its own value.  The per-step terms
+are dimensionless; where every one of them is zero in exact arithmetic (the
+lengthscale derivative of a one-observation series: H P_inf H^T does not
+depend on the lengthscale) each still carries the rounding of the model's
+tangent (up to ~1e-13 for the RBF model, whose tangent goes through a root
+finder), so the scale is never taken below 1e-5 per sqrt(step).  Against central
 differences (h = 1e-6): |g_i - fd_i| <= 1e-5 |fd_i| + 4 eps |loglik| / h, the
 second term the rounding of the two log-likelihood values the difference
 divides by 2h.
@@ -55,9 +60,9 @@ REPORT = None
 
 
 def check_grad(g, ref, scale, nobs, tol, what=""):
-    """Relative error per component, floored at scale / sqrt(n_obs)."""
+    """Relative error per component, floored at max(scale / sqrt(n_obs), 1e-5 sqrt(n_obs))."""
     g = np.asarray(g, dtype=np.float64)
-    floor = np.asarray(scale) / np.sqrt(max(nobs, 1))
+    floor = np.maximum(np.asarray(scale) / np.sqrt(max(nobs, 1)), 1e-5 * np.sqrt(max(nobs, 1)))
     err = np.max(np.abs(g - ref) / np.maximum(np.maximum(np.abs(ref), floor), 1e-300))
     if REPORT is not None:
         REPORT(f"gradient vs forward mode, {what[0] if isinstance(what, tuple) else what}".split("/")[0], err, tol)

@@ -160,7 +160,7 @@ def test_filter_and_smoother_states(kind, n):
     fm, fv, xs, Ps, ws2 = P.smooth(m, tg, xf, Pf, states=True)
     assert P.status(ws2) == 0
     check_marginals(host(fm), host(fv), None, res.f_mean, res.f_var, None, s.N, TOL[kind], f"smooth {kind}")
-    check_states(host(xs).T, unpack(host(Ps), d), res.ms, res.Ps, 10 * TOL[kind], f"smooth states {kind}")
+    check_states(host(xs).T, unpack(host(Ps), d), res.ms, res.Ps, TOL[kind], f"smooth states {kind}")
     # the log-likelihood entry point sums per chunk from the fold's zero-start
     # terms (no propagate pass): the same value up to the summation order
     ll2, _ = P.loglik(m, tg, yg, mg, 0.01)
