@@ -257,6 +257,81 @@ int pssgp_loglik_grad_batched(const pssgp_model* model, const int64_t* offsets,
                               double* loglik, double* grad, void* ws,
                               size_t ws_bytes, void* stream);
 
+/* ---- one long series split over several GPUs (Sec. 3, Prop. 1; supplement
+ * Prop. 2) --------------------------------------------------------------------
+ * The scans over time are scans of associative operators, so a series cut
+ * into G contiguous chunks (chunk r on GPU r: its steps, in time order, after
+ * those of chunk r-1) needs one exchange per direction:
+ *   1. every rank: pssgp_split_filter_reduce -> its chunk's filter aggregate;
+ *   2. all-gather the G filter aggregates (rank order) into aggs_f[G][nf];
+ *   3. every rank: pssgp_split_filter_finish -> its filter outputs and the
+ *      log-likelihood of its observations given all earlier ones (the chunks
+ *      before it enter its scan as one element: their aggregates folded);
+ *   4. every rank: pssgp_split_smooth_reduce -> its chunk's smoother aggregate;
+ *   5. all-gather the G smoother aggregates into aggs_s[G][ns]; all-reduce
+ *      (sum) the log-likelihoods;
+ *   6. every rank: pssgp_split_smooth_finish -> its smoother outputs (the
+ *      chunks after it folded into one element after its scan).
+ * The first and last time of every chunk must be known to its neighbours
+ * (t_prev: the time of the last step of chunk r-1; t_next: the time of the
+ * first step of chunk r+1; NaN at the ends of the series).  Every rank uses
+ * the same model.  Aggregates are device arrays of pssgp_split_agg_doubles
+ * doubles in the library's internal (balanced) coordinates: opaque, to be
+ * passed between these calls unchanged.  The workspace (pssgp_workspace_size
+ * (d, n) bytes, n = the chunk's steps) carries state from each *_reduce call
+ * to the matching *_finish call: use the same workspace, inputs and scan
+ * tuning for both.  A *_reduce call clears the status word; a *_finish call
+ * adds its bits to it.  With G = 1 the sequence is pssgp_filter followed by
+ * pssgp_smooth. */
+
+/* Doubles in one chunk aggregate: filter (smoother = 0) 2 d^2 + 3 d
+ * (A, b, C, eta, J), smoother (smoother = 1) d^2 + d + d(d+1)/2 (E, g, L);
+ * 0 for d outside 1..PSSGP_DMAX. */
+int32_t pssgp_split_agg_doubles(int32_t d, int32_t smoother);
+
+/* Step 1: discretises the chunk (step 0 is the transition from
+ * t_prev, or the series' first step if t_prev is NaN), folds its filtering
+ * elements (Sec. 3) and writes the chunk's aggregate to agg (device,
+ * pssgp_split_agg_doubles(d, 0) doubles).  Other arguments as pssgp_filter
+ * for the chunk's n steps. */
+int pssgp_split_filter_reduce(const pssgp_model* model, const double* t,
+                              const double* y, const uint8_t* mask,
+                              const double* R, int32_t R_per_step, int64_t n,
+                              double t_prev, double* agg, void* ws,
+                              size_t ws_bytes, void* stream);
+
+/* Step 3: aggs: device array of the G chunks' filter aggregates in rank
+ * order; the ones before `rank` are folded into the filter state before the
+ * chunk.  Outputs as pssgp_filter (xf, Pf nullable: without both only the
+ * log-likelihood is formed); loglik (nullable, one device double): the sum
+ * over the chunk's observations of log p(y_k | all earlier y). */
+int pssgp_split_filter_finish(const pssgp_model* model, const double* t,
+                              const double* y, const uint8_t* mask,
+                              const double* R, int32_t R_per_step, int64_t n,
+                              const double* aggs, int32_t G, int32_t rank,
+                              double* xf, double* Pf, int64_t ld,
+                              double* loglik, void* ws, size_t ws_bytes,
+                              void* stream);
+
+/* Step 4: the chunk's smoothing elements (supplement Prop. 2) from its filter
+ * outputs xf, Pf (as pssgp_smooth); the element of the chunk's last step is
+ * the transition to t_next (or the series' last element if t_next is NaN).
+ * Writes the chunk's aggregate to agg (device, pssgp_split_agg_doubles(d, 1)
+ * doubles). */
+int pssgp_split_smooth_reduce(const pssgp_model* model, const double* t,
+                              const double* xf, const double* Pf, int64_t n,
+                              int64_t ld, double t_next, double* agg, void* ws,
+                              size_t ws_bytes, void* stream);
+
+/* Step 6: aggs: device array of the G chunks' smoother aggregates in rank
+ * order; the ones after `rank` are folded into the smoothed state after the
+ * chunk.  Outputs as pssgp_smooth (all nullable). */
+int pssgp_split_smooth_finish(const pssgp_model* model, int64_t n, int64_t ld,
+                              const double* aggs, int32_t G, int32_t rank,
+                              double* f_mean, double* f_var, double* xs,
+                              double* Ps, void* ws, size_t ws_bytes,
+                              void* stream);
+
 /* Allocation-free variant of pssgp_loglik for callers that cannot allocate
  * device memory themselves -- for instance a plugin inside a host program
  * that owns every device allocation and does not let third-party code call
@@ -266,8 +341,8 @@ int pssgp_loglik_grad_batched(const pssgp_model* model, const int64_t* offsets,
  *  - Scratch: a fixed 32 MiB array inside the library's device image, held on
  *    every GPU that loads the library until the process exits.  That bounds
  *    the problem size: the workspace of the current scan tuning must fit in
- *    32 MiB, which allows n (merged steps) up to 290,464 at d = 1, 137,781
- *    at d = 2, 78,584 at d = 3, 24,594 at d = 6 and 14,574 at d = 8 (the
+ *    32 MiB, which allows n (merged steps) up to 290,464 at d = 1, 137,780
+ *    at d = 2, 78,582 at d = 3, 24,593 at d = 6 and 14,573 at d = 8 (the
  *    largest n with pssgp_workspace_size(d, n) <= 32 MiB; per-step records
  *    plus the per-chunk aggregates).  Larger problems are rejected with PSSGP_ESCRATCH
  *    before anything is launched.

@@ -133,6 +133,24 @@ def kalman_filter(m, F, Q, y, mask, R):
     return mo, Po, mp, Pp, ll.value
 
 
+def kalman_filter_from(m, x0, P0, F, Q, y, mask, R):
+    """Sequential KF of a piece of a series started from the state
+    N(x0, P0) before its step 0 (every step, step 0 included, a transition
+    F[k], Q[k]); returns (m, P, m_pred, P_pred, loglik)."""
+    lib = _load()
+    d = m.d
+    n = F.shape[0]
+    Ra, per = _R_arr(R, n)
+    y = _c(y); mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    mo = np.empty((n, d)); Po = np.empty((n, d, d)); mp = np.empty((n, d)); Pp = np.empty((n, d, d))
+    ll = ctypes.c_double(0.0)
+    rc = lib.orc_kalman_filter_from(d, _p(_c(m.H).ravel()), _p(Ra), per, _p(_c(x0)), _p(_c(P0)), _p(_c(F)),
+                                    _p(_c(Q)), _p(y), _u8(mask), ctypes.c_long(n), _p(mo), _p(Po), _p(mp),
+                                    _p(Pp), ctypes.byref(ll))
+    _check(rc, "kalman_filter_from")
+    return mo, Po, mp, Pp, ll.value
+
+
 def rts_smoother(F, mo, Po, mp, Pp):
     lib = _load()
     n, d = mo.shape

@@ -283,6 +283,66 @@ int orc_kalman_filter(int d, const double *H_, const double *R, int R_per_step,
 /* Prop. 2:  P^s_k = P_k + G_k (P^s_{k+1} - F P_k F^T - Q) G_k^T.          */
 /* Here F, Q of step k+1 are the transition from step k to step k+1.       */
 /* mp, Pp: the filter's predicted moments (F m_k, F P_k F^T + Q) of k+1.   */
+/* The sequential Kalman filter started from a given state: the state at the
+ * time before step 0 is N(x0, P0), and every step k, step 0 included, is
+ * predicted through its own transition (F[k], Q[k]) and then updated as in
+ * orc_kalman_filter (supplement Eqs. (nomeas), (withmeas1)).  This is the
+ * filter of a piece of a longer series given the filter state at the piece's
+ * start; with F[0] = 0 and Q[0] = P_inf it is orc_kalman_filter.  loglik:
+ * the sum over the observed steps of log p(y_k | earlier y of the piece, start
+ * state). */
+int orc_kalman_filter_from(int d, const double *H_, const double *R, int R_per_step,
+                           const double *x0_, const double *P0_, const double *F_, const double *Q_,
+                           const double *y, const unsigned char *mask, long n,
+                           double *m_out, double *P_out, double *mp_out, double *Pp_out,
+                           double *loglik) {
+  if (d < 1 || d > DMAX || n < 1) return 3;
+  const real twopi = 6.283185307179586476925286766559L;
+  int dd = d * d;
+  real H[DMAX], m[DMAX], P[DMAX * DMAX];
+  load(1, d, H_, H);
+  load(1, d, x0_, m);
+  load(d, d, P0_, P);
+  real ll = 0.0L;
+  for (long k = 0; k < n; ++k) {
+    real F[DMAX * DMAX], Q[DMAX * DMAX], FP[DMAX * DMAX], Ft[DMAX * DMAX], mp[DMAX], Pp[DMAX * DMAX];
+    load(d, d, F_ + k * dd, F); load(d, d, Q_ + k * dd, Q);
+    mm(d, d, 1, F, m, mp);                         /* m^- = F m          */
+    mm(d, d, d, F, P, FP);
+    tr(d, d, F, Ft);
+    mm(d, d, d, FP, Ft, Pp);                       /* P^- = F P F^T + Q  */
+    for (int i = 0; i < dd; ++i) Pp[i] += Q[i];
+    symmetrize(d, Pp);
+    if (mp_out) store(1, d, mp, mp_out + k * d);
+    if (Pp_out) store(d, d, Pp, Pp_out + k * dd);
+    if (mask[k]) {
+      real Rk = (real)(R_per_step ? R[k] : R[0]);
+      real PH[DMAX], S = Rk, v = (real)y[k], K[DMAX];
+      for (int i = 0; i < d; ++i) {
+        real s = 0.0L;
+        for (int j = 0; j < d; ++j) s += Pp[i * d + j] * H[j];
+        PH[i] = s;
+      }
+      for (int i = 0; i < d; ++i) S += H[i] * PH[i];
+      if (!(S > 0.0L)) return 1;
+      for (int i = 0; i < d; ++i) v -= H[i] * mp[i];
+      for (int i = 0; i < d; ++i) K[i] = PH[i] / S;
+      for (int i = 0; i < d; ++i) m[i] = mp[i] + K[i] * v;
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) P[i * d + j] = Pp[i * d + j] - K[i] * S * K[j];
+      symmetrize(d, P);
+      ll += -0.5L * (logl(twopi * S) + v * v / S);
+    } else {
+      memcpy(m, mp, sizeof(real) * d);
+      memcpy(P, Pp, sizeof(real) * dd);
+    }
+    store(1, d, m, m_out + k * d);
+    store(d, d, P, P_out + k * dd);
+  }
+  if (loglik) *loglik = (double)ll;
+  return 0;
+}
+
 /* ----------------------------------------------------------------------- */
 int orc_rts_smoother(int d, const double *F_, const double *m_, const double *P_,
                      const double *mp_, const double *Pp_, long n,

@@ -119,6 +119,15 @@ def lib():
         L.pssgp_graph_launch.argtypes = [vp, vp]
         L.pssgp_graph_destroy.argtypes = [vp]
         L.pssgp_loglik_noalloc.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, vp, vp]
+        L.pssgp_split_agg_doubles.argtypes = [i32, i32]
+        L.pssgp_split_agg_doubles.restype = i32
+        L.pssgp_split_filter_reduce.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, dp, vp, vp,
+                                                sz, vp]
+        L.pssgp_split_filter_finish.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, i32, i32,
+                                                vp, vp, i64, vp, vp, sz, vp]
+        L.pssgp_split_smooth_reduce.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, i64, i64, dp, vp, vp, sz, vp]
+        L.pssgp_split_smooth_finish.argtypes = [ctypes.POINTER(PssgpModel), i64, i64, vp, i32, i32, vp, vp, vp, vp,
+                                                vp, sz, vp]
         L.pssgp_timing_name.argtypes = [i32]
         L.pssgp_timing_name.restype = ctypes.c_char_p
         if L.pssgp_model_bytes() != ctypes.sizeof(PssgpModel):
@@ -443,6 +452,72 @@ def predict_host(model: Model, t_train, y_train, t_test, R: float, out, ws=None,
                                   float(R), _ptr(mean), _ptr(var), _ptr(ll), _ptr(ws), ws.numel(), st)
     _check(rc, "pssgp_predict_host")
     return ws
+
+
+# ---------------------------------------------------------------------------
+# one long series split in time chunks over several GPUs (calls of one rank;
+# the exchange between them is in paper_2102_09964_b300.split)
+# ---------------------------------------------------------------------------
+def split_agg_doubles(d: int, smoother: bool) -> int:
+    return int(lib().pssgp_split_agg_doubles(int(d), int(bool(smoother))))
+
+
+def split_filter_reduce(model: Model, t, y, mask, R, t_prev: float, ws, agg=None):
+    """This chunk's filter aggregate (device float64[nf]); ws carries state to
+    split_filter_finish."""
+    d, n = model.d, t.numel()
+    R = _f64(R, t.device).reshape(-1)
+    per = 1 if R.numel() == n and n > 1 else 0
+    agg = agg if agg is not None else _empty(split_agg_doubles(d, False), dtype=torch.float64, device=t.device)
+    rc = lib().pssgp_split_filter_reduce(ctypes.byref(model.raw), _ptr(t), _ptr(y), _ptr(mask), _ptr(R), per, n,
+                                         float(t_prev), _ptr(agg), _ptr(ws), ws.numel(), _stream())
+    _check(rc, "pssgp_split_filter_reduce")
+    return agg
+
+
+def split_filter_finish(model: Model, t, y, mask, R, aggs, rank: int, ws, outputs=True):
+    """Filter outputs of this chunk given every chunk's aggregate (aggs: device
+    float64[G, nf] in rank order); returns (xf, Pf, loglik[1]) with xf, Pf
+    None unless outputs."""
+    d, n = model.d, t.numel()
+    dev = t.device
+    R = _f64(R, dev).reshape(-1)
+    per = 1 if R.numel() == n and n > 1 else 0
+    aggs = aggs.contiguous()
+    xf = _empty(d, n, dtype=torch.float64, device=dev) if outputs else None
+    Pf = _empty(d * (d + 1) // 2, n, dtype=torch.float64, device=dev) if outputs else None
+    ll = _empty(1, dtype=torch.float64, device=dev)
+    rc = lib().pssgp_split_filter_finish(ctypes.byref(model.raw), _ptr(t), _ptr(y), _ptr(mask), _ptr(R), per, n,
+                                         _ptr(aggs), aggs.shape[0], int(rank), _ptr(xf), _ptr(Pf), n, _ptr(ll),
+                                         _ptr(ws), ws.numel(), _stream())
+    _check(rc, "pssgp_split_filter_finish")
+    return xf, Pf, ll
+
+
+def split_smooth_reduce(model: Model, t, xf, Pf, t_next: float, ws, agg=None):
+    """This chunk's smoother aggregate (device float64[ns]); ws carries state
+    to split_smooth_finish."""
+    d, n = model.d, t.numel()
+    agg = agg if agg is not None else _empty(split_agg_doubles(d, True), dtype=torch.float64, device=t.device)
+    rc = lib().pssgp_split_smooth_reduce(ctypes.byref(model.raw), _ptr(t), _ptr(xf), _ptr(Pf), n, n, float(t_next),
+                                         _ptr(agg), _ptr(ws), ws.numel(), _stream())
+    _check(rc, "pssgp_split_smooth_reduce")
+    return agg
+
+
+def split_smooth_finish(model: Model, n: int, aggs, rank: int, ws, device="cuda", states=False):
+    """Smoother outputs of this chunk given every chunk's smoother aggregate;
+    returns (f_mean, f_var, xs, Ps) with xs, Ps None unless states."""
+    d = model.d
+    aggs = aggs.contiguous()
+    fm = _empty(n, dtype=torch.float64, device=device)
+    fv = _empty(n, dtype=torch.float64, device=device)
+    xs = _empty(d, n, dtype=torch.float64, device=device) if states else None
+    Ps = _empty(d * (d + 1) // 2, n, dtype=torch.float64, device=device) if states else None
+    rc = lib().pssgp_split_smooth_finish(ctypes.byref(model.raw), n, n, _ptr(aggs), aggs.shape[0], int(rank),
+                                         _ptr(fm), _ptr(fv), _ptr(xs), _ptr(Ps), _ptr(ws), ws.numel(), _stream())
+    _check(rc, "pssgp_split_smooth_finish")
+    return fm, fv, xs, Ps
 
 
 def debug_filter_aggregates(model: Model, t, y, mask, R, lanes: int = 0):

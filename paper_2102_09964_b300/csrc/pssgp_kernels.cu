@@ -127,7 +127,7 @@ struct Plan {
   int fqs, egs;      // per-step record strides (doubles, even)
   // byte offsets into the workspace
   int64_t o_status, o_fq, o_egl, o_laggf, o_waggf, o_laggs, o_waggs, o_llp, o_fmean, o_fvar, o_t, o_y, o_mask,
-      o_tpos, o_rstep, o_seg, o_llstep, o_adj, o_tauq, o_lpi, o_lmbar, o_lgj, o_gpart, o_gstep, total;
+      o_tpos, o_rstep, o_seg, o_llstep, o_adj, o_tauq, o_lpi, o_lmbar, o_lgj, o_gpart, o_gstep, o_bnd, total;
 };
 
 int warps_for(int d) {
@@ -171,6 +171,7 @@ Plan make_plan(int d, int64_t n, int64_t lanes_req, int warps = 0, bool grad = f
   p.o_rstep = o; o += align256(n * 8);     // batched: noise variance per step
   p.o_seg = o; o += align256(n);           // batched: 1 at each series' first step
   p.o_llstep = o; o += align256(n * 8);    // batched: log-likelihood pieces per step
+  p.o_bnd = o; o += align256(p.nf * 8);     // split series: the folded aggregate of the other chunks
   p.o_adj = p.o_tauq = p.o_lpi = p.o_lmbar = p.o_lgj = p.o_gpart = p.o_gstep = -1;
   if (grad) {                                // gradient: forward moments, scan state
     const int adjs = (d + sym + 2 + 1) / 2 * 2;
@@ -234,6 +235,13 @@ struct ScanArgs {
   double* lagg_a;            // [ns][P0] covariance-adjoint lane aggregates
   double* wagg_a;            // [2][ns][P2] and their warp aggregates
   const double* wfin_a;
+  // one chunk of a longer series (split over several GPUs)
+  double t_prev;             // time of the step before the chunk (NaN: the series starts at step 0)
+  double t_next;             // time of the step after the chunk (NaN: the series ends at step n-1)
+  const double* start_f;     // packed filter aggregate of all steps before the chunk (a filter state:
+                             // it holds the series' first step, so A = 0, eta = 0, J = 0), or null
+  const double* end_s;       // packed smoother aggregate of all steps after the chunk (a smoothed state:
+                             // it holds the series' last step, so E = 0), or null
 };
 
 __device__ __forceinline__ void flag(int* status, int bits) {
@@ -418,7 +426,9 @@ __device__ __forceinline__ void load_rts(const double* rec, int64_t k, Mat<D>& E
 // filter levels 0 + 1: discretise, fold the chunk's elements, warp scan
 // ---------------------------------------------------------------------------
 // discretisation into the per-step records, one thread per step; a series'
-// first step (k = 0) gets F = 0, Q = P_inf.  Also checks the times.  The
+// first step (k = 0) gets F = 0, Q = P_inf, unless t_prev (the time of the
+// step before a chunk of a longer series) is a number: then step 0 is the
+// transition from t_prev.  Also checks the times.  The
 // block's records (consecutive steps, contiguous in memory) are staged in
 // shared memory and written out with consecutive threads on consecutive
 // addresses.
@@ -428,20 +438,21 @@ constexpr int DISC_BLOCK = 128;
 // stores, and the third block fills the FP64 pipe during another's stores.
 template <int D>
 __global__ void __launch_bounds__(DISC_BLOCK, (D <= 6 ? 3 : 1)) k_discretize_rec(const DevModel<D> m, const double* t, int64_t n,
-                                                             double* rec, double* tauq, int* status) {
+                                                             double* rec, double* tauq, int* status,
+                                                             double t_prev) {
   constexpr int FQS = fqs_of<D>();
   extern __shared__ double stage[];           // DISC_BLOCK * FQS doubles
   const int64_t k0 = (int64_t)blockIdx.x * DISC_BLOCK;
   const int64_t k = k0 + threadIdx.x;
   const bool act = k < n;
-  const bool first = (k == 0);
+  const bool first = (k == 0) && isnan(t_prev);
   double h = 0.0;
   int bits = 0;
   if (act) {
     const double t1 = t[k];
     if (nonfinite(t1)) bits |= PSSGP_ENAN;
     if (!first) {
-      h = t1 - t[k - 1];
+      h = t1 - (k > 0 ? t[k - 1] : t_prev);
       if (negative_nonzero(h)) bits |= PSSGP_EUNSORTED;
     }
   }
@@ -753,6 +764,18 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
   flag(a.status, bits);
 }
 
+// The filter state (x = b, P = C) of a packed filter aggregate that holds a
+// series' first step (then A = 0, eta = 0, J = 0: a state, Prop. 1).
+template <int D>
+__device__ __forceinline__ void load_fstate(const double* p, Vec<D>& x, Mat<D>& P) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) x[i] = p[D * D + i];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) { P[i][j] = p[D * D + D + pidx<D>(i, j)]; P[j][i] = P[i][j]; }
+}
+
 // filter level 2: one Kogge-Stone round over the warp aggregates, one warp
 // per element (warp-cooperative operator, see warp_ops.cuh)
 template <int D>
@@ -861,6 +884,8 @@ __global__ void __launch_bounds__(BLOCK) k_filter_llfinish(const DevModel<D> m, 
 #pragma unroll
     for (int i = 0; i < D; ++i) x[i] = W.b[i];
     copy<D>(W.C, P);
+  } else if (a.start_f) {   // a chunk of a longer series: the state before it
+    load_fstate<D>(a.start_f, x, P);
   }
   if (lane > 0) {
     FAgg<D> I;
@@ -934,6 +959,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
 #pragma unroll
     for (int i = 0; i < D; ++i) x[i] = W.b[i];
     copy<D>(W.C, P);
+  } else if (a.start_f) {   // a chunk of a longer series: the state before it
+    load_fstate<D>(a.start_f, x, P);
   }
   if (lane > 0) {
     FAgg<D> I;
@@ -1252,6 +1279,101 @@ __global__ void __launch_bounds__(BLOCK) k_smoother_ks(const double* in, double*
   warp_sagg_combine<D>(sa, sb, work, out + i, P2, lane);
 }
 
+// ---------------------------------------------------------------------------
+// one long series split in time chunks (one per GPU): the chunk aggregates of
+// the other chunks enter each chunk's scan as one element before it (filter)
+// or after it (smoother)
+// ---------------------------------------------------------------------------
+// packed (stride 1) aggregates[lo .. hi-1] folded in order by one warp:
+// out = agg[lo] x agg[lo+1] x ... x agg[hi-1] (filtering operator, Sec. 3)
+template <int D>
+__global__ void __launch_bounds__(32) k_fold_filter_range(const double* aggs, int lo, int hi, double* out,
+                                                          int* status) {
+  constexpr int NF = FAggSize<D>::N;
+  __shared__ double sm[WarpFilterSmem<D>::N + NF];
+  double* sa = sm;
+  double* sb = sa + NF;
+  double* work = sb + NF;
+  double* so = sm + WarpFilterSmem<D>::N;
+  const int lane = threadIdx.x;
+  for (int e = lane; e < NF; e += 32) sa[e] = aggs[(int64_t)lo * NF + e];
+  __syncwarp();
+  bool ok = true;
+  for (int i = lo + 1; i < hi; ++i) {
+    for (int e = lane; e < NF; e += 32) sb[e] = aggs[(int64_t)i * NF + e];
+    __syncwarp();
+    if (!warp_fagg_combine<D>(sa, sb, work, so, 1, lane)) ok = false;
+    __syncwarp();
+    for (int e = lane; e < NF; e += 32) sa[e] = so[e];
+    __syncwarp();
+  }
+  for (int e = lane; e < NF; e += 32) out[e] = sa[e];
+  if (!ok && lane == 0) flag(status, PSSGP_ENOTPD);
+}
+
+// the same with the smoothing operator (supplement, Prop. 2)
+template <int D>
+__global__ void __launch_bounds__(32) k_fold_smoother_range(const double* aggs, int lo, int hi, double* out) {
+  constexpr int NS = SAggSize<D>::N;
+  __shared__ double sm[WarpSmootherSmem<D>::N + NS];
+  double* sa = sm;
+  double* sb = sa + NS;
+  double* work = sb + NS;
+  double* so = sm + WarpSmootherSmem<D>::N;
+  const int lane = threadIdx.x;
+  for (int e = lane; e < NS; e += 32) sa[e] = aggs[(int64_t)lo * NS + e];
+  __syncwarp();
+  for (int i = lo + 1; i < hi; ++i) {
+    for (int e = lane; e < NS; e += 32) sb[e] = aggs[(int64_t)i * NS + e];
+    __syncwarp();
+    warp_sagg_combine<D>(sa, sb, work, so, 1, lane);
+    __syncwarp();
+    for (int e = lane; e < NS; e += 32) sa[e] = so[e];
+    __syncwarp();
+  }
+  for (int e = lane; e < NS; e += 32) out[e] = sa[e];
+}
+
+// filter: every level-2 result w (steps of warps 0..w) becomes
+// start x result, so that the chunk's scan starts from the state `start`
+template <int D>
+__global__ void __launch_bounds__(BLOCK) k_apply_filter_start(double* wfin, int64_t P2, const double* start,
+                                                             int* status) {
+  constexpr int NF = FAggSize<D>::N;
+  __shared__ double sm[BLOCK / 32][WarpFilterSmem<D>::N];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (BLOCK / 32) + wid;
+  if (i >= P2) return;                       // whole warp
+  double* sa = sm[wid];
+  double* sb = sa + NF;
+  double* work = sb + NF;
+  for (int e = lane; e < NF; e += 32) { sa[e] = start[e]; sb[e] = wfin[e * P2 + i]; }
+  __syncwarp();
+  if (!warp_fagg_combine<D>(sa, sb, work, wfin + i, P2, lane) && lane == 0) flag(status, PSSGP_ENOTPD);
+}
+
+// smoother: every level-2 result w (steps of warps w..P2-1) becomes
+// result x end, so that the chunk's scan ends in the smoothed state `end`
+template <int D>
+__global__ void __launch_bounds__(BLOCK) k_apply_smoother_end(double* wfin, int64_t P2, const double* end) {
+  constexpr int NS = SAggSize<D>::N;
+  __shared__ double sm[BLOCK / 32][WarpSmootherSmem<D>::N];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (BLOCK / 32) + wid;
+  if (i >= P2) return;
+  double* sa = sm[wid];
+  double* sb = sa + NS;
+  double* work = sb + NS;
+  for (int e = lane; e < NS; e += 32) { sa[e] = wfin[e * P2 + i]; sb[e] = end[e]; }
+  __syncwarp();
+  warp_sagg_combine<D>(sa, sb, work, wfin + i, P2, lane);
+}
+
+// one aggregate from an entry-major array (stride st) to packed (stride 1)
+__global__ void k_pack_aggregate(const double* src, int64_t st, int count, double* dst) {
+  for (int e = threadIdx.x; e < count; e += blockDim.x) dst[e] = src[(int64_t)e * st];
+}
+
 // smoother outputs of step k: f = H x = H D z = z_0 (the model is built with
 // H D = e_0^T), its variance, and optionally the state in SDE coordinates
 template <int D>
@@ -1289,6 +1411,12 @@ __global__ void __launch_bounds__(BLOCK, 1) k_smoother_propagate(const DevModel<
   if (w + 1 < a.P2) {
     SAgg<D> V;
     load_sagg<D>(a.wfin_s + (w + 1), a.P2, V);
+#pragma unroll
+    for (int i = 0; i < D; ++i) ms[i] = V.g[i];
+    copy<D>(V.L, Ps);
+  } else if (a.end_s) {   // a chunk of a longer series: the smoothed state after it
+    SAgg<D> V;
+    load_sagg<D>(a.end_s, 1, V);
 #pragma unroll
     for (int i = 0; i < D; ++i) ms[i] = V.g[i];
     copy<D>(V.L, Ps);
@@ -1352,12 +1480,14 @@ __global__ void __launch_bounds__(BLOCK, 1) k_smoother_elements(const DevModel<D
   SAgg<D> sa;
   sagg_identity<D>(sa);
   double tcur = (k0 < a.n) ? a.t[k0] : 0.0;
+  const bool has_next = !isnan(a.t_next);      // a chunk of a longer series: step n follows at t_next
 #pragma unroll 1
   for (int64_t j = 0; j < a.L; ++j) {          // trip count uniform across the warp
     const int64_t k = k0 + j;
     const bool act = k < k1;
-    const bool last = (k + 1 >= a.n);
-    const double tn = (act && !last) ? a.t[k + 1] : tcur;
+    const bool at_end = (k + 1 >= a.n);
+    const bool last = at_end && !has_next;     // the terminal element (E = 0) only where the series ends
+    const double tn = (act && !last) ? (at_end ? a.t_next : a.t[k + 1]) : tcur;
     const double h = tn - tcur;
     tcur = tn;
     if (act && !last) {
@@ -1781,6 +1911,7 @@ ScanArgs base_args(const Plan& p, void* ws) {
   a.wagg_s = reinterpret_cast<double*>(ws_ptr(ws, p.o_waggs));
   a.llp = reinterpret_cast<double*>(ws_ptr(ws, p.o_llp));
   a.status = reinterpret_cast<int*>(ws_ptr(ws, p.o_status));
+  a.t_prev = a.t_next = NAN;
   if (p.o_adj >= 0) {
     a.rec_adj = reinterpret_cast<double*>(ws_ptr(ws, p.o_adj));
     a.tauq = reinterpret_cast<double*>(ws_ptr(ws, p.o_tauq));
@@ -1835,11 +1966,20 @@ struct BatchArgs {
   double* sr;
 };
 
+// the buffer that holds the final level-2 result: the rounds alternate
+// between the two halves of the warp-aggregate array
+const double* level2_result(const Plan& p, double* buf0, int nagg) {
+  int rounds = 0;
+  for (int64_t off = 1; off < p.P2; off <<= 1) ++rounds;
+  return (rounds & 1) ? buf0 + p.P2 * nagg : buf0;
+}
+
 // ll_only: the log-likelihood alone (reduce with the zero-start terms, level
-// 2, k_filter_llfinish) instead of the propagate pass
+// 2, k_filter_llfinish) instead of the propagate pass.  run_filter_front:
+// discretisation, levels 0-1 and level 2; run_filter_back: level 3.
 template <int D>
-void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s, const BatchArgs* bt = nullptr,
-                bool ll_only = false) {
+void run_filter_front(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s, const BatchArgs* bt,
+                      bool ll_only) {
   const int grid = (int)(p.P0 / BLOCK);
   if (bt) {
     Timed tm(s, T_DISC);
@@ -1855,7 +1995,7 @@ void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s
     if (!bt) {
       cudaFuncSetAttribute(k_discretize_rec<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem);
       k_discretize_rec<D><<<(unsigned)((p.n + DISC_BLOCK - 1) / DISC_BLOCK), DISC_BLOCK, dsmem, s>>>(
-          m, a.t, p.n, a.rec_fq, a.tauq, a.status);
+          m, a.t, p.n, a.rec_fq, a.tauq, a.status, a.t_prev);
     } else {
       cudaFuncSetAttribute(k_discretize_batched<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem);
       const int64_t thr = std::max<int64_t>(p.n, (int64_t)bt->B + 1);
@@ -1876,6 +2016,10 @@ void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s
     after_launch();
   }
   a.wfin_f = run_filter_level2<D>(p, a.wagg_f, a.status, s);
+}
+template <int D>
+void run_filter_back(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s, bool ll_only) {
+  const int grid = (int)(p.P0 / BLOCK);
   if (ll_only) {
     Timed tm(s, T_LLC);
     k_filter_llfinish<D><<<grid, BLOCK, 0, s>>>(m, a);
@@ -1891,6 +2035,12 @@ void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s
     kern<<<grid, BLOCK, psmem, s>>>(m, a);
     after_launch();
   }
+}
+template <int D>
+void run_filter(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s, const BatchArgs* bt = nullptr,
+                bool ll_only = false) {
+  run_filter_front<D>(m, p, a, s, bt, ll_only);
+  run_filter_back<D>(m, p, a, s, ll_only);
 }
 template <int D>
 void run_smoother_tail(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s) {
@@ -2226,6 +2376,150 @@ HostStage host_stage(int d, int64_t N, int64_t M) {
   return h;
 }
 }  // namespace
+
+// ===========================================================================
+// one long series split in contiguous time chunks over several GPUs
+// (Sec. 3, Prop. 1 and supplement Prop. 2: the scans over chunks are scans of
+// the same operators, so each chunk reduces to one aggregate, the aggregates
+// are exchanged, and each chunk folds the other chunks' aggregates into its
+// own scan as one element before it (filter) or after it (smoother))
+// ===========================================================================
+extern "C" int32_t pssgp_split_agg_doubles(int32_t d, int32_t smoother) {
+  if (d < 1 || d > PSSGP_DMAX) return 0;
+  const int sym = d * (d + 1) / 2;
+  return smoother ? d * d + d + sym : d * d + 2 * d + 2 * sym;
+}
+
+namespace {
+bool time_arg_ok(double t) { return std::isnan(t) || std::isfinite(t); }
+}  // namespace
+
+extern "C" int pssgp_split_filter_reduce(const pssgp_model* model, const double* t, const double* y,
+                                         const uint8_t* mask, const double* R, int32_t R_per_step, int64_t n,
+                                         double t_prev, double* agg, void* ws, size_t ws_bytes, void* stream) {
+  begin_call();
+  if (!model_ok(model) || !t || !y || !mask || !R || !agg || n < 1 || n > PSSGP_NMAX || !time_arg_ok(t_prev))
+    return PSSGP_EINVAL;
+  const Plan p = make_plan(model->d, n, 0);
+  const int rc = check_ws(p, ws, ws_bytes);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScanArgs a = base_args(p, ws);
+  a.t = t; a.y = y; a.mask = mask; a.R = R; a.R_per_step = R_per_step;
+  a.t_prev = t_prev;
+  if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess) return PSSGP_ECUDA;
+  PSSGP_DISPATCH(model->d, {
+    const DevModel<D> m = dev_model<D>(model);
+    // the log-likelihood terms of the reduce are kept, so the finishing call
+    // can take either level 3 (with or without per-step outputs)
+    run_filter_front<D>(m, p, a, s, nullptr, true);
+    // the chunk's aggregate: the inclusive level-2 result of the last warp
+    k_pack_aggregate<<<1, 128, 0, s>>>(a.wfin_f + (p.P2 - 1), p.P2, p.nf, agg);
+    after_launch();
+  });
+  return end_call();
+}
+
+extern "C" int pssgp_split_filter_finish(const pssgp_model* model, const double* t, const double* y,
+                                         const uint8_t* mask, const double* R, int32_t R_per_step, int64_t n,
+                                         const double* aggs, int32_t G, int32_t rank, double* xf, double* Pf,
+                                         int64_t ld, double* loglik, void* ws, size_t ws_bytes, void* stream) {
+  begin_call();
+  if (!model_ok(model) || !t || !y || !mask || !R || !aggs || n < 1 || n > PSSGP_NMAX || G < 1 || rank < 0 ||
+      rank >= G)
+    return PSSGP_EINVAL;
+  if ((xf || Pf) && ld < n) return PSSGP_EINVAL;
+  const Plan p = make_plan(model->d, n, 0);
+  const int rc = check_ws(p, ws, ws_bytes);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScanArgs a = base_args(p, ws);
+  a.t = t; a.y = y; a.mask = mask; a.R = R; a.R_per_step = R_per_step;
+  a.xf = xf; a.Pf = Pf; a.ld = ld;
+  a.wfin_f = level2_result(p, a.wagg_f, p.nf);
+  const bool ll_only = !xf && !Pf;
+  double* bnd = reinterpret_cast<double*>(ws_ptr(ws, p.o_bnd));
+  PSSGP_DISPATCH(model->d, {
+    const DevModel<D> m = dev_model<D>(model);
+    if (rank > 0) {   // the filter state before the chunk: chunks 0 .. rank-1 folded
+      k_fold_filter_range<D><<<1, 32, 0, s>>>(aggs, 0, rank, bnd, a.status);
+      after_launch();
+      k_apply_filter_start<D><<<(unsigned)((p.P2 + BLOCK / 32 - 1) / (BLOCK / 32)), BLOCK, 0, s>>>(
+          const_cast<double*>(a.wfin_f), p.P2, bnd, a.status);
+      after_launch();
+      a.start_f = bnd;
+    }
+    run_filter_back<D>(m, p, a, s, ll_only);
+  });
+  if (loglik) {
+    Timed tm(s, T_LL);
+    k_loglik_reduce<<<1, 256, 0, s>>>(a.llp, p.P0, loglik);
+    after_launch();
+  }
+  return end_call();
+}
+
+extern "C" int pssgp_split_smooth_reduce(const pssgp_model* model, const double* t, const double* xf,
+                                         const double* Pf, int64_t n, int64_t ld, double t_next, double* agg,
+                                         void* ws, size_t ws_bytes, void* stream) {
+  begin_call();
+  if (!model_ok(model) || !t || !xf || !Pf || !agg || n < 1 || n > PSSGP_NMAX || ld < n || !time_arg_ok(t_next))
+    return PSSGP_EINVAL;
+  const Plan p = make_plan(model->d, n, 0);
+  const int rc = check_ws(p, ws, ws_bytes);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScanArgs a = base_args(p, ws);
+  a.t = t; a.ld = ld; a.t_next = t_next;
+  const int grid = (int)(p.P0 / BLOCK);
+  if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess) return PSSGP_ECUDA;
+  PSSGP_DISPATCH(model->d, {
+    const DevModel<D> m = dev_model<D>(model);
+    {
+      Timed tm(s, T_SELEM);
+      k_smoother_elements<D><<<grid, BLOCK, 0, s>>>(m, a, xf, Pf);
+      after_launch();
+    }
+    a.wfin_s = run_smoother_level2<D>(p, a.wagg_s, s);
+    // the chunk's aggregate: the inclusive (suffix) level-2 result of warp 0
+    k_pack_aggregate<<<1, 128, 0, s>>>(a.wfin_s, p.P2, p.ns, agg);
+    after_launch();
+  });
+  return end_call();
+}
+
+extern "C" int pssgp_split_smooth_finish(const pssgp_model* model, int64_t n, int64_t ld, const double* aggs,
+                                         int32_t G, int32_t rank, double* f_mean, double* f_var, double* xs,
+                                         double* Ps, void* ws, size_t ws_bytes, void* stream) {
+  begin_call();
+  if (!model_ok(model) || !aggs || n < 1 || n > PSSGP_NMAX || ld < n || G < 1 || rank < 0 || rank >= G)
+    return PSSGP_EINVAL;
+  const Plan p = make_plan(model->d, n, 0);
+  const int rc = check_ws(p, ws, ws_bytes);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScanArgs a = base_args(p, ws);
+  a.ld = ld;
+  a.f_mean = f_mean; a.f_var = f_var; a.xs = xs; a.Ps = Ps;
+  a.wfin_s = level2_result(p, a.wagg_s, p.ns);
+  double* bnd = reinterpret_cast<double*>(ws_ptr(ws, p.o_bnd));
+  const int grid = (int)(p.P0 / BLOCK);
+  PSSGP_DISPATCH(model->d, {
+    const DevModel<D> m = dev_model<D>(model);
+    if (rank + 1 < G) {   // the smoothed state after the chunk: chunks rank+1 .. G-1 folded
+      k_fold_smoother_range<D><<<1, 32, 0, s>>>(aggs, rank + 1, G, bnd);
+      after_launch();
+      k_apply_smoother_end<D><<<(unsigned)((p.P2 + BLOCK / 32 - 1) / (BLOCK / 32)), BLOCK, 0, s>>>(
+          const_cast<double*>(a.wfin_s), p.P2, bnd);
+      after_launch();
+      a.end_s = bnd;
+    }
+    Timed tm(s, T_SPROP);
+    k_smoother_propagate<D><<<grid, BLOCK, 0, s>>>(m, a);
+    after_launch();
+  });
+  return end_call();
+}
 
 extern "C" size_t pssgp_predict_host_workspace_size(int32_t d, int64_t N, int64_t M) {
   if (d < 1 || d > PSSGP_DMAX || N < 1 || M < 0 || N > PSSGP_NMAX || M > PSSGP_NMAX) return 0;

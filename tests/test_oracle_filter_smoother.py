@@ -267,3 +267,31 @@ def test_merge_brute_force(seed):
     np.testing.assert_array_equal(ym, [r[2] for r in ref])
     np.testing.assert_array_equal(t[tp], ts)
     assert np.all(mask[tp] == 0) and np.all(np.diff(tp) > 0)
+
+
+@pytest.mark.parametrize("kind", ["matern32", "rbf"])
+def test_filter_from_a_start_state(oracle_lib, kind):
+    """kalman_filter_from (the filter of a piece of a series given the state
+    before it): with the start (0, anything) and the first transition
+    F = 0, Q = P_inf it is kalman_filter; started from the filter state at
+    step s-1 of a whole run, on steps s.. with their transitions, it gives the
+    whole run's states there, and the two log-likelihoods add up to the whole
+    (prediction-error decomposition, Sec. 2)."""
+    s = wl.random_series(81, 3000, 300, T=40.0)
+    t, y, mask, _ = oracle.merge(s.t_train, s.y_train, s.t_test)
+    m = om.make_model(kind, 0.8, 1.3)
+    F, Q = oracle.discretize(m, t)
+    mo, Po, mp, Pp, ll = oracle.kalman_filter(m, F, Q, y, mask, 0.02)
+    d = m.d
+    rng = np.random.default_rng(82)
+    Z = rng.normal(size=(d, d))
+    mo2, Po2, _, _, ll2 = oracle.kalman_filter_from(m, np.zeros(d), Z @ Z.T + np.eye(d), F, Q, y, mask, 0.02)
+    assert np.array_equal(mo2, mo) and np.array_equal(Po2, Po) and ll2 == ll
+    for split in (1, 1234, 3299):
+        a_m, a_P, _, _, a_ll = oracle.kalman_filter(m, F[:split], Q[:split], y[:split], mask[:split], 0.02)
+        b_m, b_P, _, _, b_ll = oracle.kalman_filter_from(m, a_m[-1], a_P[-1], F[split:], Q[split:], y[split:],
+                                                         mask[split:], 0.02)
+        sd = np.sqrt(np.einsum("kii->ki", Po[split:]))
+        assert np.max(np.abs(b_m - mo[split:]) / np.maximum(np.abs(mo[split:]), sd)) < 1e-12
+        assert np.max(np.abs(b_P - Po[split:]) / (sd[:, :, None] * sd[:, None, :])) < 1e-12
+        assert abs(a_ll + b_ll - ll) <= 1e-12 * max(abs(ll), 1.0)

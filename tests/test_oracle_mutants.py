@@ -37,6 +37,9 @@ MUTANTS = [
     ("vanloan_Q_order", "mm(d, d, d, F, E12, Q);", "mm(d, d, d, E12, F, Q);"),
     ("smoother_combine_transposed", "mm(d, d, d, Ei, Lj, T);\n  tr(d, d, Ei, Eit);\n  mm(d, d, d, T, Eit, L);",
      "tr(d, d, Ei, Eit);\n  mm(d, d, d, Eit, Lj, T);\n  mm(d, d, d, T, Ei, L);"),
+    ("filter_from_ignores_start_mean", "load(1, d, x0_, m);", "for (int i = 0; i < d; ++i) m[i] = 0.0L;"),
+    ("filter_from_drops_start_cov", "mm(d, d, d, FP, Ft, Pp);                       /* P^- = F P F^T + Q  */",
+     "mm(d, d, d, FP, Ft, Pp);                       /* P^- = F P F^T + Q  */\n    if (k == 0) memset(Pp, 0, sizeof(Pp));"),
 ]
 
 
@@ -77,6 +80,12 @@ def _battery():
         r = oracle.filter_combine(seg[0], oracle.filter_combine(seg[1], oracle.filter_combine(seg[2], seg[3])))
         for u, v in zip(l, r):
             assert np.abs(u - v).max() < 1e-11 * max(1.0, np.abs(v).max())
+        # the filter of the steps after a split, from the filter state there
+        _, _, _, _, lla = oracle.kalman_filter(m, res.F[:60], res.Q[:60], y[:60], mask[:60], 0.02)
+        mo2, Po2, _, _, llb = oracle.kalman_filter_from(m, res.m[59], res.P[59], res.F[60:], res.Q[60:], y[60:],
+                                                        mask[60:], 0.02)
+        assert np.abs(mo2 - res.m[60:]).max() < 1e-11 and np.abs(Po2 - res.P[60:]).max() < 1e-11
+        assert abs(lla + llb - res.loglik) < 1e-11 * max(1.0, abs(res.loglik))
         E, g, L = oracle.smoother_elements(res.F, res.Q, res.m, res.P)
         acc = (E[-1], g[-1], L[-1])
         for k in range(n - 2, n - 30, -1):
