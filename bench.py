@@ -40,6 +40,7 @@ METRIC = "filter+smoother time steps/s at N=2^20,d=6 FP64"
 PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1332.9, "filter_reduce": 796.7, "discretize": 415.2,
                                 "smoother_propagate": 682.3}
 UNIT = "steps/s"
+BATCH_SIM_SEED = 300          # prior simulation of the batched workload (family i: seed + i)
 WORKLOADS = {
     "rbf6": dict(kind="rbf", order=6, lengthscale=1.0, variance=1.0, noise=0.01),
     "matern52": dict(kind="matern52", order=0, lengthscale=1.0, variance=1.0, noise=0.01),
@@ -62,9 +63,11 @@ def parse():
                          "(measured at 2^20 RBF-6: 2 -> 196, 3 -> 204, 4 -> 206, 6 -> 206 M steps/s)")
     ap.add_argument("--no-fit", action="store_true", help="skip the learned-vs-plain fit and Table-1 measurements")
     ap.add_argument("--no-gradient", action="store_true", help="skip the log-likelihood gradient measurement")
-    ap.add_argument("--fit-adam", action="store_true", help="also time the Adam fits (about a minute)")
+    ap.add_argument("--no-fit-adam", action="store_true", help="skip the Adam fits (about a minute and a half)")
     ap.add_argument("--profile", default="", choices=["", "grad", "batched", "batched_grad", "learn"],
                     help="run one small case 3 times for a profiler and exit (no JSON line)")
+    ap.add_argument("--split-series", action="store_true",
+                    help="one long series split in contiguous time chunks over the GPUs (strong scaling)")
     ap.add_argument("--n-train", type=int, default=0,
                     help="profile a prefix of the workload with this many training points (0 = full 2^20)")
     return ap.parse_args()
@@ -368,18 +371,23 @@ def batched_bench(args, P, wl, dev, barrier, world, rank):
     family), autotuned lane counts, both families replayed as one CUDA graph
     per evaluation; inputs resident in HBM."""
     import torch
-    bt = wl.series_batch(**dict(wl.BATCH, seed=wl.BATCH["seed"] + rank))
-    kinds = np.array(bt.kind)
+    offs, kinds, params = wl.prior_batch_spec(**dict(wl.PRIOR_BATCH, seed=wl.PRIOR_BATCH["seed"] + rank))
+    kinds = np.array(kinds)
+    B_all = offs.size - 1
     parts = []
-    for kind in ("matern32", "matern52"):
-        sub = wl.subset(bt, np.flatnonzero(kinds == kind))
+    for fi, kind in enumerate(("matern32", "matern52")):
+        off, par = wl.subset_spec(offs, params, np.flatnonzero(kinds == kind))
         m = P.build_model(kind, 1.0, 1.0)
-        d = dict(kind=kind, m=m, n=sub.t.size, B=sub.B,
-                 off=torch.as_tensor(sub.offsets, device=dev), par=torch.as_tensor(sub.params(), device=dev),
-                 t=torch.as_tensor(sub.t, device=dev), y=torch.as_tensor(sub.y, device=dev),
-                 mask=torch.ones(sub.t.size, dtype=torch.uint8, device=dev))
+        offd = torch.as_tensor(off, device=dev)
+        pard = torch.as_tensor(par, device=dev)
+        # y drawn from the state-space prior of the series' own model (the
+        # library's simulation: Poisson time grid of mean spacing 0.01)
+        t, y, st = P.simulate_prior(m, offd, pard, seed=BATCH_SIM_SEED + fi + 10 * rank)
+        assert int(st.item()) == 0, "prior simulation status"
+        d = dict(kind=kind, m=m, n=t.numel(), B=off.size - 1, off=offd, par=pard, t=t, y=y,
+                 mask=torch.ones(t.numel(), dtype=torch.uint8, device=dev))
         d["ws"] = P.workspace(m.d, d["n"], dev)
-        d["ll"] = torch.empty(sub.B, dtype=torch.float64, device=dev)
+        d["ll"] = torch.empty(d["B"], dtype=torch.float64, device=dev)
         parts.append(d)
     tuning = {}
     for d in parts:
@@ -422,11 +430,12 @@ def batched_bench(args, P, wl, dev, barrier, world, rank):
     per = P.timing(2)
     P.timing(0)
     n_all = sum(d["n"] for d in parts)
-    return {"workload": "4,096 series, lengths log-uniform [1000, 65536], times U[0, 0.01 n], Matern-3/2 / 5/2 "
-                        "mixed, l log-uniform [0.1, 10], s2 = 1, R log-uniform [1e-3, 1e-1]; log-likelihood of "
+    return {"workload": "4,096 series, lengths log-uniform [1000, 65536], Matern-3/2 / 5/2 mixed, l log-uniform "
+                        "[0.1, 10], s2 = 1, R log-uniform [1e-3, 1e-1], times and y drawn from the SSGP prior of "
+                        "each series (Poisson grid of mean spacing 0.01, pssgp_simulate_prior); log-likelihood of "
                         "every series, one pssgp_loglik_batched per family, replayed as one CUDA graph",
-            "series": bt.B, "steps_total": int(n_all), "ms_per_eval": ms,
-            "series_per_s": job_throughput(bt.B, world, ms), "steps_per_s": job_throughput(n_all, world, ms),
+            "series": B_all, "steps_total": int(n_all), "ms_per_eval": ms,
+            "series_per_s": job_throughput(B_all, world, ms), "steps_per_s": job_throughput(n_all, world, ms),
             "tuning": tuning, "gpu_launches_per_eval": int(sum(c for _, c in per.values())),
             "kernels_ms": {k: round(v[0], 4) for k, v in per.items()},
             "l2": "inputs and workspace ~17 GB per evaluation, far above the 126 MB L2"}
@@ -503,13 +512,18 @@ def fit_bench(args, P, wl):
            "train_s": round(train_s, 3), "train_loss_final": float(losses[-64:].mean().item()),
            "heldout_steps": int(ho[-1])}
     runs = [("lbfgs", dict(method="lbfgs", patience=3, tol=1e-9, max_iter=500, check_every=1))]
-    if args.fit_adam:
+    if not args.no_fit_adam:
         runs.append(("adam", dict(method="adam", patience=10, tol=1e-7, max_iter=2000, check_every=1)))
     for name, kw in runs:
-        r = L.compare_fits(net, m, ho, t, y, **kw)
-        out[name] = {"plain": r["plain"], "learned": r["learned"],
+        r = L.compare_fits(net, m, ho, t, y, order="abba", **kw)
+        gain = r["plain"]["gpu_s"] - r["learned"]["gpu_s"]
+        out[name] = {"plain": r["plain"], "learned": r["learned"], "order": r["order"],
                      "speedup": round(r["plain"]["gpu_s"] / r["learned"]["gpu_s"], 3),
                      "learned_within_1e-3_nats_per_point": r["learned_within_1e-3_nats_per_point"],
+                     # the network's training is paid once; one batch of 4,096
+                     # series costs train_s + learned gpu_s with the learned start
+                     "learned_plus_training_gpu_s_one_batch": round(train_s + r["learned"]["gpu_s"], 3),
+                     "break_even_batches": (round(train_s / gain, 2) if gain > 0 else None),
                      "options": kw}
     del t, y
     torch.cuda.empty_cache()
@@ -812,6 +826,102 @@ def profile_case(args):
     return 0
 
 
+def run_split(args, wl_params):
+    """One long series split in G contiguous time chunks, one per rank
+    (strong scaling: the whole job is one 2^20 + 10^4-step workload).  Each
+    step, on every rank: pssgp_merge of the training and prediction times in
+    its time range [1000 r / G, 1000 (r+1) / G), then the exchange of
+    paper_2102_09964_b300.split (filter reduce, all-gather, filter finish,
+    smoother reduce, all-gather, log-likelihood all-reduce, smoother finish);
+    outputs: f-mean and f-var at every merged step and the total
+    log-likelihood.  Inputs resident in HBM."""
+    import torch
+    import paper_2102_09964_b300 as P
+    import workloads as wl
+    from paper_2102_09964_b300 import build as B
+    from paper_2102_09964_b300 import split as SP
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    B.build()
+    P.lib()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    s = wl.sinusoid_large()                       # the same series on every rank
+    lo, hi = 1000.0 * rank / world, 1000.0 * (rank + 1) / world
+    sel = lambda t: (t >= lo) & ((t < hi) if rank + 1 < world else (t <= hi))
+    a, b = sel(s.t_train), sel(s.t_test)
+    tt = torch.as_tensor(s.t_train[a], dtype=torch.float64, device=dev)
+    yy = torch.as_tensor(s.y_train[a], dtype=torch.float64, device=dev)
+    ts = torch.as_tensor(s.t_test[b], dtype=torch.float64, device=dev)
+    n_rank = tt.numel() + ts.numel()
+    n_total = s.N + s.M
+    m = P.build_model(wl_params["kind"], wl_params["lengthscale"], wl_params["variance"],
+                      order=wl_params["order"] or 6)
+    R = wl_params["noise"]
+    ws = P.workspace(m.d, n_rank, dev)
+    mws = P._empty(256, dtype=torch.uint8, device=dev)
+
+    def step():
+        t, y, mask, _, _ = P.merge(tt, yy, ts, ws=mws)
+        gen = SP.chunk_protocol(SP.LibraryChunk(m, t, y, mask, R, ws=ws), rank, world)
+        return SP.run_distributed(gen) if world > 1 else SP.run_lockstep([gen])[0]
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        fm, fv, ll = step()
+    torch.cuda.synchronize()
+    assert P.status(ws) == 0 and P.status(mws) == 0, "device status error"
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    P.timing(1)
+    step()
+    torch.cuda.synchronize()
+    per = P.timing(2)
+    P.timing(0)
+    # + the kernels the timing slots do not cover: two aggregate packs, and a
+    # fold and an apply per exchange direction that has other chunks
+    launches = sum(c for _, c in per.values()) + 2 + 2 * (rank > 0) + 2 * (rank + 1 < world)
+    line = {"metric": METRIC, "value": n_total / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: one series of 2^20 training + 10^4 prediction times split in "
+                                   f"{world} contiguous time chunks (one per GPU); merge + filter + smoother + "
+                                   "log-likelihood, f-mean and f-var at every merged step",
+                       "merged_steps_total": int(n_total), "merged_steps_this_rank": int(n_rank),
+                       "l2": "workspace traffic ~1 GB per step exceeds the 126 MB L2 (no explicit flush)"},
+            "gpu_launches": int(launches * args.steps), "clocks": clocks,
+            "kernels_ms": {k: round(v[0], 4) for k, v in per.items()}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.profile:
@@ -819,6 +929,8 @@ def main():
     wl_params = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl_params)
+    if args.split_series:
+        return run_split(args, wl_params)
     return run_ours(args, wl_params)
 
 

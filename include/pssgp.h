@@ -173,7 +173,8 @@ int pssgp_discretize(const pssgp_model* model, const double* t, int64_t n,
 /* Parallel Kalman filter: elements (A, b, C, eta, J) with missing
  * measurements (Sec. 3), combined by the filtering operator in a two-level
  * parallel scan; x_k = b*_k, P_k = C*_k (Prop. 1).  mask[k] = 0 marks a
- * missing measurement.  R: device pointer to one noise variance (R_per_step
+ * missing measurement; a non-finite y at an observed step is taken as missing
+ * and sets PSSGP_ENAN.  R: device pointer to one noise variance (R_per_step
  * = 0) or n of them (R_per_step = 1).  Outputs (nullable): xf d x ld,
  * Pf packed x ld, loglik (one device double, the log marginal likelihood by
  * prediction-error decomposition over the observed steps). */
@@ -220,7 +221,15 @@ int pssgp_loglik(const pssgp_model* model, const double* t, const double* y,
  *    the concatenation filters every series independently.
  *  - loglik: device double[B].  ws: pssgp_workspace_size(d, n) bytes.
  *  - Device status (pssgp_get_status): PSSGP_EBATCH for bad offsets or a
- *    non-positive parameter, plus the bits of pssgp_filter. */
+ *    non-positive parameter, plus the bits of pssgp_filter.
+ *  - Failed series: a series with a parameter that is not positive and
+ *    finite (PSSGP_EBATCH), a time that is not finite (PSSGP_ENAN) or
+ *    decreases (PSSGP_EUNSORTED), or a non-finite y at an observed step
+ *    (PSSGP_ENAN) gets loglik NaN (and, in pssgp_loglik_grad_batched, a NaN
+ *    gradient row) and leaves every other series' results intact: before the
+ *    scan its parameters become unit scales, its bad times zero-length steps
+ *    and its bad observations missing ones, so nothing non-finite enters the
+ *    flat scan.  The status word carries the union of all series' bits. */
 int pssgp_loglik_batched(const pssgp_model* model, const int64_t* offsets,
                          int32_t B, const double* params, const double* t,
                          const double* y, const uint8_t* mask, int64_t n,
@@ -264,68 +273,73 @@ int pssgp_loglik_grad_batched(const pssgp_model* model, const int64_t* offsets,
  * those of chunk r-1) needs one exchange per direction:
  *   1. every rank: pssgp_split_filter_reduce -> its chunk's filter aggregate;
  *   2. all-gather the G filter aggregates (rank order) into aggs_f[G][nf];
- *   3. every rank: pssgp_split_filter_finish -> its filter outputs and the
+ *   3. every rank: pssgp_split_filter_finish -> its filter outputs, the
  *      log-likelihood of its observations given all earlier ones (the chunks
- *      before it enter its scan as one element: their aggregates folded);
+ *      before it enter its scan as one element: their aggregates folded) and,
+ *      with smoother = 1, its smoother elements (fused, as in pssgp_predict);
  *   4. every rank: pssgp_split_smooth_reduce -> its chunk's smoother aggregate;
  *   5. all-gather the G smoother aggregates into aggs_s[G][ns]; all-reduce
  *      (sum) the log-likelihoods;
  *   6. every rank: pssgp_split_smooth_finish -> its smoother outputs (the
- *      chunks after it folded into one element after its scan).
+ *      chunks after it folded into the smoothed state of its last step).
+ * Chunk r's smoother aggregate covers the elements of its steps -1 .. n-2
+ * (step -1: the last step of chunk r-1, whose filter state chunk r starts
+ * from; chunk 0 has none, the last chunk also covers its step n-1), so the
+ * chunks after r fold into the smoothed state of r's last step.
  * The first and last time of every chunk must be known to its neighbours
  * (t_prev: the time of the last step of chunk r-1; t_next: the time of the
  * first step of chunk r+1; NaN at the ends of the series).  Every rank uses
  * the same model.  Aggregates are device arrays of pssgp_split_agg_doubles
  * doubles in the library's internal (balanced) coordinates: opaque, to be
  * passed between these calls unchanged.  The workspace (pssgp_workspace_size
- * (d, n) bytes, n = the chunk's steps) carries state from each *_reduce call
- * to the matching *_finish call: use the same workspace, inputs and scan
- * tuning for both.  A *_reduce call clears the status word; a *_finish call
- * adds its bits to it.  With G = 1 the sequence is pssgp_filter followed by
- * pssgp_smooth. */
+ * (d, n) bytes, n = the chunk's steps) carries state from each call to the
+ * next: use the same workspace, inputs and scan tuning for all four.  A
+ * *_reduce call of the filter clears the status word; the other calls add
+ * their bits to it.  With G = 1 and smoother = 1 the sequence computes what
+ * pssgp_predict computes on merged inputs. */
 
 /* Doubles in one chunk aggregate: filter (smoother = 0) 2 d^2 + 3 d
  * (A, b, C, eta, J), smoother (smoother = 1) d^2 + d + d(d+1)/2 (E, g, L);
  * 0 for d outside 1..PSSGP_DMAX. */
 int32_t pssgp_split_agg_doubles(int32_t d, int32_t smoother);
 
-/* Step 1: discretises the chunk (step 0 is the transition from
- * t_prev, or the series' first step if t_prev is NaN), folds its filtering
- * elements (Sec. 3) and writes the chunk's aggregate to agg (device,
- * pssgp_split_agg_doubles(d, 0) doubles).  Other arguments as pssgp_filter
- * for the chunk's n steps. */
+/* Step 1: discretises the chunk (step 0 is the transition from t_prev, or
+ * the series' first step if t_prev is NaN), folds its filtering elements
+ * (Sec. 3) and writes the chunk's aggregate to agg (device,
+ * pssgp_split_agg_doubles(d, 0) doubles).  smoother (0 or 1): whether step 3
+ * will prepare the smoother; t_next: as above.  Other arguments as
+ * pssgp_filter for the chunk's n steps. */
 int pssgp_split_filter_reduce(const pssgp_model* model, const double* t,
                               const double* y, const uint8_t* mask,
                               const double* R, int32_t R_per_step, int64_t n,
-                              double t_prev, double* agg, void* ws,
-                              size_t ws_bytes, void* stream);
+                              double t_prev, double t_next, int32_t smoother,
+                              double* agg, void* ws, size_t ws_bytes,
+                              void* stream);
 
 /* Step 3: aggs: device array of the G chunks' filter aggregates in rank
  * order; the ones before `rank` are folded into the filter state before the
- * chunk.  Outputs as pssgp_filter (xf, Pf nullable: without both only the
- * log-likelihood is formed); loglik (nullable, one device double): the sum
- * over the chunk's observations of log p(y_k | all earlier y). */
+ * chunk.  Outputs as pssgp_filter (xf, Pf nullable; with both null and
+ * smoother = 0 only the log-likelihood is formed); loglik (nullable, one
+ * device double): the sum over the chunk's observations of
+ * log p(y_k | all earlier y).  t_next and smoother as in step 1. */
 int pssgp_split_filter_finish(const pssgp_model* model, const double* t,
                               const double* y, const uint8_t* mask,
                               const double* R, int32_t R_per_step, int64_t n,
+                              double t_next, int32_t smoother,
                               const double* aggs, int32_t G, int32_t rank,
                               double* xf, double* Pf, int64_t ld,
                               double* loglik, void* ws, size_t ws_bytes,
                               void* stream);
 
-/* Step 4: the chunk's smoothing elements (supplement Prop. 2) from its filter
- * outputs xf, Pf (as pssgp_smooth); the element of the chunk's last step is
- * the transition to t_next (or the series' last element if t_next is NaN).
- * Writes the chunk's aggregate to agg (device, pssgp_split_agg_doubles(d, 1)
- * doubles). */
-int pssgp_split_smooth_reduce(const pssgp_model* model, const double* t,
-                              const double* xf, const double* Pf, int64_t n,
-                              int64_t ld, double t_next, double* agg, void* ws,
-                              size_t ws_bytes, void* stream);
+/* Step 4 (after step 3 with smoother = 1): writes the chunk's smoother
+ * aggregate (supplement Prop. 2) to agg (device,
+ * pssgp_split_agg_doubles(d, 1) doubles). */
+int pssgp_split_smooth_reduce(const pssgp_model* model, int64_t n, double* agg,
+                              void* ws, size_t ws_bytes, void* stream);
 
 /* Step 6: aggs: device array of the G chunks' smoother aggregates in rank
- * order; the ones after `rank` are folded into the smoothed state after the
- * chunk.  Outputs as pssgp_smooth (all nullable). */
+ * order; the ones after `rank` are folded into the smoothed state of the
+ * chunk's last step.  Outputs as pssgp_smooth (all nullable). */
 int pssgp_split_smooth_finish(const pssgp_model* model, int64_t n, int64_t ld,
                               const double* aggs, int32_t G, int32_t rank,
                               double* f_mean, double* f_var, double* xs,

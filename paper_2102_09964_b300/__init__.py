@@ -121,11 +121,11 @@ def lib():
         L.pssgp_loglik_noalloc.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, vp, vp]
         L.pssgp_split_agg_doubles.argtypes = [i32, i32]
         L.pssgp_split_agg_doubles.restype = i32
-        L.pssgp_split_filter_reduce.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, dp, vp, vp,
-                                                sz, vp]
-        L.pssgp_split_filter_finish.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, vp, i32, i32,
-                                                vp, vp, i64, vp, vp, sz, vp]
-        L.pssgp_split_smooth_reduce.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, i64, i64, dp, vp, vp, sz, vp]
+        L.pssgp_split_filter_reduce.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, dp, dp, i32,
+                                                vp, vp, sz, vp]
+        L.pssgp_split_filter_finish.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, vp, vp, i32, i64, dp, i32, vp,
+                                                i32, i32, vp, vp, i64, vp, vp, sz, vp]
+        L.pssgp_split_smooth_reduce.argtypes = [ctypes.POINTER(PssgpModel), i64, vp, vp, sz, vp]
         L.pssgp_split_smooth_finish.argtypes = [ctypes.POINTER(PssgpModel), i64, i64, vp, i32, i32, vp, vp, vp, vp,
                                                 vp, sz, vp]
         L.pssgp_timing_name.argtypes = [i32]
@@ -462,23 +462,25 @@ def split_agg_doubles(d: int, smoother: bool) -> int:
     return int(lib().pssgp_split_agg_doubles(int(d), int(bool(smoother))))
 
 
-def split_filter_reduce(model: Model, t, y, mask, R, t_prev: float, ws, agg=None):
+def split_filter_reduce(model: Model, t, y, mask, R, t_prev: float, t_next: float, ws, smoother=True, agg=None):
     """This chunk's filter aggregate (device float64[nf]); ws carries state to
-    split_filter_finish."""
+    split_filter_finish (which must get the same t_next and smoother)."""
     d, n = model.d, t.numel()
     R = _f64(R, t.device).reshape(-1)
     per = 1 if R.numel() == n and n > 1 else 0
     agg = agg if agg is not None else _empty(split_agg_doubles(d, False), dtype=torch.float64, device=t.device)
     rc = lib().pssgp_split_filter_reduce(ctypes.byref(model.raw), _ptr(t), _ptr(y), _ptr(mask), _ptr(R), per, n,
-                                         float(t_prev), _ptr(agg), _ptr(ws), ws.numel(), _stream())
+                                         float(t_prev), float(t_next), int(bool(smoother)), _ptr(agg), _ptr(ws),
+                                         ws.numel(), _stream())
     _check(rc, "pssgp_split_filter_reduce")
     return agg
 
 
-def split_filter_finish(model: Model, t, y, mask, R, aggs, rank: int, ws, outputs=True):
+def split_filter_finish(model: Model, t, y, mask, R, t_next: float, aggs, rank: int, ws, smoother=True,
+                        outputs=True):
     """Filter outputs of this chunk given every chunk's aggregate (aggs: device
-    float64[G, nf] in rank order); returns (xf, Pf, loglik[1]) with xf, Pf
-    None unless outputs."""
+    float64[G, nf] in rank order), and with smoother its smoother elements;
+    returns (xf, Pf, loglik[1]) with xf, Pf None unless outputs."""
     d, n = model.d, t.numel()
     dev = t.device
     R = _f64(R, dev).reshape(-1)
@@ -488,19 +490,18 @@ def split_filter_finish(model: Model, t, y, mask, R, aggs, rank: int, ws, output
     Pf = _empty(d * (d + 1) // 2, n, dtype=torch.float64, device=dev) if outputs else None
     ll = _empty(1, dtype=torch.float64, device=dev)
     rc = lib().pssgp_split_filter_finish(ctypes.byref(model.raw), _ptr(t), _ptr(y), _ptr(mask), _ptr(R), per, n,
-                                         _ptr(aggs), aggs.shape[0], int(rank), _ptr(xf), _ptr(Pf), n, _ptr(ll),
-                                         _ptr(ws), ws.numel(), _stream())
+                                         float(t_next), int(bool(smoother)), _ptr(aggs), aggs.shape[0], int(rank),
+                                         _ptr(xf), _ptr(Pf), n, _ptr(ll), _ptr(ws), ws.numel(), _stream())
     _check(rc, "pssgp_split_filter_finish")
     return xf, Pf, ll
 
 
-def split_smooth_reduce(model: Model, t, xf, Pf, t_next: float, ws, agg=None):
-    """This chunk's smoother aggregate (device float64[ns]); ws carries state
-    to split_smooth_finish."""
-    d, n = model.d, t.numel()
-    agg = agg if agg is not None else _empty(split_agg_doubles(d, True), dtype=torch.float64, device=t.device)
-    rc = lib().pssgp_split_smooth_reduce(ctypes.byref(model.raw), _ptr(t), _ptr(xf), _ptr(Pf), n, n, float(t_next),
-                                         _ptr(agg), _ptr(ws), ws.numel(), _stream())
+def split_smooth_reduce(model: Model, n: int, ws, agg=None, device="cuda"):
+    """This chunk's smoother aggregate (device float64[ns]), after
+    split_filter_finish with the smoother."""
+    agg = agg if agg is not None else _empty(split_agg_doubles(model.d, True), dtype=torch.float64, device=device)
+    rc = lib().pssgp_split_smooth_reduce(ctypes.byref(model.raw), int(n), _ptr(agg), _ptr(ws), ws.numel(),
+                                         _stream())
     _check(rc, "pssgp_split_smooth_reduce")
     return agg
 

@@ -477,16 +477,21 @@ __global__ void __launch_bounds__(DISC_BLOCK, (D <= 6 ? 3 : 1)) k_discretize_rec
 // (a non-empty series' first step is unique and < n); checks the parameters
 __global__ void __launch_bounds__(128) k_series_scales(double ell0, double var0, const int64_t* offsets, int B,
                                                       const double* params, int64_t n, double* su, double* sq,
-                                                      double* sr, int* status) {
+                                                      double* sr, int* sf, int* status) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B) return;
   const int64_t a = offsets[s], b = offsets[s + 1];
   if (!(b > a) || a < 0 || a >= n) return;      // empty (or invalid: flagged by k_discretize_batched)
   const double ell = params[3 * s], s2 = params[3 * s + 1], R = params[3 * s + 2];
-  if (bad_pos(ell) || bad_pos(s2) || bad_pos(R)) flag(status, PSSGP_EBATCH);
-  su[a] = ell0 / ell;
-  sq[a] = s2 / var0;
-  sr[a] = R;
+  // a series with a parameter that is not positive and finite is computed
+  // with unit scales (finite values, so that nothing non-finite can reach the
+  // other series through the scan) and flagged; its outputs become NaN
+  const bool badp = bad_pos(ell) || bad_pos(s2) || bad_pos(R);
+  if (badp) flag(status, PSSGP_EBATCH);
+  su[a] = badp ? 1.0 : ell0 / ell;
+  sq[a] = badp ? 1.0 : s2 / var0;
+  sr[a] = badp ? 1.0 : R;
+  sf[a] = badp ? PSSGP_EBATCH : 0;
 }
 
 template <int D>
@@ -494,7 +499,8 @@ __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_batched(const DevMode
                                                                  int B, const double* su, const double* sq,
                                                                  const double* sr, const double* t, int64_t n,
                                                                  double* rec, double* Rstep, uint8_t* seg,
-                                                                 double* tauq, int* status) {
+                                                                 double* tauq, const double* y,
+                                                                 const uint8_t* mask, int* sf, int* status) {
   constexpr int FQS = fqs_of<D>();
   extern __shared__ double stage[];
   const int64_t k0 = (int64_t)blockIdx.x * DISC_BLOCK;
@@ -522,10 +528,20 @@ __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_batched(const DevMode
     qscale = sq[ia];
     R = sr[ia];
     const double t1 = t[k];
-    if (nonfinite(t1)) bits |= PSSGP_ENAN;
+    int sbits = 0;
+    if (nonfinite(t1)) sbits |= PSSGP_ENAN;
     if (!first) {
       h = t1 - t[k - 1];
-      if (negative_nonzero(h)) bits |= PSSGP_EUNSORTED;
+      if (negative_nonzero(h)) sbits |= PSSGP_EUNSORTED;
+      // a bad time becomes a zero-length step (F = I, Q = 0), which keeps the
+      // scan finite; the series is flagged and its outputs become NaN
+      if (!(h >= 0.0) || nonfinite(h)) h = 0.0;
+    }
+    // an observed non-finite y is taken as missing by the filter kernels
+    if (mask[k] && nonfinite(y[k])) sbits |= PSSGP_ENAN;
+    if (sbits) {
+      atomicOr(sf + ia, sbits);
+      bits |= sbits;
     }
   }
   Mat<D> F, Q;
@@ -552,7 +568,7 @@ __global__ void __launch_bounds__(DISC_BLOCK) k_discretize_batched(const DevMode
 constexpr int SEG_WARPS = 4;   // series per 128-thread block
 __global__ void __launch_bounds__(32 * SEG_WARPS) k_segment_pieces(const double* v, int nv, int64_t n, int64_t L,
                                                                  const int64_t* offsets, int B, double* out,
-                                                                 int ostride) {
+                                                                 int ostride, const int* sf) {
   const int s = blockIdx.x * SEG_WARPS + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (s >= B) return;                                         // the whole warp
@@ -571,8 +587,10 @@ __global__ void __launch_bounds__(32 * SEG_WARPS) k_segment_pieces(const double*
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], off);
+  // a flagged series (bad parameter, time or observation) gets NaN
+  const bool failed = (b > a) && sf[a] != 0;
   if (lane == 0)
-    for (int i = 0; i < nv; ++i) out[(int64_t)s * ostride + i] = acc[i];
+    for (int i = 0; i < nv; ++i) out[(int64_t)s * ostride + i] = failed ? __longlong_as_double(0x7ff8000000000000LL) : acc[i];
 }
 unsigned segment_grid(int B) { return (unsigned)((B + SEG_WARPS - 1) / SEG_WARPS); }
 
@@ -597,7 +615,18 @@ __device__ __forceinline__ double ll_piece(int nobs, const LogProd& lp, double q
 
 // shared memory of k_filter_reduce: A (two buffers), J (packed) and eta per
 // thread, entry-major with stride BLOCK
-template <int D> constexpr int reduce_smem_doubles() { return (2 * D * D + Sym<D>::N + D) * BLOCK; }
+// For 4 <= d <= 6 the level-1 warp scan also runs in shared memory: two
+// buffers of one packed aggregate per thread, the second overlapping the
+// fold's region (the fold is done when the scan starts); 189 doubles per
+// thread (194 KB per block) at d = 6.  Below d = 4 the aggregates are small
+// enough for registers, above d = 6 the buffers would not fit.
+template <int D> __host__ __device__ constexpr bool reduce_l1_smem() { return D >= 4 && D <= 6; }
+template <int D> __host__ __device__ constexpr int reduce_fold_doubles() { return 2 * D * D + Sym<D>::N + D; }
+template <int D> constexpr int reduce_smem_doubles() {
+  return (reduce_l1_smem<D>() ? FAggSize<D>::N + (reduce_fold_doubles<D>() > FAggSize<D>::N
+                                                      ? reduce_fold_doubles<D>() : FAggSize<D>::N)
+                              : reduce_fold_doubles<D>()) * BLOCK;
+}
 
 // RMODE:
 //  RED_LL: also the log-likelihood of the chunk's observations given the
@@ -633,7 +662,10 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
   // in the others they cost more register spills than they saved
   constexpr bool VECMODE = RMODE == RED_ADJ;
   extern __shared__ double smem[];
-  double* sA0 = smem + threadIdx.x;
+  constexpr bool L1S = reduce_l1_smem<D>();
+  constexpr int NF = FAggSize<D>::N;
+  double* sB0 = smem + threadIdx.x;                    // level-1 buffer 0 (shared-memory scan)
+  double* sA0 = smem + (L1S ? NF * BLOCK : 0) + threadIdx.x;
   double* sA1 = sA0 + D * D * BLOCK;
   double* sJ = sA1 + D * D * BLOCK;
   double* seta = sJ + Sym<D>::N * BLOCK;
@@ -678,7 +710,8 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
       }
     }
     if constexpr (RMODE == RED_SMOOTH) {
-      if (k == k1 - 1 && k1 < a.n) save_fold_state<D>(a, g, Ain, seta, sJ);   // steps k0 .. k1-2
+      // steps k0 .. k1-2 (also in the last lane when the series goes on in a next chunk)
+      if (k == k1 - 1 && (k1 < a.n || !isnan(a.t_next))) save_fold_state<D>(a, g, Ain, seta, sJ);
     }
     Mat<D> F, Q;
     load_fq<D, VECMODE>(a.rec_fq, k, F, Q);
@@ -688,10 +721,11 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
         set_zero<D>(Q);
       }
     }
-    const bool obs = a.mask[k] != 0;
     const double yk = a.y[k];
     const double Rk = a.R_per_step ? a.R[k] : R0;
-    if (obs && nonfinite(yk)) bits |= PSSGP_ENAN;
+    // a non-finite observation is flagged and taken as missing
+    const bool obs = a.mask[k] != 0 && !nonfinite(yk);
+    if (a.mask[k] != 0 && nonfinite(yk)) bits |= PSSGP_ENAN;
     double S, Si, r;
     fagg_fold_step_smem<D, BLOCK>(b, C, Ain, Aout, sJ, seta, F, Q, obs, yk, Rk, bad, S, Si, r);
     if constexpr (LL) {
@@ -704,7 +738,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
     Aout = tsw;
   }
   if constexpr (RMODE == RED_SMOOTH) {
-    if (k1 == a.n && k1 > k0) save_fold_state<D>(a, g, Ain, seta, sJ);      // the lane with the last step
+    if (k1 == a.n && k1 > k0 && isnan(a.t_next)) save_fold_state<D>(a, g, Ain, seta, sJ);   // the series' last step
   }
   if constexpr (RMODE == RED_ADJ) {
     if (k1 > k0) save_fold_state<D>(a, g, Ain, seta, sJ);
@@ -719,47 +753,118 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
 #pragma unroll
     for (int e = 0; e < Sym<D>::N; ++e) a.lane_ll[(1 + D + e) * a.P0 + g] = sJ[e * BLOCK];
   }
-  FAgg<D> ag;
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    ag.b[i] = b[i];
-    ag.eta[i] = seta[i * BLOCK];
-#pragma unroll
-    for (int jj = 0; jj < D; ++jj) {
-      ag.A[i][jj] = Ain[(i * D + jj) * BLOCK];
-      ag.C[i][jj] = C[i][jj];
-      ag.J[i][jj] = sJ[(i <= jj ? pidx<D>(i, jj) : pidx<D>(jj, i)) * BLOCK];
-    }
-  }
-  if constexpr (RMODE == RED_ADJ) {
-    if (k1 > k0) {   // the transition of step k0 in front: (F, 0, Q, 0, 0) x aggregate
-      FAgg<D> T, r;
-      load_fq<D>(a.rec_fq, k0, T.A, T.C);
+  if constexpr (L1S) {
+    // the chunk aggregate, packed into buffer 0, then the level-1 scan in
+    // shared memory (partner lane's aggregate read in place, no shuffles)
+    double* B0 = sB0;
+    if constexpr (RMODE == RED_ADJ) {
+      // the transition of step k0 in front: (F, 0, Q, 0, 0) x aggregate (registers, once per lane)
+      FAgg<D> ag;
 #pragma unroll
       for (int i = 0; i < D; ++i) {
-        T.b[i] = 0.0;
-        T.eta[i] = 0.0;
+        ag.b[i] = b[i];
+        ag.eta[i] = seta[i * BLOCK];
 #pragma unroll
-        for (int j = 0; j < D; ++j) T.J[i][j] = 0.0;
+        for (int jj = 0; jj < D; ++jj) {
+          ag.A[i][jj] = Ain[(i * D + jj) * BLOCK];
+          ag.C[i][jj] = C[i][jj];
+          ag.J[i][jj] = sJ[(i <= jj ? pidx<D>(i, jj) : pidx<D>(jj, i)) * BLOCK];
+        }
       }
-      if (!fagg_combine<D>(T, ag, r)) bad = true;
-      ag = r;
+      if (k1 > k0) {
+        FAgg<D> T, r;
+        load_fq<D>(a.rec_fq, k0, T.A, T.C);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          T.b[i] = 0.0;
+          T.eta[i] = 0.0;
+#pragma unroll
+          for (int j = 0; j < D; ++j) T.J[i][j] = 0.0;
+        }
+        if (!fagg_combine<D>(T, ag, r)) bad = true;
+        ag = r;
+      }
+      store_fagg<D>(B0, BLOCK, ag);
+    } else {
+#pragma unroll
+      for (int e = 0; e < D * D; ++e) B0[e * BLOCK] = Ain[e * BLOCK];
+#pragma unroll
+      for (int i = 0; i < D; ++i) B0[(D * D + i) * BLOCK] = b[i];
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = i; j < D; ++j) B0[(D * D + D + pidx<D>(i, j)) * BLOCK] = C[i][j];
+#pragma unroll
+      for (int i = 0; i < D; ++i) B0[(D * D + D + Sym<D>::N + i) * BLOCK] = seta[i * BLOCK];
+#pragma unroll
+      for (int e = 0; e < Sym<D>::N; ++e) B0[(D * D + 2 * D + Sym<D>::N + e) * BLOCK] = sJ[e * BLOCK];
     }
-  }
-  if (a.dbg_agg) store_fagg<D>(a.dbg_agg + g, a.P0, ag);
-  // level 1: inclusive scan over the 32 lanes of the warp
+    if (a.dbg_agg) {
+      for (int e = 0; e < NF; ++e) a.dbg_agg[e * a.P0 + g] = B0[e * BLOCK];
+    }
+    __syncwarp();
+    double* cur = B0;
+    double* nxt = sA0;                // buffer 1 over the fold's region
 #pragma unroll 1
-  for (int off = 1; off < 32; off <<= 1) {
-    FAgg<D> o = ag;
-    shfl_up_fagg<D>(o, off);
-    if (lane >= off) {
-      FAgg<D> r;
-      if (!fagg_combine<D>(o, ag, r)) bad = true;
-      ag = r;
+    for (int off = 1; off < 32; off <<= 1) {
+      if (lane >= off) {
+        if (!fagg_combine_smem<D, BLOCK>(cur - off, cur, nxt)) bad = true;
+      } else {
+        for (int e = 0; e < NF; ++e) nxt[e * BLOCK] = cur[e * BLOCK];
+      }
+      __syncwarp();
+      double* tsw = cur;
+      cur = nxt;
+      nxt = tsw;
     }
+    for (int e = 0; e < NF; ++e) {
+      const double v = cur[e * BLOCK];
+      a.lagg_f[e * a.P0 + g] = v;
+      if (lane == 31) a.wagg_f[e * a.P2 + (g >> 5)] = v;
+    }
+  } else {
+    FAgg<D> ag;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      ag.b[i] = b[i];
+      ag.eta[i] = seta[i * BLOCK];
+#pragma unroll
+      for (int jj = 0; jj < D; ++jj) {
+        ag.A[i][jj] = Ain[(i * D + jj) * BLOCK];
+        ag.C[i][jj] = C[i][jj];
+        ag.J[i][jj] = sJ[(i <= jj ? pidx<D>(i, jj) : pidx<D>(jj, i)) * BLOCK];
+      }
+    }
+    if constexpr (RMODE == RED_ADJ) {
+      if (k1 > k0) {   // the transition of step k0 in front: (F, 0, Q, 0, 0) x aggregate
+        FAgg<D> T, r;
+        load_fq<D>(a.rec_fq, k0, T.A, T.C);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          T.b[i] = 0.0;
+          T.eta[i] = 0.0;
+#pragma unroll
+          for (int j = 0; j < D; ++j) T.J[i][j] = 0.0;
+        }
+        if (!fagg_combine<D>(T, ag, r)) bad = true;
+        ag = r;
+      }
+    }
+    if (a.dbg_agg) store_fagg<D>(a.dbg_agg + g, a.P0, ag);
+    // level 1: inclusive scan over the 32 lanes of the warp
+#pragma unroll 1
+    for (int off = 1; off < 32; off <<= 1) {
+      FAgg<D> o = ag;
+      shfl_up_fagg<D>(o, off);
+      if (lane >= off) {
+        FAgg<D> r;
+        if (!fagg_combine<D>(o, ag, r)) bad = true;
+        ag = r;
+      }
+    }
+    store_fagg<D>(a.lagg_f + g, a.P0, ag);
+    if (lane == 31) store_fagg<D>(a.wagg_f + (g >> 5), a.P2, ag);
   }
-  store_fagg<D>(a.lagg_f + g, a.P0, ag);
-  if (lane == 31) store_fagg<D>(a.wagg_f + (g >> 5), a.P2, ag);
   if (bad) bits |= PSSGP_ENOTPD;
   flag(a.status, bits);
 }
@@ -1003,11 +1108,12 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
     mul<D>(F, P, T);
     mul_Bt_sym_add<D>(T, F, Q, Pm);
     // the update without a branch (1/S and v are 0 on a missing step)
-    const bool obs = a.mask[k] != 0;
+    const double yk = a.y[k];
+    const bool obs = a.mask[k] != 0 && !nonfinite(yk);   // a non-finite observation is missing (flagged by the reduce)
     const double S = Pm[0][0] + (a.R_per_step ? a.R[k] : R0);
     if (obs && bad_pos(S)) bad = true;
     const double Si = obs ? __drcp_rn(S) : 0.0;
-    const double v = obs ? a.y[k] - xm[0] : 0.0;
+    const double v = obs ? yk - xm[0] : 0.0;
     if constexpr (fuse) {
       if (k == k1 - 1) {   // the prediction of the lane's last step closes the smoother chunk aggregate
 #pragma unroll
@@ -1202,7 +1308,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
           for (int j = 0; j < D; ++j) fp.V[i][j] = 0.5 * (X[i][1 + j] + X[j][1 + i]);
         }
       }
-      if (k1 < a.n) {
+      // the lane holding the chunk's last step closes like the others when
+      // the series goes on in a next chunk (which holds that step's element)
+      if (k1 < a.n || !isnan(a.t_next)) {
 #pragma unroll
         for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -1434,11 +1542,13 @@ __global__ void __launch_bounds__(BLOCK, 1) k_smoother_propagate(const DevModel<
     copy<D>(P2, Ps);
   }
   // With the fused filter pass a lane's smoother chunk is the elements
-  // k0-1 .. k1-2 (k0-1 .. n-1 in the lane with the last step), so the start
-  // above is the smoothed state of step k1-1 itself, which this lane writes;
-  // from pssgp_smooth the chunk is k0 .. k1-1 and the start is step k1's.
+  // k0-1 .. k1-2 (k0-1 .. n-1 in the lane with the series' last step), so the
+  // start above is the smoothed state of step k1-1 itself, which this lane
+  // writes; in a chunk of a longer series the next chunk holds element n-1
+  // and the end state is the smoothed state of step n-1.  From pssgp_smooth
+  // the chunk is k0 .. k1-1 and the start is step k1's.
   int64_t khi = k1 - 1;
-  if (a.fuse_smoother && k1 < a.n) {
+  if (a.fuse_smoother && (k1 < a.n || a.end_s)) {
     smooth_out<D>(m, a, k1 - 1, ms, Ps);
     khi = k1 - 2;
   }
@@ -1480,14 +1590,12 @@ __global__ void __launch_bounds__(BLOCK, 1) k_smoother_elements(const DevModel<D
   SAgg<D> sa;
   sagg_identity<D>(sa);
   double tcur = (k0 < a.n) ? a.t[k0] : 0.0;
-  const bool has_next = !isnan(a.t_next);      // a chunk of a longer series: step n follows at t_next
 #pragma unroll 1
   for (int64_t j = 0; j < a.L; ++j) {          // trip count uniform across the warp
     const int64_t k = k0 + j;
     const bool act = k < k1;
-    const bool at_end = (k + 1 >= a.n);
-    const bool last = at_end && !has_next;     // the terminal element (E = 0) only where the series ends
-    const double tn = (act && !last) ? (at_end ? a.t_next : a.t[k + 1]) : tcur;
+    const bool last = (k + 1 >= a.n);
+    const double tn = (act && !last) ? a.t[k + 1] : tcur;
     const double h = tn - tcur;
     tcur = tn;
     if (act && !last) {
@@ -1964,6 +2072,7 @@ struct BatchArgs {
   double* su;               // [n] each: (uscale, qscale, R) of every series at its first step
   double* sq;
   double* sr;
+  int* sf;                  // [n]: error bits of every series at its first step (0: the series is fine)
 };
 
 // the buffer that holds the final level-2 result: the rounds alternate
@@ -1985,7 +2094,7 @@ void run_filter_front(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStre
     Timed tm(s, T_DISC);
     k_series_scales<<<(unsigned)((bt->B + 127) / 128), 128, 0, s>>>(bt->ell0, bt->var0, bt->offsets, bt->B,
                                                                      bt->params, p.n, bt->su, bt->sq, bt->sr,
-                                                                     a.status);
+                                                                     bt->sf, a.status);
     after_launch();
   }
   {
@@ -2001,7 +2110,7 @@ void run_filter_front(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStre
       const int64_t thr = std::max<int64_t>(p.n, (int64_t)bt->B + 1);
       k_discretize_batched<D><<<(unsigned)((thr + DISC_BLOCK - 1) / DISC_BLOCK), DISC_BLOCK, dsmem, s>>>(
           m, bt->offsets, bt->B, bt->su, bt->sq, bt->sr, a.t, p.n, a.rec_fq, bt->Rstep, bt->seg, a.tauq,
-          a.status);
+          a.y, a.mask, bt->sf, a.status);
     }
     after_launch();
   }
@@ -2239,6 +2348,7 @@ extern "C" int pssgp_loglik_batched(const pssgp_model* model, const int64_t* off
   bt.su = reinterpret_cast<double*>(ws_ptr(ws, p.o_fmean));
   bt.sq = reinterpret_cast<double*>(ws_ptr(ws, p.o_fvar));
   bt.sr = reinterpret_cast<double*>(ws_ptr(ws, p.o_tpos));
+  bt.sf = reinterpret_cast<int*>(ws_ptr(ws, p.o_t));       // the merge's time array, unused here
   a.t = t; a.y = y; a.mask = mask; a.R = bt.Rstep; a.R_per_step = 1;
   a.fuse_smoother = 0;
   a.seg_start = bt.seg;
@@ -2250,7 +2360,8 @@ extern "C" int pssgp_loglik_batched(const pssgp_model* model, const int64_t* off
   });
   {
     Timed tm(s, T_LL);
-    k_segment_pieces<<<segment_grid(B), 32 * SEG_WARPS, 0, s>>>(a.ll_step, 1, n, p.L, offsets, B, loglik, 1);
+    k_segment_pieces<<<segment_grid(B), 32 * SEG_WARPS, 0, s>>>(a.ll_step, 1, n, p.L, offsets, B, loglik, 1,
+                                                                bt.sf);
     after_launch();
   }
   return end_call();
@@ -2314,6 +2425,7 @@ extern "C" int pssgp_loglik_grad_batched(const pssgp_model* model, const int64_t
   bt.su = reinterpret_cast<double*>(ws_ptr(ws, p.o_fmean));
   bt.sq = reinterpret_cast<double*>(ws_ptr(ws, p.o_fvar));
   bt.sr = reinterpret_cast<double*>(ws_ptr(ws, p.o_tpos));
+  bt.sf = reinterpret_cast<int*>(ws_ptr(ws, p.o_t));       // the merge's time array, unused here
   a.t = t; a.y = y; a.mask = mask; a.R = bt.Rstep; a.R_per_step = 1;
   a.seg_start = bt.seg;
   a.ll_step = reinterpret_cast<double*>(ws_ptr(ws, p.o_llstep));
@@ -2327,10 +2439,10 @@ extern "C" int pssgp_loglik_grad_batched(const pssgp_model* model, const int64_t
     Timed tm(s, T_LL);
     const unsigned sg = segment_grid(B);
     if (loglik) {
-      k_segment_pieces<<<sg, 32 * SEG_WARPS, 0, s>>>(a.ll_step, 1, n, p.L, offsets, B, loglik, 1);
+      k_segment_pieces<<<sg, 32 * SEG_WARPS, 0, s>>>(a.ll_step, 1, n, p.L, offsets, B, loglik, 1, bt.sf);
       after_launch();
     }
-    k_segment_pieces<<<sg, 32 * SEG_WARPS, 0, s>>>(a.g_step, 3, n, p.L, offsets, B, grad, 3);
+    k_segment_pieces<<<sg, 32 * SEG_WARPS, 0, s>>>(a.g_step, 3, n, p.L, offsets, B, grad, 3, bt.sf);
     after_launch();
   }
   return end_call();
@@ -2396,9 +2508,11 @@ bool time_arg_ok(double t) { return std::isnan(t) || std::isfinite(t); }
 
 extern "C" int pssgp_split_filter_reduce(const pssgp_model* model, const double* t, const double* y,
                                          const uint8_t* mask, const double* R, int32_t R_per_step, int64_t n,
-                                         double t_prev, double* agg, void* ws, size_t ws_bytes, void* stream) {
+                                         double t_prev, double t_next, int32_t smoother, double* agg, void* ws,
+                                         size_t ws_bytes, void* stream) {
   begin_call();
-  if (!model_ok(model) || !t || !y || !mask || !R || !agg || n < 1 || n > PSSGP_NMAX || !time_arg_ok(t_prev))
+  if (!model_ok(model) || !t || !y || !mask || !R || !agg || n < 1 || n > PSSGP_NMAX || !time_arg_ok(t_prev) ||
+      !time_arg_ok(t_next) || (smoother != 0 && smoother != 1))
     return PSSGP_EINVAL;
   const Plan p = make_plan(model->d, n, 0);
   const int rc = check_ws(p, ws, ws_bytes);
@@ -2407,12 +2521,15 @@ extern "C" int pssgp_split_filter_reduce(const pssgp_model* model, const double*
   ScanArgs a = base_args(p, ws);
   a.t = t; a.y = y; a.mask = mask; a.R = R; a.R_per_step = R_per_step;
   a.t_prev = t_prev;
+  a.t_next = t_next;
+  a.fuse_smoother = smoother;
   if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess) return PSSGP_ECUDA;
   PSSGP_DISPATCH(model->d, {
     const DevModel<D> m = dev_model<D>(model);
-    // the log-likelihood terms of the reduce are kept, so the finishing call
-    // can take either level 3 (with or without per-step outputs)
-    run_filter_front<D>(m, p, a, s, nullptr, true);
+    // without the smoother the log-likelihood terms of the reduce are kept,
+    // so the finishing call can take either level 3 (with or without filter
+    // outputs); with it the reduce saves what the fused pass needs
+    run_filter_front<D>(m, p, a, s, nullptr, !smoother);
     // the chunk's aggregate: the inclusive level-2 result of the last warp
     k_pack_aggregate<<<1, 128, 0, s>>>(a.wfin_f + (p.P2 - 1), p.P2, p.nf, agg);
     after_launch();
@@ -2422,11 +2539,12 @@ extern "C" int pssgp_split_filter_reduce(const pssgp_model* model, const double*
 
 extern "C" int pssgp_split_filter_finish(const pssgp_model* model, const double* t, const double* y,
                                          const uint8_t* mask, const double* R, int32_t R_per_step, int64_t n,
-                                         const double* aggs, int32_t G, int32_t rank, double* xf, double* Pf,
-                                         int64_t ld, double* loglik, void* ws, size_t ws_bytes, void* stream) {
+                                         double t_next, int32_t smoother, const double* aggs, int32_t G,
+                                         int32_t rank, double* xf, double* Pf, int64_t ld, double* loglik, void* ws,
+                                         size_t ws_bytes, void* stream) {
   begin_call();
   if (!model_ok(model) || !t || !y || !mask || !R || !aggs || n < 1 || n > PSSGP_NMAX || G < 1 || rank < 0 ||
-      rank >= G)
+      rank >= G || !time_arg_ok(t_next) || (smoother != 0 && smoother != 1))
     return PSSGP_EINVAL;
   if ((xf || Pf) && ld < n) return PSSGP_EINVAL;
   const Plan p = make_plan(model->d, n, 0);
@@ -2436,8 +2554,10 @@ extern "C" int pssgp_split_filter_finish(const pssgp_model* model, const double*
   ScanArgs a = base_args(p, ws);
   a.t = t; a.y = y; a.mask = mask; a.R = R; a.R_per_step = R_per_step;
   a.xf = xf; a.Pf = Pf; a.ld = ld;
+  a.t_next = t_next;
+  a.fuse_smoother = smoother;
   a.wfin_f = level2_result(p, a.wagg_f, p.nf);
-  const bool ll_only = !xf && !Pf;
+  const bool ll_only = !smoother && !xf && !Pf;
   double* bnd = reinterpret_cast<double*>(ws_ptr(ws, p.o_bnd));
   PSSGP_DISPATCH(model->d, {
     const DevModel<D> m = dev_model<D>(model);
@@ -2459,27 +2579,17 @@ extern "C" int pssgp_split_filter_finish(const pssgp_model* model, const double*
   return end_call();
 }
 
-extern "C" int pssgp_split_smooth_reduce(const pssgp_model* model, const double* t, const double* xf,
-                                         const double* Pf, int64_t n, int64_t ld, double t_next, double* agg,
-                                         void* ws, size_t ws_bytes, void* stream) {
+extern "C" int pssgp_split_smooth_reduce(const pssgp_model* model, int64_t n, double* agg, void* ws,
+                                         size_t ws_bytes, void* stream) {
   begin_call();
-  if (!model_ok(model) || !t || !xf || !Pf || !agg || n < 1 || n > PSSGP_NMAX || ld < n || !time_arg_ok(t_next))
-    return PSSGP_EINVAL;
+  if (!model_ok(model) || !agg || n < 1 || n > PSSGP_NMAX) return PSSGP_EINVAL;
   const Plan p = make_plan(model->d, n, 0);
   const int rc = check_ws(p, ws, ws_bytes);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   ScanArgs a = base_args(p, ws);
-  a.t = t; a.ld = ld; a.t_next = t_next;
-  const int grid = (int)(p.P0 / BLOCK);
-  if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess) return PSSGP_ECUDA;
   PSSGP_DISPATCH(model->d, {
-    const DevModel<D> m = dev_model<D>(model);
-    {
-      Timed tm(s, T_SELEM);
-      k_smoother_elements<D><<<grid, BLOCK, 0, s>>>(m, a, xf, Pf);
-      after_launch();
-    }
+    // levels 0-1 ran in the fused filter pass
     a.wfin_s = run_smoother_level2<D>(p, a.wagg_s, s);
     // the chunk's aggregate: the inclusive (suffix) level-2 result of warp 0
     k_pack_aggregate<<<1, 128, 0, s>>>(a.wfin_s, p.P2, p.ns, agg);
@@ -2501,12 +2611,13 @@ extern "C" int pssgp_split_smooth_finish(const pssgp_model* model, int64_t n, in
   ScanArgs a = base_args(p, ws);
   a.ld = ld;
   a.f_mean = f_mean; a.f_var = f_var; a.xs = xs; a.Ps = Ps;
+  a.fuse_smoother = 1;
   a.wfin_s = level2_result(p, a.wagg_s, p.ns);
   double* bnd = reinterpret_cast<double*>(ws_ptr(ws, p.o_bnd));
   const int grid = (int)(p.P0 / BLOCK);
   PSSGP_DISPATCH(model->d, {
     const DevModel<D> m = dev_model<D>(model);
-    if (rank + 1 < G) {   // the smoothed state after the chunk: chunks rank+1 .. G-1 folded
+    if (rank + 1 < G) {   // the smoothed state of the chunk's last step: chunks rank+1 .. G-1 folded
       k_fold_smoother_range<D><<<1, 32, 0, s>>>(aggs, rank + 1, G, bnd);
       after_launch();
       k_apply_smoother_end<D><<<(unsigned)((p.P2 + BLOCK / 32 - 1) / (BLOCK / 32)), BLOCK, 0, s>>>(

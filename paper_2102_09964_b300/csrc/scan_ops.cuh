@@ -597,6 +597,126 @@ __device__ __noinline__ bool fagg_combine(const FAgg<D>& a, const FAgg<D>& b, FA
   return ok;
 }
 
+// fagg_combine with the operands and the result in shared memory, in the
+// packed layout of store_fagg (entry e of this thread's aggregate at
+// ptr[e * SST]), and the right-hand sides of the LU solve taken one column
+// at a time: only M's factors and a few vectors live in registers, so the
+// combine needs no local memory.  The same operations in the same order as
+// fagg_combine (bit-identical results).  o must not alias a or b; o's A
+// block holds the product A_b M^{-1} C_a while the C block is formed.
+template <int D, int SST>
+__device__ __forceinline__ bool fagg_combine_smem(const double* __restrict__ a, const double* __restrict__ b,
+                                                  double* __restrict__ o) {
+  constexpr int S = Sym<D>::N;
+  constexpr int OA = 0, OB = D * D, OC = D * D + D, OE = D * D + D + S, OJ = D * D + 2 * D + S;
+  auto A_ = [](const double* p, int i, int j) { return p[(OA + i * D + j) * SST]; };
+  auto b_ = [](const double* p, int i) { return p[(OB + i) * SST]; };
+  auto C_ = [](const double* p, int i, int j) { return p[(OC + (i <= j ? pidx<D>(i, j) : pidx<D>(j, i))) * SST]; };
+  auto e_ = [](const double* p, int i) { return p[(OE + i) * SST]; };
+  auto J_ = [](const double* p, int i, int j) { return p[(OJ + (i <= j ? pidx<D>(i, j) : pidx<D>(j, i))) * SST]; };
+  Mat<D> M;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double s = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) s = fma(C_(a, i, k), J_(b, k, j), s);
+      M[i][j] = s;
+    }
+  Vec<D> v;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double s = e_(b, i);
+#pragma unroll
+    for (int k = 0; k < D; ++k) s = fma(-J_(b, i, k), b_(a, k), s);
+    v[i] = s;
+  }
+  double X2[D][2];   // [x_b | x_v] right-hand sides
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double sb = b_(a, i), sv = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) { sb = fma(C_(a, i, k), e_(b, k), sb); sv = fma(C_(a, i, k), v[k], sv); }
+    X2[i][0] = sb;
+    X2[i][1] = sv;
+  }
+  int perm[D];
+  double invd[D];
+  const bool ok = lu_factor<D>(M, perm, invd);
+  lu_solve<D, 2>(M, perm, invd, X2);
+  // b = A_b x_b + b_b ; eta = A_a^T (v - J_b x_v) + eta_a
+  Vec<D> w;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double sb = b_(b, i);
+#pragma unroll
+    for (int k = 0; k < D; ++k) sb = fma(A_(b, i, k), X2[k][0], sb);
+    o[(OB + i) * SST] = sb;
+    double sw = v[i];
+#pragma unroll
+    for (int k = 0; k < D; ++k) sw = fma(-J_(b, i, k), X2[k][1], sw);
+    w[i] = sw;
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double s = e_(a, i);
+#pragma unroll
+    for (int k = 0; k < D; ++k) s = fma(A_(a, k, i), w[k], s);
+    o[(OE + i) * SST] = s;
+  }
+  // T = A_b M^{-1} C_a, column by column into o's A block; C = T A_b^T + C_b
+#pragma unroll 1
+  for (int j = 0; j < D; ++j) {
+    double x[D][1];
+#pragma unroll
+    for (int i = 0; i < D; ++i) x[i][0] = C_(a, i, j);
+    lu_solve<D, 1>(M, perm, invd, x);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) t = fma(A_(b, i, k), x[k][0], t);
+      o[(OA + i * D + j) * SST] = t;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) {
+      double s = C_(b, i, j);
+#pragma unroll
+      for (int k = 0; k < D; ++k) s = fma(A_(o, i, k), A_(b, j, k), s);
+      o[(OC + pidx<D>(i, j)) * SST] = s;
+    }
+  // A = A_b M^{-1} A_a and U = J_b M^{-1} A_a, column by column;
+  // J = A_a^T U + J_a (upper triangle: column j gives the rows i <= j)
+#pragma unroll 1
+  for (int j = 0; j < D; ++j) {
+    double x[D][1];
+#pragma unroll
+    for (int i = 0; i < D; ++i) x[i][0] = A_(a, i, j);
+    lu_solve<D, 1>(M, perm, invd, x);
+    Vec<D> u;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      double s = 0.0, q = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) { s = fma(A_(b, i, k), x[k][0], s); q = fma(J_(b, i, k), x[k][0], q); }
+      o[(OA + i * D + j) * SST] = s;
+      u[i] = q;
+    }
+#pragma unroll
+    for (int i = 0; i <= j; ++i) {
+      double s = J_(a, i, j);
+#pragma unroll
+      for (int k = 0; k < D; ++k) s = fma(A_(a, k, i), u[k], s);
+      o[(OJ + pidx<D>(i, j)) * SST] = s;
+    }
+  }
+  return ok;
+}
+
 // A filter state (x, P) -- a prefix aggregate, which has A = 0, eta = 0, J = 0
 // because it contains the first step -- combined with an aggregate b:
 //   M = I + P J_b,  x' = A_b M^{-1} (x + P eta_b) + b_b,

@@ -47,39 +47,43 @@ def train_network(model, offsets, params, seed: int, epochs: int = 8, batch: int
     return net, time.perf_counter() - t0, losses
 
 
-def compare_fits(net, model, offsets: np.ndarray, t, y, **fit_kw):
-    """Plain-init and learned-init fits of the same series.  Times are device
-    wall-clock around each fit (the learned one includes its features and
-    the network's forward pass).  fit_kw: options of fit_batched (the same
-    for both fits).  Returns a dict of results."""
+def compare_fits(net, model, offsets: np.ndarray, t, y, order: str = "abba", **fit_kw):
+    """Plain-init and learned-init fits of the same series with the same
+    options (fit_kw: options of fit_batched).  Each fit runs in the order
+    given (default plain, learned, learned, plain, so that neither start
+    always runs first); a fit's time is device wall clock around it (the
+    learned one includes its features and the network's forward pass), and
+    the mean over its runs is reported.  Returns a dict of results."""
     B = offsets.size - 1
     dev = t.device
     mask = torch.ones(t.numel(), dtype=torch.uint8, device=dev)
     off = torch.as_tensor(offsets, dtype=torch.int64, device=dev)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    th_p, ll_p, it_p, n_p = fit_batched(model, offsets, t, y, mask, np.zeros((B, 3)), **fit_kw)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    init = net.predict(features(off, t, y))
-    th_l, ll_l, it_l, n_l = fit_batched(model, offsets, t, y, mask, init, **fit_kw)
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
+    runs = {"plain": [], "learned": []}
+    out = {}
+    for which in {"ab": ("plain", "learned"), "ba": ("learned", "plain"),
+                  "abba": ("plain", "learned", "learned", "plain")}[order]:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        init = np.zeros((B, 3)) if which == "plain" else net.predict(features(off, t, y))
+        th, ll, it, nloop = fit_batched(model, offsets, t, y, mask, init, **fit_kw)
+        torch.cuda.synchronize()
+        runs[which].append(time.perf_counter() - t0)
+        out[which] = (ll.cpu().numpy(), int(it.sum().item()), nloop, init)
     n = np.diff(offsets).astype(np.float64)
-    llp, lll = ll_p.cpu().numpy(), ll_l.cpu().numpy()
-    return {
-        "series": B,
-        "steps_total": int(offsets[-1]),
-        "plain": {"gpu_s": t1 - t0, "series_per_s": B / (t1 - t0), "iterations_total": int(it_p.sum().item()),
-                  "loop_iterations": n_p},
-        "learned": {"gpu_s": t2 - t1, "series_per_s": B / (t2 - t1), "iterations_total": int(it_l.sum().item()),
-                    "loop_iterations": n_l},
+    (llp, itp, np_, _), (lll, itl, nl, init) = out["plain"], out["learned"]
+    res = {"series": B, "steps_total": int(offsets[-1]), "order": order}
+    for which, (it_total, nloop) in (("plain", (itp, np_)), ("learned", (itl, nl))):
+        gs = float(np.mean(runs[which]))
+        res[which] = {"gpu_s": gs, "gpu_s_runs": [round(x, 4) for x in runs[which]], "series_per_s": B / gs,
+                      "iterations_total": it_total, "loop_iterations": nloop}
+    res.update({
         "learned_within_1e-3_nats_per_point": float(np.mean(lll >= llp - 1e-3 * n)),
         "learned_better_by_1e-3_nats_per_point": float(np.mean(lll > llp + 1e-3 * n)),
-        "theta_learned_init": init.cpu().numpy(),
+        "theta_learned_init": init.cpu().numpy() if torch.is_tensor(init) else init,
         "loglik_plain": llp,
         "loglik_learned": lll,
-    }
+    })
+    return res
 
 
 def heldout_series(model, offsets: np.ndarray, params: np.ndarray, seed: int, device="cuda"):

@@ -35,9 +35,9 @@ def chunk_protocol(chunk, rank: int, G: int):
     ends = yield ("all_gather", chunk.time_ends())          # [G, 2]: first and last time of each chunk
     t_prev = float(ends[rank - 1, 1]) if rank > 0 else math.nan
     t_next = float(ends[rank + 1, 0]) if rank + 1 < G else math.nan
-    aggs_f = yield ("all_gather", chunk.filter_reduce(t_prev))
+    aggs_f = yield ("all_gather", chunk.filter_reduce(t_prev, t_next))
     ll = chunk.filter_finish(aggs_f, rank)
-    aggs_s = yield ("all_gather", chunk.smooth_reduce(t_next))
+    aggs_s = yield ("all_gather", chunk.smooth_reduce())
     ll_total = yield ("all_reduce_sum", ll)
     f_mean, f_var = chunk.smooth_finish(aggs_s, rank)
     return f_mean, f_var, ll_total
@@ -107,26 +107,31 @@ def run_lockstep(gens):
 class LibraryChunk:
     """One rank's chunk on its GPU: sorted times t, observations y, mask (1
     observed, 0 missing), noise variance R (scalar or per step); device
-    tensors.  The workspace carries each reduce call's state to its finish
-    call."""
+    tensors.  The workspace carries each call's state to the next.  The
+    filter pass also forms the smoother elements (fused, as in the prediction
+    path); with `filter_outputs` it writes the filter states too."""
 
-    def __init__(self, model: Model, t, y, mask, R, ws=None):
+    def __init__(self, model: Model, t, y, mask, R, ws=None, filter_outputs=False):
         self.model, self.t, self.y, self.mask, self.R = model, t, y, mask, R
         self.ws = ws if ws is not None else workspace(model.d, t.numel(), t.device)
+        self.filter_outputs = filter_outputs
         self.xf = self.Pf = None
+        self.t_next = math.nan
 
     def time_ends(self):
         return torch.stack([self.t[0], self.t[-1]])
 
-    def filter_reduce(self, t_prev: float):
-        return split_filter_reduce(self.model, self.t, self.y, self.mask, self.R, t_prev, self.ws)
+    def filter_reduce(self, t_prev: float, t_next: float):
+        self.t_next = t_next
+        return split_filter_reduce(self.model, self.t, self.y, self.mask, self.R, t_prev, t_next, self.ws)
 
     def filter_finish(self, aggs, rank: int):
-        self.xf, self.Pf, ll = split_filter_finish(self.model, self.t, self.y, self.mask, self.R, aggs, rank, self.ws)
+        self.xf, self.Pf, ll = split_filter_finish(self.model, self.t, self.y, self.mask, self.R, self.t_next, aggs,
+                                                   rank, self.ws, outputs=self.filter_outputs)
         return ll
 
-    def smooth_reduce(self, t_next: float):
-        return split_smooth_reduce(self.model, self.t, self.xf, self.Pf, t_next, self.ws)
+    def smooth_reduce(self):
+        return split_smooth_reduce(self.model, self.t.numel(), self.ws, device=self.t.device)
 
     def smooth_finish(self, aggs, rank: int):
         fm, fv, _, _ = split_smooth_finish(self.model, self.t.numel(), aggs, rank, self.ws, device=self.t.device)

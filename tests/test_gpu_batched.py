@@ -228,3 +228,70 @@ def test_graph_replay_with_new_parameters():
             sub = wl.subset(d["sub"], np.arange(d["sub"].B))
             sub.lengthscale = sub.lengthscale * scale
             check_series(kind, sub, got, idx=[0, sub.B - 1])
+
+
+@pytest.mark.parametrize("kind", ["matern32", "matern52"])
+def test_failed_series_are_nan_and_leave_the_others_intact(kind):
+    """A series with a NaN observation, one with a non-positive lengthscale
+    and one whose times decrease, inside a batch of healthy series: the three
+    get NaN log-likelihoods and gradients, the status word carries their bits,
+    and every healthy series (including those after the bad ones in the flat
+    scan) still matches the oracle."""
+    bt = wl.series_batch(seed=45, lengths=[3000, 2500, 4000, 1800, 2200, 5000, 700], kinds=(kind,))
+    params = bt.params().copy()
+    t, y = bt.t.copy(), bt.y.copy()
+    y[bt.offsets[1] + 100] = np.nan                    # series 1: a non-finite observation
+    params[3, 0] = -1.0                                # series 3: a negative lengthscale
+    a4 = bt.offsets[4]
+    t[a4 + 50] = t[a4 + 49] - 1.0                      # series 4: the times decrease
+    bad = {1, 3, 4}
+    m = P.build_model(kind, 1.0, 1.0)
+    n = t.size
+    args = (dev(bt.offsets, torch.int64), dev(params), dev(t), dev(y), dev(np.ones(n, np.uint8), torch.uint8))
+    ll, ws = P.loglik_batched(m, *args)
+    st = P.status(ws)
+    assert st & P.ENAN and st & P.EBATCH and st & P.EUNSORTED
+    llg, g, wsg = P.loglik_grad_batched(m, *args)
+    stg = P.status(wsg)
+    assert stg & P.ENAN and stg & P.EBATCH and stg & P.EUNSORTED
+    ll, llg, g = ll.cpu().numpy(), llg.cpu().numpy(), g.cpu().numpy()
+    for s in range(bt.B):
+        if s in bad:
+            assert np.isnan(ll[s]) and np.isnan(llg[s]) and np.all(np.isnan(g[s])), s
+            continue
+        a, b = bt.offsets[s], bt.offsets[s + 1]
+        rll, rg, sc = oracle.loglik_grad_fwd(kind, bt.lengthscale[s], bt.variance[s], t[a:b], y[a:b],
+                                             np.ones(b - a, np.uint8), bt.noise[s], with_scale=True)
+        assert abs(ll[s] - rll) <= TOL[kind] * max(abs(rll), b - a), (s, ll[s], rll)
+        assert abs(llg[s] - rll) <= TOL[kind] * max(abs(rll), b - a), (s, llg[s], rll)
+        floor = np.maximum(sc / np.sqrt(b - a), 1e-5 * np.sqrt(b - a))
+        assert np.max(np.abs(g[s] - rg) / np.maximum(np.abs(rg), floor)) <= 1e-8, (s, g[s], rg)
+
+
+def test_batched_prior_workload_sampled():
+    """The benchmark's 4,096-series workload with y drawn from the prior
+    (the library's simulation, seeds as in the benchmark), one call per
+    family; sampled series against the oracle on the oracle's own simulation
+    of the same series (Philox4x32-10 on both sides)."""
+    offs, kinds, params = wl.prior_batch_spec(**wl.PRIOR_BATCH)
+    kinds = np.array(kinds)
+    rng = np.random.default_rng(46)
+    for fi, kind in enumerate(("matern32", "matern52")):
+        off, par = wl.subset_spec(offs, params, np.flatnonzero(kinds == kind))
+        m = P.build_model(kind, 1.0, 1.0)
+        offd = dev(off, torch.int64)
+        seed = 300 + fi
+        t, y, st = P.simulate_prior(m, offd, dev(par), seed=seed)
+        assert int(st.item()) == 0
+        ll, ws = P.loglik_batched(m, offd, dev(par), t, y, torch.ones(t.numel(), dtype=torch.uint8, device="cuda"))
+        assert P.status(ws) == 0
+        ll = ll.cpu().numpy()
+        assert np.all(np.isfinite(ll))
+        lens = np.diff(off)
+        pick = sorted({int(np.argmin(lens)), int(np.argmax(lens)), *rng.choice(lens.size, 2, replace=False).tolist()})
+        for s in pick:
+            n = int(lens[s])
+            mo = om.make_model(kind, par[s, 0], par[s, 1])
+            rt, ry = oracle.simulate_series(mo, par[s, 2], n, seed, s)
+            ref = oracle.run(mo, rt, ry, np.ones(n, np.uint8), par[s, 2]).loglik
+            assert abs(ll[s] - ref) <= TOL[kind] * max(abs(ref), n), (kind, s, ll[s], ref)

@@ -41,9 +41,10 @@ def merged(seed, n_train, n_test, T):
     return oracle.merge(s.t_train, s.y_train, s.t_test)[:3]
 
 
-def run_split(m, t, y, mask, R, bounds):
+def run_split(m, t, y, mask, R, bounds, filter_outputs=False):
     G = len(bounds)
-    chunks = [split.LibraryChunk(m, dev(t[a:b]), dev(y[a:b]), dev(mask[a:b], torch.uint8), R) for a, b in bounds]
+    chunks = [split.LibraryChunk(m, dev(t[a:b]), dev(y[a:b]), dev(mask[a:b], torch.uint8), R,
+                                 filter_outputs=filter_outputs) for a, b in bounds]
     res = split.run_lockstep([split.chunk_protocol(c, r, G) for r, c in enumerate(chunks)])
     for c in chunks:
         assert P.status(c.ws) == 0
@@ -105,7 +106,7 @@ def test_split_filter_states_equal_the_unsplit_filter(kind, report):
     assert P.status(ws) == 0
     xf, Pf = xf.cpu().numpy(), Pf.cpu().numpy()
     bounds = split.chunk_bounds(t.size, 3)
-    _, _, lls, chunks = run_split(m, t, y, mask, 0.01, bounds)
+    _, _, lls, chunks = run_split(m, t, y, mask, 0.01, bounds, filter_outputs=True)
     d = m.d
     pidx = [(i, j) for i in range(d) for j in range(i, d)]
     diag = [e for e, (i, j) in enumerate(pidx) if i == j]
@@ -118,12 +119,16 @@ def test_split_filter_states_equal_the_unsplit_filter(kind, report):
         worst = max(worst, dx, dP)
     report(f"split filter states vs unsplit library filter, {kind}", worst, 1e-9)
     assert worst <= 1e-9
-    # log-likelihood only (no per-step outputs): the chunk sums of reading r21
+    # log-likelihood only (no per-step outputs, no smoother): the chunk sums of reading r21
     tot = 0.0
-    aggs = torch.stack([c.filter_reduce(float("nan") if r == 0 else float(t[bounds[r - 1][1] - 1]))
-                        for r, c in enumerate(chunks)])
+    nan = float("nan")
+    ends = [(nan if r == 0 else float(t[bounds[r - 1][1] - 1]), nan if r + 1 == len(bounds) else float(t[b]))
+            for r, (a, b) in enumerate(bounds)]
+    aggs = torch.stack([P.split_filter_reduce(m, c.t, c.y, c.mask, c.R, tp, tn, c.ws, smoother=False)
+                        for c, (tp, tn) in zip(chunks, ends)])
     for r, c in enumerate(chunks):
-        _, _, llr = P.split_filter_finish(m, c.t, c.y, c.mask, c.R, aggs, r, c.ws, outputs=False)
+        _, _, llr = P.split_filter_finish(m, c.t, c.y, c.mask, c.R, ends[r][1], aggs, r, c.ws, smoother=False,
+                                          outputs=False)
         assert P.status(c.ws) == 0
         tot += float(llr.item())
     assert abs(tot - float(ll.item())) <= 1e-11 * max(abs(float(ll.item())), t.size)

@@ -61,8 +61,9 @@ class OracleChunk:
     def time_ends(self):
         return torch.tensor([self.t[0], self.t[-1]], dtype=torch.float64)
 
-    def filter_reduce(self, t_prev):
+    def filter_reduce(self, t_prev, t_next):
         m, n = self.m, self.t.size
+        self.t_next = t_next
         if math.isnan(t_prev):
             self.F, self.Q = oracle.discretize(m, self.t)
             el = oracle.filter_elements(m, self.F, self.Q, self.y, self.mask, self.R)
@@ -93,8 +94,8 @@ class OracleChunk:
                                                                    self.mask, self.R)
         return torch.tensor([ll], dtype=torch.float64)
 
-    def smooth_reduce(self, t_next):
-        m, n = self.m, self.t.size
+    def smooth_reduce(self):
+        m, n, t_next = self.m, self.t.size, self.t_next
         if math.isnan(t_next):
             self.el = oracle.smoother_elements(self.F, self.Q, self.mo, self.Po)
         else:

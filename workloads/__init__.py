@@ -169,6 +169,36 @@ def prior_spec(seed: int, B: int, n: int | None = None, n_min: int | None = None
     return offsets, params
 
 
+def prior_batch_spec(seed: int = 3, B: int = 4096, n_min: int = 1000, n_max: int = 65536):
+    """The batched workload with its y drawn from the state-space prior: per
+    series the length (log-uniform on [n_min, n_max]), the kernel family
+    (Matern-3/2 or 5/2, each with probability 1/2) and (lengthscale, variance,
+    noise variance) = (log-uniform [0.1, 10], 1, log-uniform [1e-3, 1e-1]).
+    The times and y are drawn by a prior simulation (Poisson time grid of mean
+    spacing 0.01), which this module does not do.  Returns (offsets
+    int64[B+1], kinds list[B], params float64[B, 3])."""
+    rng = np.random.default_rng(seed)
+    lengths = np.rint(np.exp(rng.uniform(np.log(n_min), np.log(n_max), B))).astype(np.int64)
+    offsets = np.zeros(B + 1, dtype=np.int64)
+    np.cumsum(lengths, out=offsets[1:])
+    kinds = [("matern32", "matern52")[i] for i in rng.integers(0, 2, B)]
+    params = np.stack([np.exp(rng.uniform(np.log(0.1), np.log(10.0), B)), np.ones(B),
+                       np.exp(rng.uniform(np.log(1e-3), np.log(1e-1), B))], axis=1)
+    return offsets, kinds, params
+
+
+PRIOR_BATCH = dict(seed=3, B=4096, n_min=1000, n_max=65536)
+
+
+def subset_spec(offsets: np.ndarray, params: np.ndarray, idx):
+    """Offsets and parameter rows of the series idx, re-concatenated in that order."""
+    idx = np.asarray(idx, dtype=np.int64)
+    lengths = offsets[idx + 1] - offsets[idx]
+    off = np.zeros(idx.size + 1, dtype=np.int64)
+    np.cumsum(lengths, out=off[1:])
+    return off, params[idx].copy()
+
+
 # The learned-initialisation workload: Matern-5/2 prior series, mean spacing
 # 0.01 (a Poisson time grid), log-uniform hyperparameters.
 LEARN_TRAIN = dict(seed=50, B=1_000_000, n=4096)
