@@ -563,6 +563,22 @@ int pssgp_mlp_grad(void* state, const float* feat, const double* theta,
 /* One Adam step (0.9, 0.999, 1e-8; step counts from 1) on the parameters. */
 int pssgp_mlp_adam(void* state, const float* grad, float lr, int32_t step,
                    void* stream);
+/* The network's GEMMs run on the 5th-generation tensor cores (tcgen05.mma
+ * with the accumulator in tensor memory, operands loaded by TMA) unless
+ * path = 1 selects the legacy mma.sync kernel (kept as a checked baseline).
+ * Affects calls made afterwards.  A GEMM whose waits time out sets a word in
+ * the workspace instead of hanging; PSSGP_ECUDA if a TMA descriptor cannot be
+ * made. */
+int pssgp_mlp_set_gemm(int32_t path);
+
+/* Diagnostic: C[M][N] = A[M][K] B[N][K]^T (device bf16 row-major inputs, K a
+ * multiple of 8; C device float row-major) with the GEMM of `path` (0
+ * tcgen05, 1 mma.sync); *err (device int32) is cleared, and set to 1 if the
+ * tcgen05 kernel's waits timed out. */
+int pssgp_debug_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N,
+                          int32_t K, float* C, int32_t path, int32_t* err,
+                          void* stream);
+
 /* Proposed log hyperparameters (device double[rows][3]); a row with a
  * non-finite feature, or whose standardised output is not finite or lies
  * more than 4 standard deviations

@@ -128,6 +128,8 @@ def lib():
         L.pssgp_split_smooth_reduce.argtypes = [ctypes.POINTER(PssgpModel), i64, vp, vp, sz, vp]
         L.pssgp_split_smooth_finish.argtypes = [ctypes.POINTER(PssgpModel), i64, i64, vp, i32, i32, vp, vp, vp, vp,
                                                 vp, sz, vp]
+        L.pssgp_mlp_set_gemm.argtypes = [i32]
+        L.pssgp_debug_gemm_bf16.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, vp]
         L.pssgp_timing_name.argtypes = [i32]
         L.pssgp_timing_name.restype = ctypes.c_char_p
         if L.pssgp_model_bytes() != ctypes.sizeof(PssgpModel):
@@ -547,6 +549,24 @@ def debug_filter_aggregates(model: Model, t, y, mask, R, lanes: int = 0):
         out.append((a[:d * d].reshape(d, d), a[d * d:d * d + d], a[d * d + d:2 * d * d + d].reshape(d, d),
                     a[2 * d * d + d:2 * d * d + 2 * d], a[2 * d * d + 2 * d:].reshape(d, d)))
     return out, first[:P0], status(ws)
+
+
+def mlp_set_gemm(path: int):
+    """0: the network's GEMMs on tcgen05 (default); 1: the mma.sync baseline."""
+    _check(lib().pssgp_mlp_set_gemm(int(path)), "pssgp_mlp_set_gemm")
+
+
+def debug_gemm_bf16(A, B, path: int = 0):
+    """C = A B^T (A: bf16 [M, K], B: bf16 [N, K], device) in float32 with the
+    chosen GEMM; returns (C, err) with err the kernel's timeout flag."""
+    A, B = A.contiguous(), B.contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    C = _empty(M, N, dtype=torch.float32, device=A.device)
+    err = torch.full((1,), -1, dtype=torch.int32, device=A.device)
+    _check(lib().pssgp_debug_gemm_bf16(_ptr(A), _ptr(B), M, N, K, _ptr(C), int(path), _ptr(err), _stream()),
+           "pssgp_debug_gemm_bf16")
+    return C, err
 
 
 def fp64_fma_rate() -> float:

@@ -10,11 +10,13 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/pssgp.h"
 #include "host_model.cuh"
 #include "linalg.cuh"
 #include "scan_ops.cuh"
+#include "tc_gemm.cuh"
 
 using namespace pssgp;
 
@@ -415,6 +417,7 @@ Net net_of(void* state) {
 struct Acts {
   __nv_bfloat16 *X, *XT, *H1, *H1T, *H2, *H2T, *dOh, *dOT, *dZ2, *dZ2T, *dZ1, *dZ1T;
   float *Out, *dOut, *lossp;
+  int* err;                // set by a tensor-core GEMM whose waits timed out
   int64_t bytes;
 };
 Acts acts_of(void* ws, int64_t M) {
@@ -428,6 +431,7 @@ Acts acts_of(void* ws, int64_t M) {
   a.dOh = bf(M * NOUT); a.dOT = bf(M * NOUT);
   a.dZ2 = bf(M * HID); a.dZ2T = bf(M * HID); a.dZ1 = bf(M * HID); a.dZ1T = bf(M * HID);
   a.Out = fl(M * NOUT); a.dOut = fl(M * NOUT); a.lossp = fl(M);
+  a.err = reinterpret_cast<int*>(fl(64));
   a.bytes = o;
   return a;
 }
@@ -590,31 +594,85 @@ __global__ void k_mlp_decode(const float* Out, const float* feat, int64_t M, con
 // ===========================================================================
 namespace {
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link-time dependency on libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// tensor map of a K-contiguous bf16 matrix [rows][K]: boxes of 64 K-elements
+// (one 128-byte swizzle row) by box_rows rows, zero fill outside
+bool tile_map(CUtensorMap* map, const __nv_bfloat16* ptr, int rows, int K, int box_rows) {
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn || (reinterpret_cast<uintptr_t>(ptr) & 15) || (K * 2) % 16 != 0 || rows < 1 || K < 1) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 0: tcgen05 with TMA (default); 1: the mma.sync kernel (checked baseline)
+int g_gemm_path = 0;
+
+// C = A B^T through the epilogue; returns false if a tensor map cannot be made
 template <class Epi>
-void gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int K, Epi e, cudaStream_t s) {
-  const dim3 grid((unsigned)((N + GT - 1) / GT), (unsigned)((M + GT - 1) / GT));
-  k_gemm_bf16<Epi><<<grid, 128, 0, s>>>(A, B, M, N, K, e);
+bool gemm_path(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int K, Epi e, int path, int* err,
+               cudaStream_t s) {
+  if (path == 1) {
+    const dim3 grid((unsigned)((N + GT - 1) / GT), (unsigned)((M + GT - 1) / GT));
+    k_gemm_bf16<Epi><<<grid, 128, 0, s>>>(A, B, M, N, K, e);
+    return true;
+  }
+  CUtensorMap ma, mb;
+  if (!tile_map(&ma, A, M, K, tc::BM) || !tile_map(&mb, B, N, K, tc::BN)) return false;
+  cudaFuncSetAttribute(tc::k_gemm_tc<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+  const dim3 grid((unsigned)((N + tc::BN - 1) / tc::BN), (unsigned)((M + tc::BM - 1) / tc::BM));
+  tc::k_gemm_tc<Epi><<<grid, 128, tc::SMEM_BYTES, s>>>(ma, mb, M, N, K, e, err);
+  return true;
+}
+
+thread_local bool t_gemm_ok = true;   // cleared when a tensor map could not be made
+
+template <class Epi>
+void gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N, int K, Epi e, int* err, cudaStream_t s) {
+  if (!gemm_path(A, B, M, N, K, e, g_gemm_path, err, s)) t_gemm_ok = false;
 }
 
 unsigned blocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 void forward(const Net& n, const Acts& a, const float* feat, int M, cudaStream_t s) {
   k_mlp_input<<<blocks((int64_t)M * KIN, 256), 256, 0, s>>>(feat, M, n.norm, a.X, a.XT);
-  gemm(a.X, n.W1h, M, HID, KIN, EpiBiasReLU{a.H1, a.H1T, HID, M, n.P + OB1}, s);
-  gemm(a.H1, n.W2h, M, HID, HID, EpiBiasReLU{a.H2, a.H2T, HID, M, n.P + OB2}, s);
-  gemm(a.H2, n.W3h, M, NOUT, HID, EpiBiasF32{a.Out, NOUT, n.P + OB3}, s);
+  gemm(a.X, n.W1h, M, HID, KIN, EpiBiasReLU{a.H1, a.H1T, HID, M, n.P + OB1}, a.err, s);
+  gemm(a.H1, n.W2h, M, HID, HID, EpiBiasReLU{a.H2, a.H2T, HID, M, n.P + OB2}, a.err, s);
+  gemm(a.H2, n.W3h, M, NOUT, HID, EpiBiasF32{a.Out, NOUT, n.P + OB3}, a.err, s);
 }
 
 void backward(const Net& n, const Acts& a, const double* theta, int M, float* G, float* loss, cudaStream_t s) {
   k_mlp_loss<<<blocks(M, 256), 256, 0, s>>>(a.Out, theta, M, n.norm, a.dOut, a.dOh, a.dOT, a.lossp);
   if (loss) k_sum1<<<1, 256, 0, s>>>(a.lossp, M, loss);
-  gemm(a.dOT, a.H2T, NOUT, HID, M, EpiF32{G + OW3, HID}, s);                       // dW3 = dOut^T H2
+  gemm(a.dOT, a.H2T, NOUT, HID, M, EpiF32{G + OW3, HID}, a.err, s);                       // dW3 = dOut^T H2
   k_colsum<float><<<1, NOUT, 0, s>>>(a.dOut, M, NOUT, G + OB3);
-  gemm(a.dOh, n.W3T, M, HID, NOUT, EpiReLUMask{a.dZ2, a.dZ2T, HID, M, a.H2}, s);    // dZ2 = dOut W3 .* [H2 > 0]
-  gemm(a.dZ2T, a.H1T, HID, HID, M, EpiF32{G + OW2, HID}, s);                        // dW2 = dZ2^T H1
+  gemm(a.dOh, n.W3T, M, HID, NOUT, EpiReLUMask{a.dZ2, a.dZ2T, HID, M, a.H2}, a.err, s);    // dZ2 = dOut W3 .* [H2 > 0]
+  gemm(a.dZ2T, a.H1T, HID, HID, M, EpiF32{G + OW2, HID}, a.err, s);                        // dW2 = dZ2^T H1
   k_colsum<__nv_bfloat16><<<1, HID, 0, s>>>(a.dZ2, M, HID, G + OB2);
-  gemm(a.dZ2, n.W2T, M, HID, HID, EpiReLUMask{a.dZ1, a.dZ1T, HID, M, a.H1}, s);     // dZ1 = dZ2 W2 .* [H1 > 0]
-  gemm(a.dZ1T, a.XT, HID, KIN, M, EpiF32{G + OW1, KIN}, s);                         // dW1 = dZ1^T X
+  gemm(a.dZ2, n.W2T, M, HID, HID, EpiReLUMask{a.dZ1, a.dZ1T, HID, M, a.H1}, a.err, s);     // dZ1 = dZ2 W2 .* [H1 > 0]
+  gemm(a.dZ1T, a.XT, HID, KIN, M, EpiF32{G + OW1, KIN}, a.err, s);                         // dW1 = dZ1^T X
   k_colsum<__nv_bfloat16><<<1, HID, 0, s>>>(a.dZ1, M, HID, G + OB1);
 }
 
@@ -697,8 +755,11 @@ extern "C" int pssgp_mlp_grad(void* state, const float* feat, const double* thet
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   (void)cudaGetLastError();
   const Net n = net_of(state);
+  t_gemm_ok = true;
+  if (cudaMemsetAsync(a.err, 0, sizeof(int), s) != cudaSuccess) return PSSGP_ECUDA;
   forward(n, a, feat, rows, s);
   backward(n, a, theta, rows, grad, loss, s);
+  if (!t_gemm_ok) return PSSGP_ECUDA;
   if (out && cudaMemcpyAsync(out, a.Out, (size_t)rows * NOUT * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return PSSGP_ECUDA;
   return rc_of(cudaGetLastError());
@@ -723,7 +784,29 @@ extern "C" int pssgp_mlp_predict(const void* state, const float* feat, int32_t r
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   (void)cudaGetLastError();
   const Net n = net_of(const_cast<void*>(state));
+  t_gemm_ok = true;
+  if (cudaMemsetAsync(a.err, 0, sizeof(int), s) != cudaSuccess) return PSSGP_ECUDA;
   forward(n, a, feat, rows, s);
+  if (!t_gemm_ok) return PSSGP_ECUDA;
   k_mlp_decode<<<blocks(rows, 256), 256, 0, s>>>(a.Out, feat, rows, n.norm, theta);
+  return rc_of(cudaGetLastError());
+}
+
+extern "C" int pssgp_mlp_set_gemm(int32_t path) {
+  if (path != 0 && path != 1) return PSSGP_EINVAL;
+  g_gemm_path = path;
+  return PSSGP_OK;
+}
+
+extern "C" int pssgp_debug_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K, float* C,
+                                     int32_t path, int32_t* err, void* stream) {
+  if (!A || !B || !C || !err || M < 1 || N < 1 || K < 1 || (path != 0 && path != 1)) return PSSGP_EINVAL;
+  if (K % 8 != 0) return PSSGP_EINVAL;   // 16-byte rows
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  (void)cudaGetLastError();
+  if (cudaMemsetAsync(err, 0, sizeof(int32_t), s) != cudaSuccess) return PSSGP_ECUDA;
+  if (!gemm_path(static_cast<const __nv_bfloat16*>(A), static_cast<const __nv_bfloat16*>(B), M, N, K,
+                 EpiF32{C, N}, path, err, s))
+    return PSSGP_ECUDA;
   return rc_of(cudaGetLastError());
 }
