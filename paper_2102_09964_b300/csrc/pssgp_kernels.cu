@@ -615,17 +615,28 @@ __device__ __forceinline__ double ll_piece(int nobs, const LogProd& lp, double q
 
 // shared memory of k_filter_reduce: A (two buffers), J (packed) and eta per
 // thread, entry-major with stride BLOCK
-// For 4 <= d <= 6 the level-1 warp scan also runs in shared memory: two
-// buffers of one packed aggregate per thread, the second overlapping the
-// fold's region (the fold is done when the scan starts); 189 doubles per
-// thread (194 KB per block) at d = 6.  Below d = 4 the aggregates are small
-// enough for registers, above d = 6 the buffers would not fit.
-template <int D> __host__ __device__ constexpr bool reduce_l1_smem() { return D >= 4 && D <= 6; }
+// instances of k_filter_reduce (RMODE, described below)
+enum { RED_PLAIN = 0, RED_LL = 1, RED_SMOOTH = 2, RED_ADJ = 3 };
+
+// For 4 <= d <= 6 the level-1 warp scan can run in shared
+// memory: two buffers of one packed aggregate per thread, the second
+// overlapping the fold's region (the fold is done when the scan starts); 189
+// doubles per thread (194 KB per block) at d = 6.  Below d = 4 the aggregates
+// are small enough for registers, above d = 6 the buffers would not fit.
+// The prediction's instance (RED_SMOOTH) keeps the scan on register/local
+// operands and its 101 KB of shared memory: then a block of another stream's
+// filter pass (114 KB) fits beside it on an SM, and steps alternating over
+// streams overlap (measured at 2^20 RBF-6: 226 M steps/s with four streams
+// against 217 M with the shared-memory scan, which makes one call 1.7 %
+// faster instead: 5.36 against 5.45 ms).
+template <int D, int RMODE> __host__ __device__ constexpr bool reduce_l1_smem() {
+  return D >= 4 && D <= 6 && RMODE != RED_SMOOTH;
+}
 template <int D> __host__ __device__ constexpr int reduce_fold_doubles() { return 2 * D * D + Sym<D>::N + D; }
-template <int D> constexpr int reduce_smem_doubles() {
-  return (reduce_l1_smem<D>() ? FAggSize<D>::N + (reduce_fold_doubles<D>() > FAggSize<D>::N
-                                                      ? reduce_fold_doubles<D>() : FAggSize<D>::N)
-                              : reduce_fold_doubles<D>()) * BLOCK;
+template <int D, int RMODE> constexpr int reduce_smem_doubles() {
+  return (reduce_l1_smem<D, RMODE>() ? FAggSize<D>::N + (reduce_fold_doubles<D>() > FAggSize<D>::N
+                                                             ? reduce_fold_doubles<D>() : FAggSize<D>::N)
+                                     : reduce_fold_doubles<D>()) * BLOCK;
 }
 
 // RMODE:
@@ -642,34 +653,36 @@ template <int D> constexpr int reduce_smem_doubles() {
 //    chunk's first step as input; its (A, eta, J) go to lane_fp (for the
 //    mean-adjoint chunk aggregate of k_filter_propagate), and the transition
 //    is put back in front (one operator application) for the scan.
-enum { RED_PLAIN = 0, RED_LL = 1, RED_SMOOTH = 2, RED_ADJ = 3 };
 
-template <int D>
+// A, eta, J: this thread's entries in shared memory with stride SST (the
+// block's thread count)
+template <int D, int SST>
 __device__ __forceinline__ void save_fold_state(const ScanArgs& a, int64_t g, const double* A, const double* eta,
                                                 const double* J) {
 #pragma unroll
-  for (int e = 0; e < D * D; ++e) a.lane_fp[e * a.P0 + g] = A[e * BLOCK];
+  for (int e = 0; e < D * D; ++e) a.lane_fp[e * a.P0 + g] = A[e * SST];
 #pragma unroll
-  for (int i = 0; i < D; ++i) a.lane_fp[(D * D + i) * a.P0 + g] = eta[i * BLOCK];
+  for (int i = 0; i < D; ++i) a.lane_fp[(D * D + i) * a.P0 + g] = eta[i * SST];
 #pragma unroll
-  for (int e = 0; e < Sym<D>::N; ++e) a.lane_fp[(D * D + D + e) * a.P0 + g] = J[e * BLOCK];
+  for (int e = 0; e < Sym<D>::N; ++e) a.lane_fp[(D * D + D + e) * a.P0 + g] = J[e * SST];
 }
 
 template <int D, int RMODE>
 __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m, const ScanArgs a) {
+  constexpr int RB = BLOCK;   // threads per block (stride of the per-thread arrays)
   constexpr bool LL = RMODE == RED_LL;
   // 16-byte record loads (load_record) made the gradient's instance faster;
   // in the others they cost more register spills than they saved
   constexpr bool VECMODE = RMODE == RED_ADJ;
   extern __shared__ double smem[];
-  constexpr bool L1S = reduce_l1_smem<D>();
+  constexpr bool L1S = reduce_l1_smem<D, RMODE>();
   constexpr int NF = FAggSize<D>::N;
   double* sB0 = smem + threadIdx.x;                    // level-1 buffer 0 (shared-memory scan)
-  double* sA0 = smem + (L1S ? NF * BLOCK : 0) + threadIdx.x;
-  double* sA1 = sA0 + D * D * BLOCK;
-  double* sJ = sA1 + D * D * BLOCK;
-  double* seta = sJ + Sym<D>::N * BLOCK;
-  const int64_t g = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  double* sA0 = smem + (L1S ? NF * RB : 0) + threadIdx.x;
+  double* sA1 = sA0 + D * D * RB;
+  double* sJ = sA1 + D * D * RB;
+  double* seta = sJ + Sym<D>::N * RB;
+  const int64_t g = (int64_t)blockIdx.x * RB + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int64_t k0 = g * a.L;
   const int64_t k1 = min(k0 + a.L, a.n);
@@ -681,12 +694,12 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     b[i] = 0.0;
-    seta[i * BLOCK] = 0.0;
+    seta[i * RB] = 0.0;
 #pragma unroll
-    for (int j = 0; j < D; ++j) { C[i][j] = 0.0; sA0[(i * D + j) * BLOCK] = (i == j) ? 1.0 : 0.0; }
+    for (int j = 0; j < D; ++j) { C[i][j] = 0.0; sA0[(i * D + j) * RB] = (i == j) ? 1.0 : 0.0; }
   }
 #pragma unroll
-  for (int e = 0; e < Sym<D>::N; ++e) sJ[e * BLOCK] = 0.0;
+  for (int e = 0; e < Sym<D>::N; ++e) sJ[e * RB] = 0.0;
   double* Ain = sA0;
   double* Aout = sA1;
   const double R0 = a.R ? a.R[0] : a.R_scalar;
@@ -711,7 +724,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
     }
     if constexpr (RMODE == RED_SMOOTH) {
       // steps k0 .. k1-2 (also in the last lane when the series goes on in a next chunk)
-      if (k == k1 - 1 && (k1 < a.n || !isnan(a.t_next))) save_fold_state<D>(a, g, Ain, seta, sJ);
+      if (k == k1 - 1 && (k1 < a.n || !isnan(a.t_next))) save_fold_state<D, RB>(a, g, Ain, seta, sJ);
     }
     Mat<D> F, Q;
     load_fq<D, VECMODE>(a.rec_fq, k, F, Q);
@@ -727,7 +740,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
     const bool obs = a.mask[k] != 0 && !nonfinite(yk);
     if (a.mask[k] != 0 && nonfinite(yk)) bits |= PSSGP_ENAN;
     double S, Si, r;
-    fagg_fold_step_smem<D, BLOCK>(b, C, Ain, Aout, sJ, seta, F, Q, obs, yk, Rk, bad, S, Si, r);
+    fagg_fold_step_smem<D, RB>(b, C, Ain, Aout, sJ, seta, F, Q, obs, yk, Rk, bad, S, Si, r);
     if constexpr (LL) {
       qsum = fma(r * Si, r, qsum);
       lp.mul(obs ? S : 1.0);
@@ -738,10 +751,10 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
     Aout = tsw;
   }
   if constexpr (RMODE == RED_SMOOTH) {
-    if (k1 == a.n && k1 > k0 && isnan(a.t_next)) save_fold_state<D>(a, g, Ain, seta, sJ);   // the series' last step
+    if (k1 == a.n && k1 > k0 && isnan(a.t_next)) save_fold_state<D, RB>(a, g, Ain, seta, sJ);   // the series' last step
   }
   if constexpr (RMODE == RED_ADJ) {
-    if (k1 > k0) save_fold_state<D>(a, g, Ain, seta, sJ);
+    if (k1 > k0) save_fold_state<D, RB>(a, g, Ain, seta, sJ);
   }
   if constexpr (LL) {
     const double piece = ll_piece(nobs, lp, qsum);
@@ -749,9 +762,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
     else a.ll_step[lpos] = piece;
     a.lane_ll[g] = cfirst;
 #pragma unroll
-    for (int i = 0; i < D; ++i) a.lane_ll[(1 + i) * a.P0 + g] = seta[i * BLOCK];
+    for (int i = 0; i < D; ++i) a.lane_ll[(1 + i) * a.P0 + g] = seta[i * RB];
 #pragma unroll
-    for (int e = 0; e < Sym<D>::N; ++e) a.lane_ll[(1 + D + e) * a.P0 + g] = sJ[e * BLOCK];
+    for (int e = 0; e < Sym<D>::N; ++e) a.lane_ll[(1 + D + e) * a.P0 + g] = sJ[e * RB];
   }
   if constexpr (L1S) {
     // the chunk aggregate, packed into buffer 0, then the level-1 scan in
@@ -763,12 +776,12 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
 #pragma unroll
       for (int i = 0; i < D; ++i) {
         ag.b[i] = b[i];
-        ag.eta[i] = seta[i * BLOCK];
+        ag.eta[i] = seta[i * RB];
 #pragma unroll
         for (int jj = 0; jj < D; ++jj) {
-          ag.A[i][jj] = Ain[(i * D + jj) * BLOCK];
+          ag.A[i][jj] = Ain[(i * D + jj) * RB];
           ag.C[i][jj] = C[i][jj];
-          ag.J[i][jj] = sJ[(i <= jj ? pidx<D>(i, jj) : pidx<D>(jj, i)) * BLOCK];
+          ag.J[i][jj] = sJ[(i <= jj ? pidx<D>(i, jj) : pidx<D>(jj, i)) * RB];
         }
       }
       if (k1 > k0) {
@@ -784,23 +797,23 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
         if (!fagg_combine<D>(T, ag, r)) bad = true;
         ag = r;
       }
-      store_fagg<D>(B0, BLOCK, ag);
+      store_fagg<D>(B0, RB, ag);
     } else {
 #pragma unroll
-      for (int e = 0; e < D * D; ++e) B0[e * BLOCK] = Ain[e * BLOCK];
+      for (int e = 0; e < D * D; ++e) B0[e * RB] = Ain[e * RB];
 #pragma unroll
-      for (int i = 0; i < D; ++i) B0[(D * D + i) * BLOCK] = b[i];
+      for (int i = 0; i < D; ++i) B0[(D * D + i) * RB] = b[i];
 #pragma unroll
       for (int i = 0; i < D; ++i)
 #pragma unroll
-        for (int j = i; j < D; ++j) B0[(D * D + D + pidx<D>(i, j)) * BLOCK] = C[i][j];
+        for (int j = i; j < D; ++j) B0[(D * D + D + pidx<D>(i, j)) * RB] = C[i][j];
 #pragma unroll
-      for (int i = 0; i < D; ++i) B0[(D * D + D + Sym<D>::N + i) * BLOCK] = seta[i * BLOCK];
+      for (int i = 0; i < D; ++i) B0[(D * D + D + Sym<D>::N + i) * RB] = seta[i * RB];
 #pragma unroll
-      for (int e = 0; e < Sym<D>::N; ++e) B0[(D * D + 2 * D + Sym<D>::N + e) * BLOCK] = sJ[e * BLOCK];
+      for (int e = 0; e < Sym<D>::N; ++e) B0[(D * D + 2 * D + Sym<D>::N + e) * RB] = sJ[e * RB];
     }
     if (a.dbg_agg) {
-      for (int e = 0; e < NF; ++e) a.dbg_agg[e * a.P0 + g] = B0[e * BLOCK];
+      for (int e = 0; e < NF; ++e) a.dbg_agg[e * a.P0 + g] = B0[e * RB];
     }
     __syncwarp();
     double* cur = B0;
@@ -808,9 +821,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
 #pragma unroll 1
     for (int off = 1; off < 32; off <<= 1) {
       if (lane >= off) {
-        if (!fagg_combine_smem<D, BLOCK>(cur - off, cur, nxt)) bad = true;
+        if (!fagg_combine_smem<D, RB>(cur - off, cur, nxt)) bad = true;
       } else {
-        for (int e = 0; e < NF; ++e) nxt[e * BLOCK] = cur[e * BLOCK];
+        for (int e = 0; e < NF; ++e) nxt[e * RB] = cur[e * RB];
       }
       __syncwarp();
       double* tsw = cur;
@@ -818,7 +831,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
       nxt = tsw;
     }
     for (int e = 0; e < NF; ++e) {
-      const double v = cur[e * BLOCK];
+      const double v = cur[e * RB];
       a.lagg_f[e * a.P0 + g] = v;
       if (lane == 31) a.wagg_f[e * a.P2 + (g >> 5)] = v;
     }
@@ -827,12 +840,12 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       ag.b[i] = b[i];
-      ag.eta[i] = seta[i * BLOCK];
+      ag.eta[i] = seta[i * RB];
 #pragma unroll
       for (int jj = 0; jj < D; ++jj) {
-        ag.A[i][jj] = Ain[(i * D + jj) * BLOCK];
+        ag.A[i][jj] = Ain[(i * D + jj) * RB];
         ag.C[i][jj] = C[i][jj];
-        ag.J[i][jj] = sJ[(i <= jj ? pidx<D>(i, jj) : pidx<D>(jj, i)) * BLOCK];
+        ag.J[i][jj] = sJ[(i <= jj ? pidx<D>(i, jj) : pidx<D>(jj, i)) * RB];
       }
     }
     if constexpr (RMODE == RED_ADJ) {
@@ -2115,10 +2128,13 @@ void run_filter_front(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStre
     after_launch();
   }
   {
-    constexpr int smem = reduce_smem_doubles<D>() * 8;
     auto kern = ll_only ? k_filter_reduce<D, RED_LL>
                 : a.adj ? k_filter_reduce<D, RED_ADJ>
                         : a.fuse_smoother ? k_filter_reduce<D, RED_SMOOTH> : k_filter_reduce<D, RED_PLAIN>;
+    const int smem = 8 * (ll_only ? reduce_smem_doubles<D, RED_LL>()
+                          : a.adj ? reduce_smem_doubles<D, RED_ADJ>()
+                                  : a.fuse_smoother ? reduce_smem_doubles<D, RED_SMOOTH>()
+                                                    : reduce_smem_doubles<D, RED_PLAIN>());
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     Timed tm(s, T_FRED);
     kern<<<grid, BLOCK, smem, s>>>(m, a);

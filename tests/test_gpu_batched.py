@@ -271,8 +271,11 @@ def test_failed_series_are_nan_and_leave_the_others_intact(kind):
 def test_batched_prior_workload_sampled():
     """The benchmark's 4,096-series workload with y drawn from the prior
     (the library's simulation, seeds as in the benchmark), one call per
-    family; sampled series against the oracle on the oracle's own simulation
-    of the same series (Philox4x32-10 on both sides)."""
+    family.  The sampled series are replaced in the batch by the oracle's own
+    simulation of them (the same Philox4x32-10 stream: the two simulations
+    agree to about 1e-10, which smooth, nearly noise-free series amplify in
+    the log-likelihood), so that the GPU and the oracle evaluate the same
+    inputs."""
     offs, kinds, params = wl.prior_batch_spec(**wl.PRIOR_BATCH)
     kinds = np.array(kinds)
     rng = np.random.default_rng(46)
@@ -283,15 +286,22 @@ def test_batched_prior_workload_sampled():
         seed = 300 + fi
         t, y, st = P.simulate_prior(m, offd, dev(par), seed=seed)
         assert int(st.item()) == 0
-        ll, ws = P.loglik_batched(m, offd, dev(par), t, y, torch.ones(t.numel(), dtype=torch.uint8, device="cuda"))
-        assert P.status(ws) == 0
-        ll = ll.cpu().numpy()
-        assert np.all(np.isfinite(ll))
         lens = np.diff(off)
         pick = sorted({int(np.argmin(lens)), int(np.argmax(lens)), *rng.choice(lens.size, 2, replace=False).tolist()})
+        ref = {}
+        t, y = t.clone(), y.clone()
         for s in pick:
             n = int(lens[s])
             mo = om.make_model(kind, par[s, 0], par[s, 1])
             rt, ry = oracle.simulate_series(mo, par[s, 2], n, seed, s)
-            ref = oracle.run(mo, rt, ry, np.ones(n, np.uint8), par[s, 2]).loglik
-            assert abs(ll[s] - ref) <= TOL[kind] * max(abs(ref), n), (kind, s, ll[s], ref)
+            a = int(off[s])
+            t[a:a + n] = dev(rt)
+            y[a:a + n] = dev(ry)
+            ref[s] = oracle.run(mo, rt, ry, np.ones(n, np.uint8), par[s, 2]).loglik
+        ll, ws = P.loglik_batched(m, offd, dev(par), t, y, torch.ones(t.numel(), dtype=torch.uint8, device="cuda"))
+        assert P.status(ws) == 0
+        ll = ll.cpu().numpy()
+        assert np.all(np.isfinite(ll))
+        for s in pick:
+            n = int(lens[s])
+            assert abs(ll[s] - ref[s]) <= TOL[kind] * max(abs(ref[s]), n), (kind, s, ll[s], ref[s])
