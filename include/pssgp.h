@@ -296,19 +296,42 @@ int pssgp_loglik_grad_batched(const pssgp_model* model, const int64_t* offsets,
  * next: use the same workspace, inputs and scan tuning for all four.  A
  * *_reduce call of the filter clears the status word; the other calls add
  * their bits to it.  With G = 1 and smoother = 1 the sequence computes what
- * pssgp_predict computes on merged inputs. */
+ * pssgp_predict computes on merged inputs.
+ *
+ * The gradient of the log-likelihood (as pssgp_loglik_grad) over a split
+ * series takes smoother = 2 in steps 1 and 3 (the filter pass then keeps the
+ * predicted moments and forms the mean adjoint's lane aggregates) and a
+ * workspace of pssgp_workspace_size_grad(d, n) bytes, then two backward
+ * exchanges instead of steps 4-6:
+ *   4'. every rank: pssgp_split_grad_mean_reduce -> its chunk's mean-adjoint
+ *       aggregate (Pi, gamma: mb_first = Pi mb_after + gamma, mb the adjoint
+ *       of a predicted mean);
+ *   5'. all-gather them; every rank: pssgp_split_grad_mean_finish (the
+ *       chunks after it folded into the mean adjoint after its last step)
+ *       -> its covariance-adjoint aggregate (Pi, L: Mb_first =
+ *       Pi Mb_after Pi^T + L);
+ *   6'. all-gather those; every rank: pssgp_split_grad_finish -> its chunk's
+ *       three derivative sums; all-reduce (sum) them and the
+ *       log-likelihoods.
+ * The transition from a chunk's first time back to t_prev belongs to that
+ * chunk (its derivative terms are summed there), the one after its last
+ * step to the next chunk; step 3 also discretises the latter (t_next) for
+ * the adjoints.  Every aggregate of 4'-6' has pssgp_split_agg_doubles(d, 1)
+ * doubles and the smoother's operator (E = Pi, g, L). */
 
 /* Doubles in one chunk aggregate: filter (smoother = 0) 2 d^2 + 3 d
- * (A, b, C, eta, J), smoother (smoother = 1) d^2 + d + d(d+1)/2 (E, g, L);
- * 0 for d outside 1..PSSGP_DMAX. */
+ * (A, b, C, eta, J), smoother or adjoint (smoother = 1) d^2 + d + d(d+1)/2
+ * (E, g, L); 0 for d outside 1..PSSGP_DMAX. */
 int32_t pssgp_split_agg_doubles(int32_t d, int32_t smoother);
 
 /* Step 1: discretises the chunk (step 0 is the transition from t_prev, or
  * the series' first step if t_prev is NaN), folds its filtering elements
  * (Sec. 3) and writes the chunk's aggregate to agg (device,
- * pssgp_split_agg_doubles(d, 0) doubles).  smoother (0 or 1): whether step 3
- * will prepare the smoother; t_next: as above.  Other arguments as
- * pssgp_filter for the chunk's n steps. */
+ * pssgp_split_agg_doubles(d, 0) doubles).  smoother: 0 filter and
+ * log-likelihood, 1 step 3 will prepare the smoother, 2 the gradient (the
+ * gradient's workspace size); t_next: as above.  Other arguments as
+ * pssgp_filter for the chunk's n steps.  PSSGP_EINVAL for another value of
+ * smoother or a time argument that is infinite. */
 int pssgp_split_filter_reduce(const pssgp_model* model, const double* t,
                               const double* y, const uint8_t* mask,
                               const double* R, int32_t R_per_step, int64_t n,
@@ -321,7 +344,8 @@ int pssgp_split_filter_reduce(const pssgp_model* model, const double* t,
  * chunk.  Outputs as pssgp_filter (xf, Pf nullable; with both null and
  * smoother = 0 only the log-likelihood is formed); loglik (nullable, one
  * device double): the sum over the chunk's observations of
- * log p(y_k | all earlier y).  t_next and smoother as in step 1. */
+ * log p(y_k | all earlier y).  t_next and smoother as in step 1 (the same
+ * values). */
 int pssgp_split_filter_finish(const pssgp_model* model, const double* t,
                               const double* y, const uint8_t* mask,
                               const double* R, int32_t R_per_step, int64_t n,
@@ -345,6 +369,32 @@ int pssgp_split_smooth_finish(const pssgp_model* model, int64_t n, int64_t ld,
                               double* f_mean, double* f_var, double* xs,
                               double* Ps, void* ws, size_t ws_bytes,
                               void* stream);
+
+/* Step 4' (after step 3 with smoother = 2): writes the chunk's mean-adjoint
+ * aggregate to agg (device, pssgp_split_agg_doubles(d, 1) doubles). */
+int pssgp_split_grad_mean_reduce(const pssgp_model* model, int64_t n,
+                                 double* agg, void* ws, size_t ws_bytes,
+                                 void* stream);
+
+/* Step 5': aggs: device array of the G chunks' mean-adjoint aggregates in
+ * rank order; the ones after `rank` are folded into the mean adjoint after
+ * the chunk.  Writes the chunk's covariance-adjoint aggregate to agg_cov
+ * (device, pssgp_split_agg_doubles(d, 1) doubles). */
+int pssgp_split_grad_mean_finish(const pssgp_model* model, int64_t n,
+                                 const double* aggs, int32_t G, int32_t rank,
+                                 double* agg_cov, void* ws, size_t ws_bytes,
+                                 void* stream);
+
+/* Step 6': aggs_cov: device array of the G chunks' covariance-adjoint
+ * aggregates in rank order.  grad: device double[3], the chunk's terms of
+ * d loglik / d(log lengthscale, log variance, log noise variance); their sum
+ * over the ranks is pssgp_loglik_grad's gradient of the whole series.  R and
+ * R_per_step as in step 1. */
+int pssgp_split_grad_finish(const pssgp_model* model, const double* R,
+                            int32_t R_per_step, int64_t n,
+                            const double* aggs_cov, int32_t G, int32_t rank,
+                            double* grad, void* ws, size_t ws_bytes,
+                            void* stream);
 
 /* Allocation-free variant of pssgp_loglik for callers that cannot allocate
  * device memory themselves -- for instance a plugin inside a host program

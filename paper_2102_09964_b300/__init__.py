@@ -128,6 +128,10 @@ def lib():
         L.pssgp_split_smooth_reduce.argtypes = [ctypes.POINTER(PssgpModel), i64, vp, vp, sz, vp]
         L.pssgp_split_smooth_finish.argtypes = [ctypes.POINTER(PssgpModel), i64, i64, vp, i32, i32, vp, vp, vp, vp,
                                                 vp, sz, vp]
+        L.pssgp_split_grad_mean_reduce.argtypes = [ctypes.POINTER(PssgpModel), i64, vp, vp, sz, vp]
+        L.pssgp_split_grad_mean_finish.argtypes = [ctypes.POINTER(PssgpModel), i64, vp, i32, i32, vp, vp, sz, vp]
+        L.pssgp_split_grad_finish.argtypes = [ctypes.POINTER(PssgpModel), vp, i32, i64, vp, i32, i32, vp, vp, sz,
+                                              vp]
         L.pssgp_mlp_set_gemm.argtypes = [i32]
         L.pssgp_debug_gemm_bf16.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, vp]
         L.pssgp_timing_name.argtypes = [i32]
@@ -464,22 +468,28 @@ def split_agg_doubles(d: int, smoother: bool) -> int:
     return int(lib().pssgp_split_agg_doubles(int(d), int(bool(smoother))))
 
 
-def split_filter_reduce(model: Model, t, y, mask, R, t_prev: float, t_next: float, ws, smoother=True, agg=None):
+def _split_mode(smoother, grad):
+    return 2 if grad else int(bool(smoother))
+
+
+def split_filter_reduce(model: Model, t, y, mask, R, t_prev: float, t_next: float, ws, smoother=True, agg=None,
+                        grad=False):
     """This chunk's filter aggregate (device float64[nf]); ws carries state to
-    split_filter_finish (which must get the same t_next and smoother)."""
+    split_filter_finish (which must get the same t_next, smoother and grad).
+    grad: the adjoint pass of the gradient follows (ws from workspace_grad)."""
     d, n = model.d, t.numel()
     R = _f64(R, t.device).reshape(-1)
     per = 1 if R.numel() == n and n > 1 else 0
     agg = agg if agg is not None else _empty(split_agg_doubles(d, False), dtype=torch.float64, device=t.device)
     rc = lib().pssgp_split_filter_reduce(ctypes.byref(model.raw), _ptr(t), _ptr(y), _ptr(mask), _ptr(R), per, n,
-                                         float(t_prev), float(t_next), int(bool(smoother)), _ptr(agg), _ptr(ws),
+                                         float(t_prev), float(t_next), _split_mode(smoother, grad), _ptr(agg), _ptr(ws),
                                          ws.numel(), _stream())
     _check(rc, "pssgp_split_filter_reduce")
     return agg
 
 
 def split_filter_finish(model: Model, t, y, mask, R, t_next: float, aggs, rank: int, ws, smoother=True,
-                        outputs=True):
+                        outputs=True, grad=False):
     """Filter outputs of this chunk given every chunk's aggregate (aggs: device
     float64[G, nf] in rank order), and with smoother its smoother elements;
     returns (xf, Pf, loglik[1]) with xf, Pf None unless outputs."""
@@ -492,7 +502,8 @@ def split_filter_finish(model: Model, t, y, mask, R, t_next: float, aggs, rank: 
     Pf = _empty(d * (d + 1) // 2, n, dtype=torch.float64, device=dev) if outputs else None
     ll = _empty(1, dtype=torch.float64, device=dev)
     rc = lib().pssgp_split_filter_finish(ctypes.byref(model.raw), _ptr(t), _ptr(y), _ptr(mask), _ptr(R), per, n,
-                                         float(t_next), int(bool(smoother)), _ptr(aggs), aggs.shape[0], int(rank),
+                                         float(t_next), _split_mode(smoother, grad), _ptr(aggs), aggs.shape[0],
+                                         int(rank),
                                          _ptr(xf), _ptr(Pf), n, _ptr(ll), _ptr(ws), ws.numel(), _stream())
     _check(rc, "pssgp_split_filter_finish")
     return xf, Pf, ll
@@ -521,6 +532,39 @@ def split_smooth_finish(model: Model, n: int, aggs, rank: int, ws, device="cuda"
                                          _ptr(fm), _ptr(fv), _ptr(xs), _ptr(Ps), _ptr(ws), ws.numel(), _stream())
     _check(rc, "pssgp_split_smooth_finish")
     return fm, fv, xs, Ps
+
+
+def split_grad_mean_reduce(model: Model, n: int, ws, device="cuda"):
+    """This chunk's mean-adjoint aggregate (device float64[ns]), after
+    split_filter_finish with grad."""
+    agg = _empty(split_agg_doubles(model.d, True), dtype=torch.float64, device=device)
+    _check(lib().pssgp_split_grad_mean_reduce(ctypes.byref(model.raw), int(n), _ptr(agg), _ptr(ws), ws.numel(),
+                                              _stream()), "pssgp_split_grad_mean_reduce")
+    return agg
+
+
+def split_grad_mean_finish(model: Model, n: int, aggs, rank: int, ws, device="cuda"):
+    """Given every chunk's mean-adjoint aggregate (device float64[G, ns]):
+    this chunk's covariance-adjoint aggregate (device float64[ns])."""
+    aggs = aggs.contiguous()
+    agg = _empty(split_agg_doubles(model.d, True), dtype=torch.float64, device=device)
+    _check(lib().pssgp_split_grad_mean_finish(ctypes.byref(model.raw), int(n), _ptr(aggs), aggs.shape[0],
+                                              int(rank), _ptr(agg), _ptr(ws), ws.numel(), _stream()),
+           "pssgp_split_grad_mean_finish")
+    return agg
+
+
+def split_grad_finish(model: Model, n: int, R, aggs, rank: int, ws, device="cuda"):
+    """Given every chunk's covariance-adjoint aggregate: this chunk's terms of
+    the gradient (device float64[3]); R as in split_filter_reduce."""
+    R = _f64(R, device).reshape(-1)
+    per = 1 if R.numel() == n and n > 1 else 0
+    aggs = aggs.contiguous()
+    g = _empty(3, dtype=torch.float64, device=device)
+    _check(lib().pssgp_split_grad_finish(ctypes.byref(model.raw), _ptr(R), per, int(n), _ptr(aggs), aggs.shape[0],
+                                         int(rank), _ptr(g), _ptr(ws), ws.numel(), _stream()),
+           "pssgp_split_grad_finish")
+    return g
 
 
 def debug_filter_aggregates(model: Model, t, y, mask, R, lanes: int = 0):

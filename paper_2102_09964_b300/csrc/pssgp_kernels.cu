@@ -171,7 +171,8 @@ Plan make_plan(int d, int64_t n, int64_t lanes_req, int warps = 0, bool grad = f
   p.o_rstep = o; o += align256(n * 8);     // batched: noise variance per step
   p.o_seg = o; o += align256(n);           // batched: 1 at each series' first step
   p.o_llstep = o; o += align256(n * 8);    // batched: log-likelihood pieces per step
-  p.o_bnd = o; o += align256(p.nf * 8);     // split series: the folded aggregate of the other chunks
+  p.o_bnd = o; o += align256((p.nf + p.fqs) * 8);   // split series: the folded aggregate of the other
+                                                    // chunks, then the F/Q record of the step after the chunk
   p.o_adj = p.o_tauq = p.o_lpi = p.o_lmbar = p.o_lgj = p.o_gpart = p.o_gstep = -1;
   if (grad) {                                // gradient: forward moments, scan state
     const int adjs = (d + sym + 2 + 1) / 2 * 2;
@@ -241,7 +242,10 @@ struct ScanArgs {
   const double* start_f;     // packed filter aggregate of all steps before the chunk (a filter state:
                              // it holds the series' first step, so A = 0, eta = 0, J = 0), or null
   const double* end_s;       // packed smoother aggregate of all steps after the chunk (a smoothed state:
-                             // it holds the series' last step, so E = 0), or null
+                             // it holds the series' last step, so E = 0), or null; in the gradient's
+                             // backward scans the folded adjoint aggregate of the steps after the chunk
+  const double* f_next;      // gradient of a chunk of a longer series: the F/Q record of the transition
+                             // into the step after the chunk (null: the series ends with the chunk)
 };
 
 __device__ __forceinline__ void flag(int* status, int bits) {
@@ -884,14 +888,15 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
 
 // The filter state (x = b, P = C) of a packed filter aggregate that holds a
 // series' first step (then A = 0, eta = 0, J = 0: a state, Prop. 1).
+// (entry e at p[e * st])
 template <int D>
-__device__ __forceinline__ void load_fstate(const double* p, Vec<D>& x, Mat<D>& P) {
+__device__ __forceinline__ void load_fstate(const double* p, Vec<D>& x, Mat<D>& P, int64_t st = 1) {
 #pragma unroll
-  for (int i = 0; i < D; ++i) x[i] = p[D * D + i];
+  for (int i = 0; i < D; ++i) x[i] = p[(D * D + i) * st];
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
-    for (int j = i; j < D; ++j) { P[i][j] = p[D * D + D + pidx<D>(i, j)]; P[j][i] = P[i][j]; }
+    for (int j = i; j < D; ++j) { P[i][j] = p[(D * D + D + pidx<D>(i, j)) * st]; P[j][i] = P[i][j]; }
 }
 
 // filter level 2: one Kogge-Stone round over the warp aggregates, one warp
@@ -997,20 +1002,14 @@ __global__ void __launch_bounds__(BLOCK) k_filter_llfinish(const DevModel<D> m, 
   for (int i = 0; i < D; ++i) x[i] = 0.0;
   set_zero<D>(P);
   if (w > 0) {
-    FAgg<D> W;
-    load_fagg<D>(a.wfin_f + (w - 1), a.P2, W);
-#pragma unroll
-    for (int i = 0; i < D; ++i) x[i] = W.b[i];
-    copy<D>(W.C, P);
+    load_fstate<D>(a.wfin_f + (w - 1), x, P, a.P2);
   } else if (a.start_f) {   // a chunk of a longer series: the state before it
     load_fstate<D>(a.start_f, x, P);
   }
   if (lane > 0) {
-    FAgg<D> I;
-    load_fagg<D>(a.lagg_f + (g - 1), a.P0, I);
     Vec<D> x2;
     Mat<D> P2;
-    if (!fstate_combine<D>(x, P, I, x2, P2)) bad = true;
+    if (!fstate_combine<D>(x, P, a.lagg_f + (g - 1), a.P0, x2, P2)) bad = true;
 #pragma unroll
     for (int i = 0; i < D; ++i) x[i] = x2[i];
     copy<D>(P2, P);
@@ -1072,20 +1071,14 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
   for (int i = 0; i < D; ++i) x[i] = 0.0;
   set_zero<D>(P);
   if (w > 0) {
-    FAgg<D> W;
-    load_fagg<D>(a.wfin_f + (w - 1), a.P2, W);
-#pragma unroll
-    for (int i = 0; i < D; ++i) x[i] = W.b[i];
-    copy<D>(W.C, P);
+    load_fstate<D>(a.wfin_f + (w - 1), x, P, a.P2);
   } else if (a.start_f) {   // a chunk of a longer series: the state before it
     load_fstate<D>(a.start_f, x, P);
   }
   if (lane > 0) {
-    FAgg<D> I;
-    load_fagg<D>(a.lagg_f + (g - 1), a.P0, I);
     Vec<D> x2;
     Mat<D> P2;
-    if (!fstate_combine<D>(x, P, I, x2, P2)) bad = true;
+    if (!fstate_combine<D>(x, P, a.lagg_f + (g - 1), a.P0, x2, P2)) bad = true;
 #pragma unroll
     for (int i = 0; i < D; ++i) x[i] = x2[i];
     copy<D>(P2, P);
@@ -1192,6 +1185,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_propagate(const DevModel<D>
       Mat<D> F1, J, N, Pm0;
       Vec<D> eta;
       if (k1 < a.n) load_F<D>(a.rec_fq, k1, fqs_of<D>(), F1);
+      else if (a.f_next) load_F<D>(a.f_next, 0, fqs_of<D>(), F1);   // the series goes on in a next chunk
       else set_zero<D>(F1);
       load_sym_smem<D, BLOCK>(sV, Pm0);
 #pragma unroll
@@ -1490,6 +1484,33 @@ __global__ void __launch_bounds__(BLOCK) k_apply_smoother_end(double* wfin, int6
   warp_sagg_combine<D>(sa, sb, work, wfin + i, P2, lane);
 }
 
+// the F/Q record (layout of the per-step records) of the transition from the
+// chunk's last time t[n-1] to t_next, by one warp (discretize is warp-collective,
+// and the same instance as k_discretize_rec's, so that the record equals the
+// next chunk's record of its first step bit for bit); all zeros when t_next is
+// NaN (the series ends with the chunk: no transition after it)
+template <int D>
+__global__ void __launch_bounds__(32) k_discretize_next(const DevModel<D> m, const double* t, int64_t n,
+                                                        double t_next, double* rec, int* status) {
+  const bool act = threadIdx.x == 0;
+  if (isnan(t_next)) {
+    for (int e = threadIdx.x; e < fqs_of<D>(); e += 32) rec[e] = 0.0;
+    return;
+  }
+  double h = 0.0;
+  int bits = 0;
+  if (act) {
+    h = t_next - t[n - 1];
+    if (negative_nonzero(h)) bits |= PSSGP_EUNSORTED;
+  }
+  Mat<D> F, Q;
+  discretize<D, false, true>(m, h, false, act, F, Q);
+  if (act) {
+    store_fq<D>(rec, 0, F, Q);
+    flag(status, bits);
+  }
+}
+
 // one aggregate from an entry-major array (stride st) to packed (stride 1)
 __global__ void k_pack_aggregate(const double* src, int64_t st, int count, double* dst) {
   for (int e = threadIdx.x; e < count; e += blockDim.x) dst[e] = src[(int64_t)e * st];
@@ -1688,6 +1709,9 @@ __global__ void __launch_bounds__(BLOCK, 1) k_adjoint_mean(const DevModel<D> m, 
     load_sagg<D>(a.wfin_s + (w + 1), a.P2, V);
 #pragma unroll
     for (int i = 0; i < D; ++i) mb[i] = V.g[i];
+  } else if (a.end_s) {   // a chunk of a longer series: the mean adjoint after it
+#pragma unroll
+    for (int i = 0; i < D; ++i) mb[i] = a.end_s[D * D + i];
   }
   if (lane < 31) {
     SAgg<D> S;
@@ -1766,6 +1790,10 @@ __global__ void __launch_bounds__(BLOCK, 1) k_adjoint_cov(const DevModel<D> m, c
       SAgg<D> V;
       load_sagg<D>(a.wfin_a + (w + 1), a.P2, V);
       copy<D>(V.L, Mb);
+    } else if (a.end_s) {   // a chunk of a longer series: the covariance adjoint after it
+      SAgg<D> V;
+      load_sagg<D>(a.end_s, 1, V);
+      copy<D>(V.L, Mb);
     }
     if (lane < 31) {
       SAgg<D> S;
@@ -1792,6 +1820,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_adjoint_cov(const DevModel<D> m, c
     {
       Mat<D> F1;
       if (k + 1 < a.n) load_F<D>(a.rec_fq, k + 1, fqs_of<D>(), F1);
+      else if (a.f_next) load_F<D>(a.f_next, 0, fqs_of<D>(), F1);   // the series goes on in a next chunk
       else set_zero<D>(F1);
 #pragma unroll
       for (int i = 0; i < D; ++i) {
@@ -2152,7 +2181,9 @@ void run_filter_back(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStrea
     return;
   }
   {
-    const int psmem = (a.fuse_smoother ? propagate_smem_doubles<D, PROP_FUSE>() : propagate_smem_doubles<D, PROP_PLAIN>()) * 8;
+    const int psmem = 8 * (a.adj ? propagate_smem_doubles<D, PROP_ADJ>()
+                           : a.fuse_smoother ? propagate_smem_doubles<D, PROP_FUSE>()
+                                             : propagate_smem_doubles<D, PROP_PLAIN>());
     auto kern = a.adj ? k_filter_propagate<D, PROP_ADJ>
                       : a.fuse_smoother ? k_filter_propagate<D, PROP_FUSE> : k_filter_propagate<D, PROP_PLAIN>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem);
@@ -2528,9 +2559,10 @@ extern "C" int pssgp_split_filter_reduce(const pssgp_model* model, const double*
                                          size_t ws_bytes, void* stream) {
   begin_call();
   if (!model_ok(model) || !t || !y || !mask || !R || !agg || n < 1 || n > PSSGP_NMAX || !time_arg_ok(t_prev) ||
-      !time_arg_ok(t_next) || (smoother != 0 && smoother != 1))
+      !time_arg_ok(t_next) || smoother < 0 || smoother > 2)
     return PSSGP_EINVAL;
-  const Plan p = make_plan(model->d, n, 0);
+  const bool grad = smoother == 2;
+  const Plan p = make_plan(model->d, n, 0, 0, grad);
   const int rc = check_ws(p, ws, ws_bytes);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -2538,14 +2570,16 @@ extern "C" int pssgp_split_filter_reduce(const pssgp_model* model, const double*
   a.t = t; a.y = y; a.mask = mask; a.R = R; a.R_per_step = R_per_step;
   a.t_prev = t_prev;
   a.t_next = t_next;
-  a.fuse_smoother = smoother;
+  a.fuse_smoother = smoother == 1;
+  a.adj = grad;
   if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess) return PSSGP_ECUDA;
   PSSGP_DISPATCH(model->d, {
     const DevModel<D> m = dev_model<D>(model);
     // without the smoother the log-likelihood terms of the reduce are kept,
     // so the finishing call can take either level 3 (with or without filter
-    // outputs); with it the reduce saves what the fused pass needs
-    run_filter_front<D>(m, p, a, s, nullptr, !smoother);
+    // outputs); with it (or the gradient) the reduce saves what the fused
+    // (or adjoint) pass needs
+    run_filter_front<D>(m, p, a, s, nullptr, smoother == 0);
     // the chunk's aggregate: the inclusive level-2 result of the last warp
     k_pack_aggregate<<<1, 128, 0, s>>>(a.wfin_f + (p.P2 - 1), p.P2, p.nf, agg);
     after_launch();
@@ -2560,10 +2594,11 @@ extern "C" int pssgp_split_filter_finish(const pssgp_model* model, const double*
                                          size_t ws_bytes, void* stream) {
   begin_call();
   if (!model_ok(model) || !t || !y || !mask || !R || !aggs || n < 1 || n > PSSGP_NMAX || G < 1 || rank < 0 ||
-      rank >= G || !time_arg_ok(t_next) || (smoother != 0 && smoother != 1))
+      rank >= G || !time_arg_ok(t_next) || smoother < 0 || smoother > 2)
     return PSSGP_EINVAL;
   if ((xf || Pf) && ld < n) return PSSGP_EINVAL;
-  const Plan p = make_plan(model->d, n, 0);
+  const bool grad = smoother == 2;
+  const Plan p = make_plan(model->d, n, 0, 0, grad);
   const int rc = check_ws(p, ws, ws_bytes);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -2571,12 +2606,18 @@ extern "C" int pssgp_split_filter_finish(const pssgp_model* model, const double*
   a.t = t; a.y = y; a.mask = mask; a.R = R; a.R_per_step = R_per_step;
   a.xf = xf; a.Pf = Pf; a.ld = ld;
   a.t_next = t_next;
-  a.fuse_smoother = smoother;
+  a.fuse_smoother = smoother == 1;
+  a.adj = grad;
   a.wfin_f = level2_result(p, a.wagg_f, p.nf);
-  const bool ll_only = !smoother && !xf && !Pf;
+  const bool ll_only = smoother == 0 && !xf && !Pf;
   double* bnd = reinterpret_cast<double*>(ws_ptr(ws, p.o_bnd));
   PSSGP_DISPATCH(model->d, {
     const DevModel<D> m = dev_model<D>(model);
+    if (grad) {   // the transition after the chunk (zero when the series ends with it)
+      k_discretize_next<D><<<1, 32, 0, s>>>(m, t, n, t_next, bnd + p.nf, a.status);
+      after_launch();
+      a.f_next = bnd + p.nf;
+    }
     if (rank > 0) {   // the filter state before the chunk: chunks 0 .. rank-1 folded
       k_fold_filter_range<D><<<1, 32, 0, s>>>(aggs, 0, rank, bnd, a.status);
       after_launch();
@@ -2645,6 +2686,107 @@ extern "C" int pssgp_split_smooth_finish(const pssgp_model* model, int64_t n, in
     k_smoother_propagate<D><<<grid, BLOCK, 0, s>>>(m, a);
     after_launch();
   });
+  return end_call();
+}
+
+// gradient of a split series: the two backward (adjoint) scans, each with one
+// exchange of chunk aggregates (E = Pi, g, L: the smoother's operator)
+extern "C" int pssgp_split_grad_mean_reduce(const pssgp_model* model, int64_t n, double* agg, void* ws,
+                                            size_t ws_bytes, void* stream) {
+  begin_call();
+  if (!model_ok(model) || !agg || n < 1 || n > PSSGP_NMAX) return PSSGP_EINVAL;
+  const Plan p = make_plan(model->d, n, 0, 0, true);
+  const int rc = check_ws(p, ws, ws_bytes);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScanArgs a = base_args(p, ws);
+  PSSGP_DISPATCH(model->d, {
+    // levels 0-1 of the mean-adjoint scan ran in the adjoint filter pass
+    a.wfin_s = run_smoother_level2<D>(p, a.wagg_s, s);
+    k_pack_aggregate<<<1, 128, 0, s>>>(a.wfin_s, p.P2, p.ns, agg);
+    after_launch();
+  });
+  return end_call();
+}
+
+extern "C" int pssgp_split_grad_mean_finish(const pssgp_model* model, int64_t n, const double* aggs, int32_t G,
+                                            int32_t rank, double* agg_cov, void* ws, size_t ws_bytes,
+                                            void* stream) {
+  begin_call();
+  if (!model_ok(model) || !aggs || !agg_cov || n < 1 || n > PSSGP_NMAX || G < 1 || rank < 0 || rank >= G)
+    return PSSGP_EINVAL;
+  const Plan p = make_plan(model->d, n, 0, 0, true);
+  const int rc = check_ws(p, ws, ws_bytes);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScanArgs a = base_args(p, ws);
+  a.wfin_s = level2_result(p, a.wagg_s, p.ns);
+  double* bnd = reinterpret_cast<double*>(ws_ptr(ws, p.o_bnd));
+  const int grid = (int)(p.P0 / BLOCK);
+  PSSGP_DISPATCH(model->d, {
+    const DevModel<D> m = dev_model<D>(model);
+    if (rank + 1 < G) {   // the mean adjoint after the chunk: chunks rank+1 .. G-1 folded
+      k_fold_smoother_range<D><<<1, 32, 0, s>>>(aggs, rank + 1, G, bnd);
+      after_launch();
+      k_apply_smoother_end<D><<<(unsigned)((p.P2 + BLOCK / 32 - 1) / (BLOCK / 32)), BLOCK, 0, s>>>(
+          const_cast<double*>(a.wfin_s), p.P2, bnd);
+      after_launch();
+      a.end_s = bnd;
+    }
+    {
+      Timed tm(s, T_AMEAN);
+      k_adjoint_mean<D><<<grid, BLOCK, 0, s>>>(m, a);
+      after_launch();
+    }
+    // level 2 of the covariance-adjoint scan and the chunk's aggregate
+    const double* wfin_a = run_smoother_level2<D>(p, a.wagg_a, s);
+    k_pack_aggregate<<<1, 128, 0, s>>>(wfin_a, p.P2, p.ns, agg_cov);
+    after_launch();
+  });
+  return end_call();
+}
+
+extern "C" int pssgp_split_grad_finish(const pssgp_model* model, const double* R, int32_t R_per_step, int64_t n,
+                                       const double* aggs_cov, int32_t G, int32_t rank, double* grad, void* ws,
+                                       size_t ws_bytes, void* stream) {
+  begin_call();
+  if (!model_ok(model) || !R || !aggs_cov || !grad || n < 1 || n > PSSGP_NMAX || G < 1 || rank < 0 || rank >= G)
+    return PSSGP_EINVAL;
+  const Plan p = make_plan(model->d, n, 0, 0, true);
+  const int rc = check_ws(p, ws, ws_bytes);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScanArgs a = base_args(p, ws);
+  a.R = R; a.R_per_step = R_per_step;
+  a.wfin_a = level2_result(p, a.wagg_a, p.ns);
+  double* bnd = reinterpret_cast<double*>(ws_ptr(ws, p.o_bnd));
+  a.f_next = bnd + p.nf;   // written by the filter pass (zero after the series' last chunk)
+  const int grid = (int)(p.P0 / BLOCK);
+  PSSGP_DISPATCH(model->d, {
+    const DevModel<D> m = dev_model<D>(model);
+    if (rank + 1 < G) {   // the covariance adjoint after the chunk: chunks rank+1 .. G-1 folded
+      k_fold_smoother_range<D><<<1, 32, 0, s>>>(aggs_cov, rank + 1, G, bnd);
+      after_launch();
+      k_apply_smoother_end<D><<<(unsigned)((p.P2 + BLOCK / 32 - 1) / (BLOCK / 32)), BLOCK, 0, s>>>(
+          const_cast<double*>(a.wfin_a), p.P2, bnd);
+      after_launch();
+      a.end_s = bnd;
+    }
+    constexpr int asmem = adjoint_smem_doubles<D>() * 8;
+    cudaFuncSetAttribute(k_adjoint_cov<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, asmem);
+    {
+      Timed tm(s, T_ACOV);
+      k_adjoint_cov<D><<<grid, BLOCK, asmem, s>>>(m, a);
+      after_launch();
+    }
+  });
+  {
+    Timed tm(s, T_LL);
+    for (int i = 0; i < 3; ++i) {
+      k_loglik_reduce<<<1, 256, 0, s>>>(a.gpart + i * p.P0, p.P0, grad + i);
+      after_launch();
+    }
+  }
   return end_call();
 }
 

@@ -721,9 +721,17 @@ __device__ __forceinline__ bool fagg_combine_smem(const double* __restrict__ a, 
 // because it contains the first step -- combined with an aggregate b:
 //   M = I + P J_b,  x' = A_b M^{-1} (x + P eta_b) + b_b,
 //   P' = A_b M^{-1} P A_b^T + C_b.
+// The aggregate b is read in place from a packed array (entry e at p[e * st],
+// the layout of store_fagg), so that no copy of it is made.
 template <int D>
-__device__ __noinline__ bool fstate_combine(const Vec<D>& x, const Mat<D>& P, const FAgg<D>& b,
-                                            Vec<D>& xo, Mat<D>& Po) {
+__device__ __noinline__ bool fstate_combine(const Vec<D>& x, const Mat<D>& P, const double* __restrict__ p,
+                                               int64_t st, Vec<D>& xo, Mat<D>& Po) {
+  constexpr int S = Sym<D>::N;
+  auto A_ = [&](int i, int j) { return p[(int64_t)(i * D + j) * st]; };
+  auto C_ = [&](int i, int j) { return p[(int64_t)(D * D + D + (i <= j ? pidx<D>(i, j) : pidx<D>(j, i))) * st]; };
+  auto J_ = [&](int i, int j) {
+    return p[(int64_t)(D * D + 2 * D + S + (i <= j ? pidx<D>(i, j) : pidx<D>(j, i))) * st];
+  };
   Mat<D> M;
 #pragma unroll
   for (int i = 0; i < D; ++i)
@@ -731,7 +739,7 @@ __device__ __noinline__ bool fstate_combine(const Vec<D>& x, const Mat<D>& P, co
     for (int j = 0; j < D; ++j) {
       double s = (i == j) ? 1.0 : 0.0;
 #pragma unroll
-      for (int k = 0; k < D; ++k) s = fma(P[i][k], b.J[k][j], s);
+      for (int k = 0; k < D; ++k) s = fma(P[i][k], J_(k, j), s);
       M[i][j] = s;
     }
   constexpr int NR = D + 1;
@@ -740,7 +748,7 @@ __device__ __noinline__ bool fstate_combine(const Vec<D>& x, const Mat<D>& P, co
   for (int i = 0; i < D; ++i) {
     double s = x[i];
 #pragma unroll
-    for (int k = 0; k < D; ++k) s = fma(P[i][k], b.eta[k], s);
+    for (int k = 0; k < D; ++k) s = fma(P[i][k], p[(int64_t)(D * D + D + S + k) * st], s);
     X[i][0] = s;
 #pragma unroll
     for (int j = 0; j < D; ++j) X[i][1 + j] = P[i][j];
@@ -749,22 +757,31 @@ __device__ __noinline__ bool fstate_combine(const Vec<D>& x, const Mat<D>& P, co
   double invd[D];
   const bool ok = lu_factor<D>(M, perm, invd);
   lu_solve<D, NR>(M, perm, invd, X);
-  Mat<D> T;
+  Mat<D> T, Ab;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) Ab[i][j] = A_(i, j);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    double sx = b.b[i];
+    double sx = p[(int64_t)(D * D + i) * st];
 #pragma unroll
-    for (int k = 0; k < D; ++k) sx = fma(b.A[i][k], X[k][0], sx);
+    for (int k = 0; k < D; ++k) sx = fma(Ab[i][k], X[k][0], sx);
     xo[i] = sx;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       double t = 0.0;
 #pragma unroll
-      for (int k = 0; k < D; ++k) t = fma(b.A[i][k], X[k][1 + j], t);
+      for (int k = 0; k < D; ++k) t = fma(Ab[i][k], X[k][1 + j], t);
       T[i][j] = t;
     }
   }
-  mul_Bt_sym_add<D>(T, b.A, b.C, Po);
+  Mat<D> Cb;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) Cb[i][j] = C_(i, j);
+  mul_Bt_sym_add<D>(T, Ab, Cb, Po);
   return ok;
 }
 

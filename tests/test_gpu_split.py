@@ -154,3 +154,100 @@ def test_split_full_size_rbf(report):
     res = oracle.run(om.make_model("rbf", 1.0, 1.0), t, y, mask, 0.01)
     pick = tpos[::97]
     check(fm[pick], fv[pick], ll, res.f_mean[pick], res.f_var[pick], res.loglik, s.N, 1e-6, report, "2^20 rbf")
+
+
+# ---------------------------------------------------------------------------
+# the gradient over a split series (grad_protocol: the forward exchange, then
+# the mean- and covariance-adjoint exchanges), against the oracle's
+# forward-mode gradient of the whole series.  Tolerance as the unsplit
+# gradient's: per component |g - ref| / max(|ref|, s / sqrt(n_obs),
+# 1e-5 sqrt(n_obs)) <= 1e-8 (Matern), 1e-6 (RBF-6), s the oracle's sum of
+# |per-step term|.
+# ---------------------------------------------------------------------------
+GTOL = {"matern12": 1e-8, "matern32": 1e-8, "matern52": 1e-8, "rbf": 1e-6}
+
+
+def run_split_grad(m, t, y, mask, R, bounds):
+    G = len(bounds)
+    Rs = [R if np.isscalar(R) else dev(R[a:b]) for a, b in bounds]
+    chunks = [split.LibraryChunk(m, dev(t[a:b]), dev(y[a:b]), dev(mask[a:b], torch.uint8), Rs[r], grad=True)
+              for r, (a, b) in enumerate(bounds)]
+    res = split.run_lockstep([split.grad_protocol(c, r, G) for r, c in enumerate(chunks)])
+    for c in chunks:
+        assert P.status(c.ws) == 0
+    lls = {float(r[0].item()) for r in res}
+    gs = {tuple(r[1].cpu().numpy().tolist()) for r in res}
+    assert len(lls) == 1 and len(gs) == 1          # every rank holds the same totals
+    return lls.pop(), np.array(gs.pop())
+
+
+def check_split_grad(kind, ell, s2, t, y, mask, R, ll, g, report, what):
+    rll, rg, sc = oracle.loglik_grad_fwd(kind, ell, s2, t, y, mask, R, with_scale=True)
+    nobs = max(int(mask.sum()), 1)
+    floor = np.maximum(np.asarray(sc) / np.sqrt(nobs), 1e-5 * np.sqrt(nobs))
+    eg = np.max(np.abs(g - rg) / np.maximum(np.abs(rg), floor))
+    el = abs(ll - rll) / max(abs(rll), nobs)
+    tol = GTOL[kind]
+    report(f"split gradient vs forward mode, {what} (tol {tol:g})", eg, tol)
+    assert np.isfinite(eg) and eg <= tol, (what, g, rg, eg)
+    assert el <= TOL.get(kind, 1e-9), (what, ll, rll)
+
+
+@pytest.mark.parametrize("kind", ["matern12", "matern32", "matern52", "rbf"])
+@pytest.mark.parametrize("G", [1, 2, 3, 5])
+def test_split_gradient_equals_forward_mode(kind, G, report):
+    s = wl.random_series(111, 12_000, 0, T=130.0)
+    rng = np.random.default_rng(112)
+    mask = (rng.uniform(size=s.N) > 0.1).astype(np.uint8)
+    m = P.build_model(kind, 0.7, 1.3)
+    ll, g = run_split_grad(m, s.t_train, s.y_train, mask, 0.02, split.chunk_bounds(s.N, G))
+    check_split_grad(kind, 0.7, 1.3, s.t_train, s.y_train, mask, 0.02, ll, g, report, f"{kind}, G={G}")
+
+
+def test_split_gradient_g1_equals_the_unsplit_call():
+    """One chunk runs the unsplit gradient's kernels on the same elements: the
+    same sums to the last bits (a few ulps of the reduction order at most)."""
+    s = wl.random_series(113, 20_000, 0, T=200.0)
+    mask = np.ones(s.N, np.uint8)
+    m = P.build_model("matern52", 0.9, 1.1)
+    ll1, g1, ws = P.loglik_grad(m, dev(s.t_train), dev(s.y_train), dev(mask, torch.uint8), 0.03)
+    assert P.status(ws) == 0
+    ll, g = run_split_grad(m, s.t_train, s.y_train, mask, 0.03, [(0, s.N)])
+    g1 = g1.cpu().numpy()
+    assert abs(ll - float(ll1.item())) <= 1e-13 * abs(ll)
+    assert np.all(np.abs(g - g1) <= 1e-12 * np.maximum(np.abs(g1), 1.0))
+
+
+def test_split_gradient_uneven_chunks_gaps_ties_and_per_step_noise(report):
+    """Chunks of 1, 2 and 33 steps, a chunk that is one missing step, a chunk
+    boundary across a gap of 40 lengthscales and one inside a run of ties
+    (a zero-length transition between chunks), per-step noise variances."""
+    s = wl.random_series(114, 6_000, 0, T=66.0)
+    t = s.t_train.copy()
+    t[3300:] += 40.0
+    t[4999:5003] = t[4999]
+    mask = (np.random.default_rng(115).uniform(size=s.N) > 0.2).astype(np.uint8)
+    mask[3300] = 0
+    mask[36] = 0
+    R = np.exp(np.random.default_rng(116).uniform(np.log(1e-3), np.log(1e-1), s.N))
+    bounds = [(0, 1), (1, 3), (3, 36), (36, 37), (37, 3300), (3300, 5001), (5001, s.N)]
+    for kind in ("matern32", "rbf"):
+        m = P.build_model(kind, 1.0, 1.0)
+        ll, g = run_split_grad(m, t, s.y_train, mask, R, bounds)
+        check_split_grad(kind, 1.0, 1.0, t, s.y_train, mask, R, ll, g, report, f"uneven chunks, {kind}")
+
+
+def test_split_gradient_full_size_rbf(report):
+    """2^20 training steps (RBF-6) in 4 chunks against the unsplit library
+    gradient and the oracle's forward mode."""
+    s = wl.sinusoid_large(M=0)
+    mask = np.ones(s.N, np.uint8)
+    m = P.build_model("rbf", 1.0, 1.0)
+    ll, g = run_split_grad(m, s.t_train, s.y_train, mask, 0.01, split.chunk_bounds(s.N, 4))
+    ll1, g1, ws = P.loglik_grad(m, dev(s.t_train), dev(s.y_train), dev(mask, torch.uint8), 0.01)
+    assert P.status(ws) == 0
+    g1 = g1.cpu().numpy()
+    e1 = np.max(np.abs(g - g1) / np.maximum(np.abs(g1), 1e-5 * np.sqrt(s.N)))
+    report("split 2^20 rbf gradient vs unsplit pssgp_loglik_grad", e1, 1e-8)
+    assert e1 <= 1e-8 and abs(ll - float(ll1.item())) <= 1e-11 * max(abs(ll), s.N)
+    check_split_grad("rbf", 1.0, 1.0, s.t_train, s.y_train, mask, 0.01, ll, g, report, "2^20 rbf")

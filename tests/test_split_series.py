@@ -210,6 +210,94 @@ def test_gloo_ranks_equal_the_single_rank_oracle(oracle_lib, world):
     _check(kind, m, t, y, mask, 0.02, fm, fv, res[0][2])
 
 
+class RecordingGradChunk:
+    """A chunk for grad_protocol whose every result encodes (rank, stage), and
+    which checks what each exchange hands it: the [G, ...] stack of all ranks'
+    results of the stage in rank order, and the neighbours' boundary times."""
+
+    def __init__(self, rank, G, t):
+        self.rank, self.G, self.t = rank, G, t
+        self.seen = []
+
+    def _mine(self, stage):
+        return torch.tensor([100.0 * self.rank + stage, float(self.G)], dtype=torch.float64)
+
+    def _check_stack(self, aggs, stage):
+        want = torch.stack([torch.tensor([100.0 * r + stage, float(self.G)], dtype=torch.float64)
+                            for r in range(self.G)])
+        assert torch.equal(aggs, want)
+        self.seen.append(stage)
+
+    def time_ends(self):
+        return torch.tensor([self.t[0], self.t[-1]], dtype=torch.float64)
+
+    def filter_reduce(self, t_prev, t_next):
+        r = self.rank
+        assert math.isnan(t_prev) if r == 0 else t_prev == 10.0 * r - 1.0
+        assert math.isnan(t_next) if r + 1 == self.G else t_next == 10.0 * (r + 1)
+        return self._mine(1)
+
+    def filter_finish(self, aggs, rank):
+        assert rank == self.rank
+        self._check_stack(aggs, 1)
+        return torch.tensor([float(rank + 1)], dtype=torch.float64)
+
+    def mean_adjoint_reduce(self):
+        return self._mine(2)
+
+    def mean_adjoint_finish(self, aggs, rank):
+        self._check_stack(aggs, 2)
+        return self._mine(3)
+
+    def grad_finish(self, aggs, rank):
+        self._check_stack(aggs, 3)
+        return torch.tensor([1.0, float(rank), -2.0], dtype=torch.float64)
+
+
+def _recording_chunks(G):
+    return [RecordingGradChunk(r, G, np.array([10.0 * r, 10.0 * r + 5.0, 10.0 * r + 9.0])) for r in range(G)]
+
+
+def _grad_totals(G):
+    return G * (G + 1) / 2, [float(G), G * (G - 1) / 2, -2.0 * G]
+
+
+@pytest.mark.parametrize("G", [1, 2, 4])
+def test_grad_protocol_exchanges_in_lockstep(G):
+    chunks = _recording_chunks(G)
+    res = split.run_lockstep([split.grad_protocol(c, r, G) for r, c in enumerate(chunks)])
+    ll, g = _grad_totals(G)
+    for c, (rll, rg) in zip(chunks, res):
+        assert c.seen == [1, 2, 3]
+        assert float(rll) == ll and rg.tolist() == g
+
+
+def _grad_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        c = _recording_chunks(world)[rank]
+        ll, g = split.run_distributed(split.grad_protocol(c, rank, world))
+        out[rank] = (c.seen, float(ll), g.tolist())
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_grad_protocol_on_gloo_ranks():
+    world = 3
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        mp.start_processes(_grad_worker, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
+        res = dict(out)
+    ll, g = _grad_totals(world)
+    assert sorted(res) == list(range(world))
+    for r in range(world):
+        assert res[r] == ([1, 2, 3], ll, g)
+
+
 def test_lockstep_rejects_ranks_that_disagree():
     def a():
         yield ("all_gather", torch.zeros(1))
