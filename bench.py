@@ -37,8 +37,8 @@ METRIC = "filter+smoother time steps/s at N=2^20,d=6 FP64"
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels at the
 # 2^20 workload itself; a launch's traffic is this x n.  Reset an entry to None
 # whenever its kernel changes.
-PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1439.4, "filter_reduce": 477.3, "discretize": 415.2,
-                                "smoother_propagate": 682.5}
+PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1310.1, "filter_reduce": 801.4, "discretize": 415.2,
+                                "smoother_propagate": 682.7}
 UNIT = "steps/s"
 BATCH_SIM_SEED = 300          # prior simulation of the batched workload (family i: seed + i)
 WORKLOADS = {
@@ -904,6 +904,29 @@ def run_split(args, wl_params):
     # + the kernels the timing slots do not cover: two aggregate packs, and a
     # fold and an apply per exchange direction that has other chunks
     launches = sum(c for _, c in per.values()) + 2 + 2 * (rank > 0) + 2 * (rank + 1 < world)
+
+    # the gradient of the log-likelihood over the same split (training times
+    # only, grad_protocol), timed after the prediction steps
+    gws = P.workspace_grad(m.d, tt.numel(), dev)
+    gmask = torch.ones(tt.numel(), dtype=torch.uint8, device=dev)
+
+    def gstep():
+        gen = SP.grad_protocol(SP.LibraryChunk(m, tt, yy, gmask, R, ws=gws, grad=True), rank, world)
+        return SP.run_distributed(gen) if world > 1 else SP.run_lockstep([gen])[0]
+
+    for _ in range(max(args.warmup, 3)):
+        gstep()
+    torch.cuda.synchronize()
+    assert P.status(gws) == 0, "device status error (split gradient)"
+    barrier()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        gstep()
+    g1.record(stream)
+    g1.synchronize()
+    barrier()
+    gms = max_over_ranks(g0.elapsed_time(g1) / args.steps, world, dev)
     line = {"metric": METRIC, "value": n_total / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -913,7 +936,10 @@ def run_split(args, wl_params):
                        "merged_steps_total": int(n_total), "merged_steps_this_rank": int(n_rank),
                        "l2": "workspace traffic ~1 GB per step exceeds the 126 MB L2 (no explicit flush)"},
             "gpu_launches": int(launches * args.steps), "clocks": clocks,
-            "kernels_ms": {k: round(v[0], 4) for k, v in per.items()}}
+            "kernels_ms": {k: round(v[0], 4) for k, v in per.items()},
+            "gradient": {"what": "log-likelihood and its gradient (log lengthscale, log variance, log noise) of "
+                                 "the 2^20 training steps over the same split (three all-gathers, one all-reduce)",
+                         "ms_per_eval": round(gms, 4), "steps_per_s": s.N / (gms * 1e-3)}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
