@@ -58,9 +58,11 @@ def parse():
     ap.add_argument("--timing-steps", type=int, default=3)
     ap.add_argument("--warps-per-sm", type=int, default=0, help="scan lanes per SM / 32 (0 = library default)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 4,096-series batched measurement")
-    ap.add_argument("--streams", type=int, default=4,
-                    help="streams (each with its own workspace) that the timed steps alternate over "
-                         "(measured at 2^20 RBF-6: 2 -> 196, 3 -> 204, 4 -> 206, 6 -> 206 M steps/s)")
+    ap.add_argument("--streams", type=int, default=8,
+                    help="streams (each with its own workspace) that the timed steps alternate over")
+    ap.add_argument("--concurrent-warps", type=int, default=2,
+                    help="scan lanes per SM / 32 of each prediction while several run on the streams "
+                         "(0 = the library default, which targets one prediction at a time)")
     ap.add_argument("--no-fit", action="store_true", help="skip the learned-vs-plain fit and Table-1 measurements")
     ap.add_argument("--no-gradient", action="store_true", help="skip the log-likelihood gradient measurement")
     ap.add_argument("--no-fit-adam", action="store_true", help="skip the Adam fits (about a minute and a half)")
@@ -626,9 +628,13 @@ def run_ours(args, wl_params):
             dist.barrier()
 
     # --- device-timed region (inputs resident in HBM) ---
-    # one stream first (reported as ms_per_step_one_stream), then the timed
-    # value: steps alternate between --streams streams (4) with a workspace each, so
-    # one step's low-occupancy scan rounds overlap the next step's kernels
+    # one stream first at the library's default tuning (reported as
+    # ms_per_step_one_stream: the latency of one prediction), then the timed
+    # value: steps alternate between --streams streams with a workspace each,
+    # each prediction on --concurrent-warps warps per SM (fewer, longer lane
+    # chunks: less scan overhead per step, while the predictions in flight
+    # together fill the SMs; one step's low-occupancy scan rounds also
+    # overlap the other steps' kernels)
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -640,6 +646,9 @@ def run_ours(args, wl_params):
     ms_one = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
 
     ns = max(1, args.streams)
+    w_default = P.tune_get(m.d)
+    w_conc = args.concurrent_warps or w_default
+    P.tune_set(m.d, w_conc)
     dstreams = [torch.cuda.Stream() for _ in range(ns)]
     wsbs = [wsb] + [P.workspace(m.d, n, dev) for _ in range(ns - 1)]
     outs = [out] + [tuple(torch.empty_like(o) for o in out) for _ in range(ns - 1)]
@@ -710,21 +719,28 @@ def run_ours(args, wl_params):
     e2e = {"value": job_throughput(n, world, ms_e2e), "unit": UNIT,
            "h2d_bytes_per_step": int((2 * N + M) * 8), "d2h_bytes_per_step": int((2 * M + 1) * 8)}
 
-    # --- per-kernel times (events around each launch) for the roofline ---
+    # launches per step at the tuning of the timed region
+    P.timing(1)
+    step()
+    torch.cuda.synchronize()
+    gpu_launches = sum(c for _, c in P.timing(2).values()) * args.steps
+    P.timing(0)
+    P.tune_set(m.d, w_default)
+
+    # --- per-kernel times (events around each launch) for the roofline, at
+    # the default tuning (one prediction on the whole GPU) ---
     P.timing(1)
     for _ in range(args.timing_steps):
         step()
     torch.cuda.synchronize()
     per = P.timing(2)
     P.timing(0)
-    launches = sum(c for _, c in per.values()) // max(args.timing_steps, 1)
-    gpu_launches = launches * args.steps
     sm_mhz = clocks.get("sm_mhz") if isinstance(clocks, dict) else None
     peak_tflops, nominal_tflops = fp64_peaks(P, dev, sm_mhz)
 
     t_merged = np.sort(np.concatenate([s.t_train, s.t_test]), kind="stable")
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    lanes, L = lane_plan(n, sms, args.warps_per_sm or 4)
+    lanes, L = lane_plan(n, sms, w_default)
     kf, kq = taylor_terms(m, t_merged, lanes, L)
     d = m.d
     obs = N / n
@@ -758,7 +774,11 @@ def run_ours(args, wl_params):
             "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_one_stream": round(ms_one, 4),
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.workload, d, n),
+            "config": {**workload_config(args.workload, d, n),
+                       "concurrency": f"value and e2e: {ns} predictions in flight on {ns} streams, each on "
+                                      f"{w_conc} warps per SM ({lane_plan(n, sms, w_conc)[0]} lane chunks); "
+                                      f"ms_per_step_one_stream and roofline: one prediction at a time on "
+                                      f"{w_default} warps per SM ({lane_plan(n, sms, w_default)[0]} lane chunks)"},
             "e2e": e2e, "gpu_launches": int(gpu_launches), "clocks": clocks, "roofline": roofline,
             "whole_path_tflops": round(whole, 4), "kernels": kernels}
     if not args.no_batched:

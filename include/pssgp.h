@@ -476,10 +476,14 @@ int pssgp_timing(int32_t mode, double* ms, int64_t* counts, int32_t nslots);
 const char* pssgp_timing_name(int32_t slot);
 
 /* Scan tuning: the number of chunks ("lanes", one per thread) of the scans
- * is SMs x warps_per_sm x 32, i.e. n / (SMs x warps_per_sm x 32) steps per
- * thread; warps_per_sm is 4, 8, 12 or 16 (default 8 for d <= 3, else 4).  More lanes give each
- * SM more warps to hide latency but shorter chunks and more scan overhead.
- * Affects calls planned afterwards.  pssgp_set_warps_per_sm sets every state
+ * is SMs x warps_per_sm x 32 (rounded up to whole blocks of 128), i.e.
+ * n / (SMs x warps_per_sm x 32) steps per thread; warps_per_sm is 1 to 16
+ * (default 8 for d <= 3, else 4).  More lanes give each SM more warps to
+ * hide latency but shorter chunks and more scan overhead.  Below 4 one call
+ * leaves SMs idle: meant for several independent calls in flight on
+ * different streams, where fewer, longer chunks per call cut the scan
+ * overhead per step while the calls together fill the GPU.  PSSGP_EINVAL
+ * outside 1..16.  Affects calls planned afterwards.  pssgp_set_warps_per_sm sets every state
  * dimension; pssgp_tune_set one (PSSGP_EDIM for d outside 1..8);
  * pssgp_tune_get returns the current value for d. */
 int pssgp_set_warps_per_sm(int32_t warps_per_sm);

@@ -3056,7 +3056,7 @@ extern "C" int pssgp_loglik_noalloc(const pssgp_model* model, const double* t, c
 }
 
 extern "C" int pssgp_set_warps_per_sm(int32_t warps_per_sm) {
-  if (warps_per_sm < 4 || warps_per_sm > WARPS_MAX || warps_per_sm % 4) return PSSGP_EINVAL;
+  if (warps_per_sm < 1 || warps_per_sm > WARPS_MAX) return PSSGP_EINVAL;
   std::lock_guard<std::mutex> lk(g_mu);
   for (int d = 0; d <= PSSGP_DMAX; ++d) g_warps_per_sm[d] = warps_per_sm;
   return PSSGP_OK;
@@ -3064,7 +3064,7 @@ extern "C" int pssgp_set_warps_per_sm(int32_t warps_per_sm) {
 
 extern "C" int pssgp_tune_set(int32_t d, int32_t warps_per_sm) {
   if (d < 1 || d > PSSGP_DMAX) return PSSGP_EDIM;
-  if (warps_per_sm < 4 || warps_per_sm > WARPS_MAX || warps_per_sm % 4) return PSSGP_EINVAL;
+  if (warps_per_sm < 1 || warps_per_sm > WARPS_MAX) return PSSGP_EINVAL;
   std::lock_guard<std::mutex> lk(g_mu);
   g_warps_per_sm[d] = warps_per_sm;
   return PSSGP_OK;

@@ -238,7 +238,12 @@ def test_host_argument_errors_of_the_newer_entry_points(lib):
     # workspaces
     assert lib.pssgp_workspace_size_grad(3, 1000) > lib.pssgp_workspace_size(3, 1000)
     assert lib.pssgp_fit_workspace_size(3, 1000, 4) > lib.pssgp_workspace_size_grad(3, 1000)
-    assert lib.pssgp_tune_set(0, 8) == -2 and lib.pssgp_tune_set(3, 5) == EINVAL and lib.pssgp_tune_get(9) == -2
+    assert lib.pssgp_tune_set(0, 8) == -2 and lib.pssgp_tune_get(9) == -2
+    assert lib.pssgp_tune_set(3, 0) == EINVAL and lib.pssgp_tune_set(3, 17) == EINVAL
+    assert lib.pssgp_set_warps_per_sm(0) == EINVAL and lib.pssgp_set_warps_per_sm(17) == EINVAL
+    old = lib.pssgp_tune_get(3)
+    assert lib.pssgp_tune_set(3, 2) == 0 and lib.pssgp_tune_get(3) == 2
+    assert lib.pssgp_tune_set(3, old) == 0
 
 
 def test_noalloc_size_limits_stated_in_the_header(lib):
