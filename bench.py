@@ -37,8 +37,8 @@ METRIC = "filter+smoother time steps/s at N=2^20,d=6 FP64"
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels at the
 # 2^20 workload itself; a launch's traffic is this x n.  Reset an entry to None
 # whenever its kernel changes.
-PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1310.1, "filter_reduce": 801.4, "discretize": 415.2,
-                                "smoother_propagate": 682.7}
+PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1375.0, "filter_reduce": 477.6, "discretize": 415.3,
+                                "smoother_propagate": 682.8}
 UNIT = "steps/s"
 BATCH_SIM_SEED = 300          # prior simulation of the batched workload (family i: seed + i)
 WORKLOADS = {
@@ -50,7 +50,7 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rbf6", choices=list(WORKLOADS))

@@ -123,6 +123,7 @@ struct Plan {
   int64_t P0;        // lanes (multiple of BLOCK)
   int64_t P2;        // warps
   int64_t L;         // steps per lane
+  int warps;         // the tuning the plan was made for (lanes per SM / 32)
   int nf, ns;        // aggregate sizes (doubles)
   int fqs, egs;      // per-step record strides (doubles, even)
   // byte offsets into the workspace
@@ -140,7 +141,8 @@ Plan make_plan(int d, int64_t n, int64_t lanes_req, int warps = 0, bool grad = f
   Plan p{};
   p.d = d;
   p.n = n;
-  const int64_t lanes_max = (int64_t)num_sms() * (warps > 0 ? warps : warps_for(d)) * 32;
+  p.warps = warps > 0 ? warps : warps_for(d);
+  const int64_t lanes_max = (int64_t)num_sms() * p.warps * 32;
   const int64_t want = (n + MIN_CHUNK - 1) / MIN_CHUNK;
   int64_t P0 = std::min(lanes_max, std::max<int64_t>(want, 1));
   if (lanes_req > 0) P0 = lanes_req;
@@ -627,20 +629,21 @@ enum { RED_PLAIN = 0, RED_LL = 1, RED_SMOOTH = 2, RED_ADJ = 3 };
 // overlapping the fold's region (the fold is done when the scan starts); 189
 // doubles per thread (194 KB per block) at d = 6.  Below d = 4 the aggregates
 // are small enough for registers, above d = 6 the buffers would not fit.
-// The prediction's instance (RED_SMOOTH) keeps the scan on register/local
-// operands and its 101 KB of shared memory: then a block of another stream's
-// filter pass (114 KB) fits beside it on an SM, and steps alternating over
-// streams overlap (measured at 2^20 RBF-6: 226 M steps/s with four streams
-// against 217 M with the shared-memory scan, which makes one call 1.7 %
-// faster instead: 5.36 against 5.45 ms).
-template <int D, int RMODE> __host__ __device__ constexpr bool reduce_l1_smem() {
-  return D >= 4 && D <= 6 && RMODE != RED_SMOOTH;
-}
+// The other form runs the scan on register/local operands and keeps the
+// fold's 101 KB of shared memory only, so that a block of another call's
+// filter pass (114 KB) fits beside it on an SM.  The prediction's instance
+// (RED_SMOOTH) takes the shared-memory form when the call is planned on the
+// whole GPU (4 or more warps per SM: one call at a time) and the small form
+// when it is planned on fewer (several calls in flight on streams, which
+// overlap only if their blocks share SMs).  Measured at 2^20 RBF-6: one call
+// 5.35 against 5.44 ms; eight calls in flight at 2 warps per SM 235 against
+// 240 M steps/s, four at 4 warps per SM 217 against 226 M.
+template <int D> __host__ __device__ constexpr bool l1_smem_fits() { return D >= 4 && D <= 6; }
 template <int D> __host__ __device__ constexpr int reduce_fold_doubles() { return 2 * D * D + Sym<D>::N + D; }
-template <int D, int RMODE> constexpr int reduce_smem_doubles() {
-  return (reduce_l1_smem<D, RMODE>() ? FAggSize<D>::N + (reduce_fold_doubles<D>() > FAggSize<D>::N
-                                                             ? reduce_fold_doubles<D>() : FAggSize<D>::N)
-                                     : reduce_fold_doubles<D>()) * BLOCK;
+template <int D, bool L1S> constexpr int reduce_smem_doubles() {
+  return (L1S ? FAggSize<D>::N + (reduce_fold_doubles<D>() > FAggSize<D>::N ? reduce_fold_doubles<D>()
+                                                                            : FAggSize<D>::N)
+              : reduce_fold_doubles<D>()) * BLOCK;
 }
 
 // RMODE:
@@ -671,7 +674,7 @@ __device__ __forceinline__ void save_fold_state(const ScanArgs& a, int64_t g, co
   for (int e = 0; e < Sym<D>::N; ++e) a.lane_fp[(D * D + D + e) * a.P0 + g] = J[e * SST];
 }
 
-template <int D, int RMODE>
+template <int D, int RMODE, bool L1S>
 __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m, const ScanArgs a) {
   constexpr int RB = BLOCK;   // threads per block (stride of the per-thread arrays)
   constexpr bool LL = RMODE == RED_LL;
@@ -679,7 +682,6 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
   // in the others they cost more register spills than they saved
   constexpr bool VECMODE = RMODE == RED_ADJ;
   extern __shared__ double smem[];
-  constexpr bool L1S = reduce_l1_smem<D, RMODE>();
   constexpr int NF = FAggSize<D>::N;
   double* sB0 = smem + threadIdx.x;                    // level-1 buffer 0 (shared-memory scan)
   double* sA0 = smem + (L1S ? NF * RB : 0) + threadIdx.x;
@@ -2157,13 +2159,17 @@ void run_filter_front(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStre
     after_launch();
   }
   {
-    auto kern = ll_only ? k_filter_reduce<D, RED_LL>
-                : a.adj ? k_filter_reduce<D, RED_ADJ>
-                        : a.fuse_smoother ? k_filter_reduce<D, RED_SMOOTH> : k_filter_reduce<D, RED_PLAIN>;
-    const int smem = 8 * (ll_only ? reduce_smem_doubles<D, RED_LL>()
-                          : a.adj ? reduce_smem_doubles<D, RED_ADJ>()
-                                  : a.fuse_smoother ? reduce_smem_doubles<D, RED_SMOOTH>()
-                                                    : reduce_smem_doubles<D, RED_PLAIN>());
+    constexpr bool L1S = l1_smem_fits<D>();
+    // the prediction's instance: the shared-memory scan only when the call
+    // has the whole GPU (see l1_smem_fits)
+    const bool smooth_l1s = L1S && p.warps >= 4;
+    auto kern = ll_only ? k_filter_reduce<D, RED_LL, L1S>
+                : a.adj ? k_filter_reduce<D, RED_ADJ, L1S>
+                : a.fuse_smoother ? (smooth_l1s ? k_filter_reduce<D, RED_SMOOTH, L1S>
+                                                : k_filter_reduce<D, RED_SMOOTH, false>)
+                                  : k_filter_reduce<D, RED_PLAIN, L1S>;
+    const int smem = 8 * ((!a.adj && !ll_only && a.fuse_smoother && !smooth_l1s) ? reduce_smem_doubles<D, false>()
+                                                                                   : reduce_smem_doubles<D, L1S>());
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     Timed tm(s, T_FRED);
     kern<<<grid, BLOCK, smem, s>>>(m, a);
