@@ -774,11 +774,11 @@ def run_ours(args, wl_params):
             "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_one_stream": round(ms_one, 4),
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {**workload_config(args.workload, d, n),
-                       "concurrency": f"value and e2e: {ns} predictions in flight on {ns} streams, each on "
-                                      f"{w_conc} warps per SM ({lane_plan(n, sms, w_conc)[0]} lane chunks); "
-                                      f"ms_per_step_one_stream and roofline: one prediction at a time on "
-                                      f"{w_default} warps per SM ({lane_plan(n, sms, w_default)[0]} lane chunks)"},
+            "config": workload_config(args.workload, d, n),
+            "concurrency": f"value and e2e: {ns} predictions in flight on {ns} streams, each on "
+                           f"{w_conc} warps per SM ({lane_plan(n, sms, w_conc)[0]} lane chunks); "
+                           f"ms_per_step_one_stream and roofline: one prediction at a time on "
+                           f"{w_default} warps per SM ({lane_plan(n, sms, w_default)[0]} lane chunks)",
             "e2e": e2e, "gpu_launches": int(gpu_launches), "clocks": clocks, "roofline": roofline,
             "whole_path_tflops": round(whole, 4), "kernels": kernels}
     if not args.no_batched:
