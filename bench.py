@@ -780,7 +780,8 @@ def run_ours(args, wl_params):
                            f"ms_per_step_one_stream and roofline: one prediction at a time on "
                            f"{w_default} warps per SM ({lane_plan(n, sms, w_default)[0]} lane chunks)",
             "e2e": e2e, "gpu_launches": int(gpu_launches), "clocks": clocks, "roofline": roofline,
-            "whole_path_tflops": round(whole, 4), "kernels": kernels}
+            "whole_path_tflops": round(whole, 4), "whole_path_frac": round(whole / peak_tflops, 4),
+            "kernels": kernels}
     if not args.no_batched:
         line["batched"] = batched_bench(args, P, wl, dev, barrier, world, rank)
     if not args.no_gradient:
