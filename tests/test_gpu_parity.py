@@ -130,14 +130,60 @@ def test_predict_large_workload_prefix(kind, n_train):
     check_marginals(mean, var, ll, fm, fv, res.loglik, s.N, TOL[kind], f"{kind}/{n_train}")
 
 
+class _tuning:
+    """Scan tuning (warps per SM) for state dimension d inside the block."""
+
+    def __init__(self, d, warps):
+        self.d, self.warps = d, warps
+
+    def __enter__(self):
+        self.old = P.tune_get(self.d)
+        P.tune_set(self.d, self.warps)
+
+    def __exit__(self, *exc):
+        P.tune_set(self.d, self.old)
+        return False
+
+
+@pytest.mark.parametrize("warps", [0, 2])
 @pytest.mark.parametrize("kind", ["rbf", "matern52"])
-def test_predict_full_size(kind):
-    """The full 2^20 + 10^4 workload in the launch configuration of the benchmark."""
+def test_predict_full_size(kind, warps):
+    """The full 2^20 + 10^4 workload in the launch configurations of the
+    benchmark: one prediction at a time (the default tuning) and each of
+    several concurrent predictions (2 warps per SM)."""
     s = wl.sinusoid_large()
-    mean, var, ll, st = run_predict(kind, s, 0.01)
+    d = P.build_model(kind, 1.0, 1.0).d
+    with _tuning(d, warps or P.tune_get(d)):
+        mean, var, ll, st = run_predict(kind, s, 0.01)
     assert st == 0
     fm, fv, res, _ = oracle_predict(kind, s, 0.01)
-    check_marginals(mean, var, ll, fm, fv, res.loglik, s.N, TOL[kind], f"full/{kind}")
+    check_marginals(mean, var, ll, fm, fv, res.loglik, s.N, TOL[kind], f"full/{kind}/warps {warps or 'default'}")
+
+
+@pytest.mark.parametrize("kind,order", [("rbf", 6), ("rbf", 4), ("matern52", 0)])
+def test_predict_at_every_lane_tuning(kind, order):
+    """1 to 8 warps per SM: the lane chunks change length (and, at d = 4..6,
+    the prediction's reduce pass switches between its shared-memory and
+    register warp scans at 4 warps per SM); every tuning must agree with the
+    oracle and, to rounding, with the others."""
+    s = wl.prefix(wl.sinusoid_large(), 150_001)
+    o = om.make_model(kind, 1.0, 1.0, order=order) if order else om.make_model(kind, 1.0, 1.0)
+    fm, fv, res, _ = oracle.predict(o, s.t_train, s.y_train, s.t_test, 0.01)
+    m = P.build_model(kind, 1.0, 1.0, order=order) if order else P.build_model(kind, 1.0, 1.0)
+    tol = TOL[kind]
+    outs = []
+    for warps in (1, 2, 3, 4, 8):
+        with _tuning(m.d, warps):
+            mean, var, ll, ws = P.predict(m, dev(s.t_train), dev(s.y_train), dev(s.t_test), 0.01)
+            assert P.status(ws) == 0
+        mean, var, ll = host(mean), host(var), float(host(ll)[0])
+        check_marginals(mean, var, ll, fm, fv, res.loglik, s.N, tol, f"tuning/{kind}{order or ''}/warps {warps}")
+        outs.append((mean, var, ll))
+    m0, v0, l0 = outs[3]
+    for mean, var, ll in outs:
+        assert np.max(np.abs(mean - m0) / np.maximum(np.abs(m0), np.sqrt(v0))) <= 1e-11
+        assert np.max(np.abs(var - v0) / v0) <= 1e-11
+        assert abs(ll - l0) <= 1e-12 * max(abs(l0), s.N)
 
 
 # --------------------------------------------------------------------------
