@@ -659,7 +659,10 @@ template <int D, bool L1S> constexpr int reduce_smem_doubles() {
 //    (F = I, Q = 0): the aggregate then takes the predicted state of the
 //    chunk's first step as input; its (A, eta, J) go to lane_fp (for the
 //    mean-adjoint chunk aggregate of k_filter_propagate), and the transition
-//    is put back in front (one operator application) for the scan.
+//    is put back in front (one operator application) for the scan: in
+//    shared memory with the transition read from its record
+//    (fagg_transition_combine_smem) where the scan runs there, else on
+//    register operands.
 
 // A, eta, J: this thread's entries in shared memory with stride SST (the
 // block's thread count)
@@ -776,35 +779,7 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
     // the chunk aggregate, packed into buffer 0, then the level-1 scan in
     // shared memory (partner lane's aggregate read in place, no shuffles)
     double* B0 = sB0;
-    if constexpr (RMODE == RED_ADJ) {
-      // the transition of step k0 in front: (F, 0, Q, 0, 0) x aggregate (registers, once per lane)
-      FAgg<D> ag;
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        ag.b[i] = b[i];
-        ag.eta[i] = seta[i * RB];
-#pragma unroll
-        for (int jj = 0; jj < D; ++jj) {
-          ag.A[i][jj] = Ain[(i * D + jj) * RB];
-          ag.C[i][jj] = C[i][jj];
-          ag.J[i][jj] = sJ[(i <= jj ? pidx<D>(i, jj) : pidx<D>(jj, i)) * RB];
-        }
-      }
-      if (k1 > k0) {
-        FAgg<D> T, r;
-        load_fq<D>(a.rec_fq, k0, T.A, T.C);
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-          T.b[i] = 0.0;
-          T.eta[i] = 0.0;
-#pragma unroll
-          for (int j = 0; j < D; ++j) T.J[i][j] = 0.0;
-        }
-        if (!fagg_combine<D>(T, ag, r)) bad = true;
-        ag = r;
-      }
-      store_fagg<D>(B0, RB, ag);
-    } else {
+    {
 #pragma unroll
       for (int e = 0; e < D * D; ++e) B0[e * RB] = Ain[e * RB];
 #pragma unroll
@@ -817,6 +792,14 @@ __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m,
       for (int i = 0; i < D; ++i) B0[(D * D + D + Sym<D>::N + i) * RB] = seta[i * RB];
 #pragma unroll
       for (int e = 0; e < Sym<D>::N; ++e) B0[(D * D + 2 * D + Sym<D>::N + e) * RB] = sJ[e * RB];
+    }
+    if constexpr (RMODE == RED_ADJ) {
+      // the transition of step k0 in front, (F, 0, Q, 0, 0) x aggregate, once
+      // per lane: into the fold's (now free) region, then back to buffer 0
+      if (k1 > k0) {
+        if (!fagg_transition_combine_smem<D, RB>(a.rec_fq + k0 * fqs_of<D>(), B0, sA0)) bad = true;
+        for (int e = 0; e < NF; ++e) B0[e * RB] = sA0[e * RB];
+      }
     }
     if (a.dbg_agg) {
       for (int e = 0; e < NF; ++e) a.dbg_agg[e * a.P0 + g] = B0[e * RB];

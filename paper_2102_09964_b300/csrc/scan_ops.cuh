@@ -717,6 +717,118 @@ __device__ __forceinline__ bool fagg_combine_smem(const double* __restrict__ a, 
   return ok;
 }
 
+// T x b for the transition element of one step, T = (F, 0, Q, 0, 0), read
+// from the step's F/Q record (F row-major, then Q packed upper), b and o as
+// in fagg_combine_smem.  With b_a = 0, eta_a = 0 and J_a = 0 the operator
+// reduces to (v = eta_b, x_v = x_b):
+//   M = I + Q J_b,  x_b = M^{-1} Q eta_b,  b = A_b x_b + b_b,
+//   eta = F^T (eta_b - J_b x_b),  C = A_b M^{-1} Q A_b^T + C_b,
+//   A = A_b M^{-1} F,  J = F^T J_b M^{-1} F.
+template <int D, int SST>
+__device__ __noinline__ bool fagg_transition_combine_smem(const double* __restrict__ rec,
+                                                             const double* __restrict__ b,
+                                                             double* __restrict__ o) {
+  constexpr int S = Sym<D>::N;
+  constexpr int OA = 0, OB = D * D, OC = D * D + D, OE = D * D + D + S, OJ = D * D + 2 * D + S;
+  auto F_ = [&](int i, int j) { return rec[i * D + j]; };
+  auto Q_ = [&](int i, int j) { return rec[D * D + (i <= j ? pidx<D>(i, j) : pidx<D>(j, i))]; };
+  auto A_ = [](const double* p, int i, int j) { return p[(OA + i * D + j) * SST]; };
+  auto b_ = [](const double* p, int i) { return p[(OB + i) * SST]; };
+  auto C_ = [](const double* p, int i, int j) { return p[(OC + (i <= j ? pidx<D>(i, j) : pidx<D>(j, i))) * SST]; };
+  auto e_ = [](const double* p, int i) { return p[(OE + i) * SST]; };
+  auto J_ = [](const double* p, int i, int j) { return p[(OJ + (i <= j ? pidx<D>(i, j) : pidx<D>(j, i))) * SST]; };
+  Mat<D> M;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double s = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) s = fma(Q_(i, k), J_(b, k, j), s);
+      M[i][j] = s;
+    }
+  double x[D][1];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) s = fma(Q_(i, k), e_(b, k), s);
+    x[i][0] = s;
+  }
+  int perm[D];
+  double invd[D];
+  const bool ok = lu_factor<D>(M, perm, invd);
+  lu_solve<D, 1>(M, perm, invd, x);
+  Vec<D> w;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double sb = b_(b, i);
+#pragma unroll
+    for (int k = 0; k < D; ++k) sb = fma(A_(b, i, k), x[k][0], sb);
+    o[(OB + i) * SST] = sb;
+    double sw = e_(b, i);
+#pragma unroll
+    for (int k = 0; k < D; ++k) sw = fma(-J_(b, i, k), x[k][0], sw);
+    w[i] = sw;
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) s = fma(F_(k, i), w[k], s);
+    o[(OE + i) * SST] = s;
+  }
+  // A_b M^{-1} Q column by column into o's A block; C = that A_b^T + C_b
+#pragma unroll 1
+  for (int j = 0; j < D; ++j) {
+    double y[D][1];
+#pragma unroll
+    for (int i = 0; i < D; ++i) y[i][0] = Q_(i, j);
+    lu_solve<D, 1>(M, perm, invd, y);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) t = fma(A_(b, i, k), y[k][0], t);
+      o[(OA + i * D + j) * SST] = t;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = i; j < D; ++j) {
+      double s = C_(b, i, j);
+#pragma unroll
+      for (int k = 0; k < D; ++k) s = fma(A_(o, i, k), A_(b, j, k), s);
+      o[(OC + pidx<D>(i, j)) * SST] = s;
+    }
+  // A = A_b M^{-1} F and U = J_b M^{-1} F column by column; J = F^T U
+#pragma unroll 1
+  for (int j = 0; j < D; ++j) {
+    double y[D][1];
+#pragma unroll
+    for (int i = 0; i < D; ++i) y[i][0] = F_(i, j);
+    lu_solve<D, 1>(M, perm, invd, y);
+    Vec<D> u;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      double s = 0.0, q = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) { s = fma(A_(b, i, k), y[k][0], s); q = fma(J_(b, i, k), y[k][0], q); }
+      o[(OA + i * D + j) * SST] = s;
+      u[i] = q;
+    }
+#pragma unroll
+    for (int i = 0; i <= j; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) s = fma(F_(k, i), u[k], s);
+      o[(OJ + pidx<D>(i, j)) * SST] = s;
+    }
+  }
+  return ok;
+}
+
 // A filter state (x, P) -- a prefix aggregate, which has A = 0, eta = 0, J = 0
 // because it contains the first step -- combined with an aggregate b:
 //   M = I + P J_b,  x' = A_b M^{-1} (x + P eta_b) + b_b,
