@@ -269,3 +269,44 @@ def test_step_count_bound(lib):
     assert lib.pssgp_workspace_size(6, 1 << 40) > 0
     assert lib.pssgp_workspace_size(6, (1 << 40) + 1) == 0
     assert lib.pssgp_workspace_size_grad(6, (1 << 41)) == 0
+
+
+def test_split_series_argument_errors(lib):
+    """The split-series calls reject bad arguments on the host before any
+    launch (dummy pointers are never dereferenced); the gradient mode of the
+    filter calls asks for the gradient's workspace."""
+    import ctypes
+    fake = ctypes.c_void_p(256)
+    mm = P.build_model("rbf", 1.0, 1.0)
+    m = ctypes.byref(mm.raw)
+    EINVAL, EWS = -1, -4
+    nan, inf = float("nan"), float("inf")
+    assert lib.pssgp_split_agg_doubles(6, 0) == 2 * 36 + 18 and lib.pssgp_split_agg_doubles(6, 1) == 36 + 6 + 21
+    assert lib.pssgp_split_agg_doubles(0, 0) == 0 and lib.pssgp_split_agg_doubles(9, 1) == 0
+    n = 1000
+    big = 1 << 34
+    small_grad = lib.pssgp_workspace_size(6, n)
+    assert lib.pssgp_workspace_size_grad(6, n) > small_grad
+    red = lambda *a: lib.pssgp_split_filter_reduce(m, fake, fake, fake, fake, 0, *a)
+    assert red(n, nan, nan, 3, fake, fake, big, None) == EINVAL            # mode outside 0..2
+    assert red(n, inf, nan, 1, fake, fake, big, None) == EINVAL            # an infinite boundary time
+    assert red(n, nan, -inf, 1, fake, fake, big, None) == EINVAL
+    assert red(0, nan, nan, 1, fake, fake, big, None) == EINVAL            # empty chunk
+    assert red(n, nan, nan, 1, None, fake, big, None) == EINVAL            # no output
+    assert red(n, nan, nan, 2, fake, fake, small_grad, None) == EWS        # gradient mode: gradient workspace
+    fin = lambda *a: lib.pssgp_split_filter_finish(m, fake, fake, fake, fake, 0, *a)
+    assert fin(n, nan, 1, fake, 2, 2, None, None, n, None, fake, big, None) == EINVAL   # rank >= G
+    assert fin(n, nan, 1, fake, 0, 0, None, None, n, None, fake, big, None) == EINVAL   # G < 1
+    assert fin(n, nan, 1, None, 2, 0, None, None, n, None, fake, big, None) == EINVAL   # no aggregates
+    assert fin(n, nan, 1, fake, 2, 0, fake, None, n - 1, None, fake, big, None) == EINVAL   # ld < n
+    assert fin(n, nan, 2, fake, 2, 0, None, None, n, None, fake, small_grad, None) == EWS
+    assert lib.pssgp_split_smooth_reduce(m, 0, fake, fake, big, None) == EINVAL
+    assert lib.pssgp_split_smooth_finish(m, n, n, fake, 3, 3, None, None, None, None, fake, big, None) == EINVAL
+    assert lib.pssgp_split_grad_mean_reduce(m, n, None, fake, big, None) == EINVAL
+    assert lib.pssgp_split_grad_mean_reduce(m, n, fake, fake, small_grad, None) == EWS
+    assert lib.pssgp_split_grad_mean_finish(m, n, fake, 2, 2, fake, fake, big, None) == EINVAL
+    assert lib.pssgp_split_grad_mean_finish(m, n, fake, 2, 1, None, fake, big, None) == EINVAL
+    assert lib.pssgp_split_grad_finish(m, None, 0, n, fake, 2, 1, fake, fake, big, None) == EINVAL   # no R
+    assert lib.pssgp_split_grad_finish(m, fake, 0, n, fake, 2, 1, None, fake, big, None) == EINVAL   # no grad
+    assert lib.pssgp_split_grad_finish(m, fake, 0, n, fake, 2, -1, fake, fake, big, None) == EINVAL
+    assert lib.pssgp_split_grad_finish(m, fake, 0, n, fake, 2, 1, fake, fake, small_grad, None) == EWS
