@@ -397,6 +397,41 @@ def test_deterministic():
     assert a[2] == b[2]
 
 
+def test_concurrent_predictions_on_streams_equal_serial_ones():
+    """Eight predictions of different series in flight on eight streams, each
+    with its own workspace, at the benchmark's concurrent tuning (2 warps per
+    SM): every result equals, bit for bit, the same prediction run alone on
+    one stream (no state shared between calls)."""
+    m = P.build_model("rbf", 1.0, 1.0)
+    series = [wl.prefix(wl.sinusoid_large(seed=40 + i), 60_000 + 997 * i) for i in range(8)]
+    ins = [(dev(s.t_train), dev(s.y_train), dev(s.t_test)) for s in series]
+    with _tuning(m.d, 2):
+        ref = []
+        for tt, yy, ts in ins:
+            mean, var, ll, ws = P.predict(m, tt, yy, ts, 0.01)
+            assert P.status(ws) == 0
+            ref.append((host(mean), host(var), float(host(ll)[0])))
+        streams = [torch.cuda.Stream() for _ in ins]
+        wss = [P.workspace(m.d, s.N + s.M) for s in series]
+        outs = [None] * len(ins)
+        cur = torch.cuda.current_stream()
+        for rep in range(2):
+            for i, ((tt, yy, ts), st) in enumerate(zip(ins, streams)):
+                st.wait_stream(cur)
+                with torch.cuda.stream(st):
+                    outs[i] = P.predict(m, tt, yy, ts, 0.01, ws=wss[i])
+            for st in streams:
+                cur.wait_stream(st)
+            torch.cuda.synchronize()
+            for i, (mean, var, ll, ws) in enumerate(outs):
+                assert P.status(ws) == 0
+                np.testing.assert_array_equal(host(mean), ref[i][0])
+                np.testing.assert_array_equal(host(var), ref[i][1])
+                assert float(host(ll)[0]) == ref[i][2]
+    fm, fv, res, _ = oracle_predict("rbf", series[3], 0.01)
+    check_marginals(ref[3][0], ref[3][1], ref[3][2], fm, fv, res.loglik, series[3].N, TOL["rbf"], "concurrent/rbf")
+
+
 def test_user_sde_with_scaled_measurement_row():
     """y = h0 x_0 + e with h0 = 2 (pssgp_model_from_sde): f = H x, so the
     marginals are those of the oracle run with the same H."""
