@@ -432,6 +432,7 @@ def batched_bench(args, P, wl, dev, barrier, world, rank):
     per = P.timing(2)
     P.timing(0)
     n_all = sum(d["n"] for d in parts)
+    pred = batched_predict_bench(args, P, parts, dev, barrier, world)
     return {"workload": "4,096 series, lengths log-uniform [1000, 65536], Matern-3/2 / 5/2 mixed, l log-uniform "
                         "[0.1, 10], s2 = 1, R log-uniform [1e-3, 1e-1], times and y drawn from the SSGP prior of "
                         "each series (Poisson grid of mean spacing 0.01, pssgp_simulate_prior); log-likelihood of "
@@ -440,7 +441,57 @@ def batched_bench(args, P, wl, dev, barrier, world, rank):
             "series_per_s": job_throughput(B_all, world, ms), "steps_per_s": job_throughput(n_all, world, ms),
             "tuning": tuning, "gpu_launches_per_eval": int(sum(c for _, c in per.values())),
             "kernels_ms": {k: round(v[0], 4) for k, v in per.items()},
-            "l2": "inputs and workspace ~17 GB per evaluation, far above the 126 MB L2"}
+            "l2": "inputs and workspace ~17 GB per evaluation, far above the 126 MB L2",
+            "predict": pred}
+
+
+def batched_predict_bench(args, P, parts, dev, barrier, world):
+    """Posterior predictions of the same 4,096 series in one pssgp_predict_batched
+    call per family: a prediction time midway between the training times k and
+    k + 1 for every k = 50 mod 100 of each series (1 % of its steps, at least
+    one), merged, filtered and smoothed with each series' log-likelihood."""
+    import torch
+    legs = []
+    for d in parts:
+        off = d["off"].cpu().numpy()
+        idx, uo = [], [0]
+        for s in range(off.size - 1):
+            a, b = int(off[s]), int(off[s + 1])
+            ks = np.arange(a + 50, b - 1, 100) if b - a > 51 else np.array([a] if b - a > 1 else [], dtype=np.int64)
+            idx.append(ks)
+            uo.append(uo[-1] + ks.size)
+        idx_d = torch.as_tensor(np.concatenate(idx).astype(np.int64), device=dev)
+        u = 0.5 * (d["t"][idx_d] + d["t"][idx_d + 1])
+        uoff = torch.as_tensor(np.array(uo, dtype=np.int64), device=dev)
+        ws = P._empty(int(P.lib().pssgp_predict_batched_workspace_size(d["m"].d, d["n"], u.numel(), d["B"])),
+                      dtype=torch.uint8, device=dev)
+        legs.append((d, u, uoff, ws))
+
+    def call():
+        for d, u, uoff, ws in legs:
+            P.predict_batched(d["m"], d["off"], uoff, d["par"], d["t"], d["y"], u, ws=ws)
+
+    for _ in range(max(args.warmup, 3)):
+        call()
+    torch.cuda.synchronize()
+    assert all(P.status(ws) == 0 for _, _, _, ws in legs), "device status error (batched prediction)"
+    barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        call()
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    B_all = sum(d["B"] for d, *_ in legs)
+    n_all = sum(d["n"] + u.numel() for d, u, *_ in legs)
+    return {"what": "posterior mean and variance at 1 % of each series' steps (between training times 50 mod 100) "
+                    "and every series' log-likelihood, one pssgp_predict_batched call per family",
+            "prediction_times": int(sum(u.numel() for _, u, *_ in legs)), "merged_steps": int(n_all),
+            "ms_per_call": ms, "series_per_s": job_throughput(B_all, world, ms),
+            "steps_per_s": job_throughput(n_all, world, ms)}
 
 
 def gradient_bench(args, P, wl, dev, sm_mhz=None):

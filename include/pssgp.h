@@ -236,6 +236,40 @@ int pssgp_loglik_batched(const pssgp_model* model, const int64_t* offsets,
                          double* loglik, void* ws, size_t ws_bytes,
                          void* stream);
 
+/* Posterior predictions of a batch of B independent series in one pass
+ * (Sec. 4.3 per series: each series' prediction times merged into its
+ * training times as missing measurements, then filter, smoother and
+ * log-likelihood over the concatenation, as pssgp_predict for one series).
+ *  - Series s: training times/values t_train, y_train at
+ *    train_offsets[s] .. train_offsets[s+1]-1 (device arrays of length N)
+ *    and prediction times t_test at test_offsets[s] .. test_offsets[s+1]-1
+ *    (length M); both sorted within each series.  Offsets: device
+ *    int64[B + 1], starting at 0, non-decreasing, ending at N (M).  A series
+ *    may have no training or no prediction times (no training times: the
+ *    prior at its prediction times).
+ *  - params, model: as pssgp_loglik_batched (per series lengthscale,
+ *    variance, noise variance R; the model of the family carries where it
+ *    was built).
+ *  - Outputs (device): mean_test, var_test: double[M], the posterior mean
+ *    and variance of f at each prediction time, in the order of t_test;
+ *    loglik (nullable): double[B], each series' log marginal likelihood.
+ *  - Ties: a training time equal to a prediction time goes first.
+ *  - Failed series (as pssgp_loglik_batched, and decreasing or non-finite
+ *    training or prediction times): NaN outputs and loglik; the other series
+ *    are not affected.  Bad offsets: PSSGP_EBATCH in the status word.
+ *  - ws: pssgp_predict_batched_workspace_size(d, N, M, B) bytes (0 for
+ *    arguments out of range). */
+size_t pssgp_predict_batched_workspace_size(int32_t d, int64_t N, int64_t M,
+                                            int32_t B);
+int pssgp_predict_batched(const pssgp_model* model,
+                          const int64_t* train_offsets,
+                          const int64_t* test_offsets, int32_t B,
+                          const double* params, const double* t_train,
+                          const double* y_train, int64_t N,
+                          const double* t_test, int64_t M, double* mean_test,
+                          double* var_test, double* loglik, void* ws,
+                          size_t ws_bytes, void* stream);
+
 /* ---- gradient of the log marginal likelihood ------------------------------ */
 /* d loglik / d(log lengthscale, log variance, log noise variance) by adjoint
  * (reverse-mode) scans: the filter pass stores the predicted moments, then

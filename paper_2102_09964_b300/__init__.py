@@ -132,6 +132,10 @@ def lib():
         L.pssgp_split_grad_mean_finish.argtypes = [ctypes.POINTER(PssgpModel), i64, vp, i32, i32, vp, vp, sz, vp]
         L.pssgp_split_grad_finish.argtypes = [ctypes.POINTER(PssgpModel), vp, i32, i64, vp, i32, i32, vp, vp, sz,
                                               vp]
+        L.pssgp_predict_batched_workspace_size.restype = sz
+        L.pssgp_predict_batched_workspace_size.argtypes = [i32, i64, i64, i32]
+        L.pssgp_predict_batched.argtypes = [ctypes.POINTER(PssgpModel), vp, vp, i32, vp, vp, vp, i64, vp, i64, vp, vp,
+                                            vp, vp, sz, vp]
         L.pssgp_mlp_set_gemm.argtypes = [i32]
         L.pssgp_debug_gemm_bf16.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, vp]
         L.pssgp_timing_name.argtypes = [i32]
@@ -441,6 +445,33 @@ def predict(model: Model, t_train, y_train, t_test, R: float, ws=None, out=None,
                              _ptr(mean), _ptr(var), _ptr(ll) if with_loglik else None, _ptr(ws), ws.numel(),
                              _stream())
     _check(rc, "pssgp_predict")
+    return mean, var, ll, ws
+
+
+def predict_batched(model: Model, train_offsets, test_offsets, params, t_train, y_train, t_test, ws=None,
+                    with_loglik=True):
+    """Posterior mean and variance at the prediction times of B series, and
+    each series' log-likelihood, in one pass (pssgp_predict_batched).  Offsets:
+    device int64[B + 1] into the training (t_train, y_train) and prediction
+    (t_test) arrays; params: device float64[B, 3] (lengthscale, variance,
+    noise variance).  Returns (mean[M], var[M], loglik[B] or None, ws)."""
+    dev = t_train.device if t_train.numel() else t_test.device
+    B = train_offsets.numel() - 1
+    N, M = t_train.numel(), t_test.numel()
+    for o in (train_offsets, test_offsets):
+        if o.dtype != torch.int64 or not o.is_contiguous():
+            raise PssgpError("offsets must be contiguous int64")
+    params = params.contiguous()
+    if ws is None:
+        ws = _empty(int(lib().pssgp_predict_batched_workspace_size(model.d, N, M, B)), dtype=torch.uint8,
+                    device=dev)
+    mean = _empty(M, dtype=torch.float64, device=dev)
+    var = _empty(M, dtype=torch.float64, device=dev)
+    ll = _empty(B, dtype=torch.float64, device=dev) if with_loglik else None
+    rc = lib().pssgp_predict_batched(ctypes.byref(model.raw), _ptr(train_offsets), _ptr(test_offsets), B,
+                                     _ptr(params), _ptr(t_train), _ptr(y_train), N, _ptr(t_test), M, _ptr(mean),
+                                     _ptr(var), _ptr(ll), _ptr(ws), ws.numel(), _stream())
+    _check(rc, "pssgp_predict_batched")
     return mean, var, ll, ws
 
 

@@ -2004,6 +2004,95 @@ __global__ void k_gather(const double* src_m, const double* src_v, const int64_t
   ov[j] = src_v[p];
 }
 
+// ---------------------------------------------------------------------------
+// batched prediction: B series, series s with training times/values
+// [toff_s, toff_{s+1}) and prediction times [uoff_s, uoff_{s+1}); merged
+// series s occupies [toff_s + uoff_s, toff_{s+1} + uoff_{s+1}) (Sec. 4.3 per
+// series: prediction times as missing measurements)
+// ---------------------------------------------------------------------------
+__global__ void k_merged_offsets(const int64_t* toff, const int64_t* uoff, int B, int64_t* mo) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s <= B) mo[s] = toff[s] + uoff[s];
+}
+
+// each element's merged position by its rank within its series (training
+// before prediction at equal times, as k_merge): a training time goes after
+// the prediction times strictly before it, a prediction time after the
+// training times at or before it.  Positions stay inside the series' range;
+// an element whose series range is invalid is not written (PSSGP_EBATCH).
+// Non-finite or decreasing times flag the series (sf at its first merged
+// step; its outputs become NaN).
+__global__ void __launch_bounds__(BLOCK) k_merge_batched(const int64_t* toff, const int64_t* uoff, int B,
+                                                         const double* A, const double* yA, int64_t N,
+                                                         const double* Bt, int64_t M, double* t, double* y,
+                                                         uint8_t* mask, int64_t* tpos, int* sf, int* status) {
+  const int64_t idx = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (idx >= N + M) return;
+  const bool train = idx < N;
+  const int64_t e = train ? idx : idx - N;
+  const int64_t* off = train ? toff : uoff;
+  int lo = 0, hi = B;                      // last s with off[s] <= e
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= e) lo = mid; else hi = mid;
+  }
+  const int s = lo;
+  const int64_t a0 = toff[s], a1 = toff[s + 1], b0 = uoff[s], b1 = uoff[s + 1];
+  if (!(a0 >= 0 && a0 <= a1 && a1 <= N && b0 >= 0 && b0 <= b1 && b1 <= M) ||
+      !(train ? (a0 <= e && e < a1) : (b0 <= e && e < b1))) {
+    flag(status, PSSGP_EBATCH);
+    return;
+  }
+  const int64_t base = a0 + b0;
+  const double v = train ? A[e] : Bt[e];
+  const long long kv = okey(v);
+  int64_t pos;
+  if (train) {
+    int64_t l = b0, h = b1;
+    while (l < h) {
+      const int64_t m = (l + h) >> 1;
+      if (okey(Bt[m]) < kv) l = m + 1; else h = m;
+    }
+    pos = base + (e - a0) + (l - b0);
+  } else {
+    int64_t l = a0, h = a1;
+    while (l < h) {
+      const int64_t m = (l + h) >> 1;
+      if (okey(A[m]) <= kv) l = m + 1; else h = m;
+    }
+    pos = base + (e - b0) + (l - a0);
+  }
+  int bits = 0;
+  if (nonfinite(v)) bits |= PSSGP_ENAN;
+  const int64_t eend = train ? a1 : b1;
+  if (e + 1 < eend && okey((train ? A : Bt)[e + 1]) < kv) bits |= PSSGP_EUNSORTED;
+  t[pos] = v;
+  y[pos] = train ? yA[e] : 0.0;
+  mask[pos] = train ? 1 : 0;
+  if (!train) tpos[e] = pos;
+  if (bits) {
+    atomicOr(sf + base, bits);
+    flag(status, bits);
+  }
+}
+
+// outputs at the prediction times; NaN for the prediction times of a flagged series
+__global__ void k_gather_batched(const double* src_m, const double* src_v, const int64_t* pos,
+                                 const int64_t* uoff, const int64_t* mo, int B, const int* sf, int64_t M,
+                                 double* om, double* ov) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  int lo = 0, hi = B;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (uoff[mid] <= j) lo = mid; else hi = mid;
+  }
+  const bool bad = sf[mo[lo]] != 0;
+  const int64_t p = pos[j];
+  om[j] = bad ? NAN : src_m[p];
+  ov[j] = bad ? NAN : src_v[p];
+}
+
 // FP64 FMA rate probe: four independent dependent chains per thread
 __global__ void k_dfma_probe(double* out, int iters) {
   double a[8];
@@ -2100,6 +2189,7 @@ struct BatchArgs {
   double* sq;
   double* sr;
   int* sf;                  // [n]: error bits of every series at its first step (0: the series is fine)
+  bool scales_ready = false;  // the per-series table is already made (k_series_scales ran)
 };
 
 // the buffer that holds the final level-2 result: the rounds alternate
@@ -2117,7 +2207,7 @@ template <int D>
 void run_filter_front(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s, const BatchArgs* bt,
                       bool ll_only) {
   const int grid = (int)(p.P0 / BLOCK);
-  if (bt) {
+  if (bt && !bt->scales_ready) {
     Timed tm(s, T_DISC);
     k_series_scales<<<(unsigned)((bt->B + 127) / 128), 128, 0, s>>>(bt->ell0, bt->var0, bt->offsets, bt->B,
                                                                      bt->params, p.n, bt->su, bt->sq, bt->sr,
@@ -2398,6 +2488,110 @@ extern "C" int pssgp_loglik_batched(const pssgp_model* model, const int64_t* off
     Timed tm(s, T_LL);
     k_segment_pieces<<<segment_grid(B), 32 * SEG_WARPS, 0, s>>>(a.ll_step, 1, n, p.L, offsets, B, loglik, 1,
                                                                 bt.sf);
+    after_launch();
+  }
+  return end_call();
+}
+
+// batched prediction: the scan plan of the merged batch (the size for every
+// tuning), then the merged offsets [B + 1] and the per-series table
+// (k_series_scales: uscale, qscale, R, flags at each series' first merged step)
+namespace {
+struct PredBatchLayout {
+  int64_t o_mo, o_su, o_sq, o_sr, o_sf, total;
+};
+PredBatchLayout pred_batch_layout(int d, int64_t n, int B) {
+  PredBatchLayout l;
+  int64_t o = make_plan(d, n, 0, WARPS_MAX).total;
+  l.o_mo = o; o += align256(((int64_t)B + 1) * 8);
+  l.o_su = o; o += align256(n * 8);
+  l.o_sq = o; o += align256(n * 8);
+  l.o_sr = o; o += align256(n * 8);
+  l.o_sf = o; o += align256(n * 4);
+  l.total = o;
+  return l;
+}
+}  // namespace
+
+extern "C" size_t pssgp_predict_batched_workspace_size(int32_t d, int64_t N, int64_t M, int32_t B) {
+  if (d < 1 || d > PSSGP_DMAX || N < 0 || M < 0 || B < 1 || N + M < 1 || N + M > PSSGP_NMAX) return 0;
+  return (size_t)pred_batch_layout(d, N + M, B).total;
+}
+
+extern "C" int pssgp_predict_batched(const pssgp_model* model, const int64_t* train_offsets,
+                                     const int64_t* test_offsets, int32_t B, const double* params,
+                                     const double* t_train, const double* y_train, int64_t N, const double* t_test,
+                                     int64_t M, double* mean_test, double* var_test, double* loglik, void* ws,
+                                     size_t ws_bytes, void* stream) {
+  begin_call();
+  if (!model_ok(model) || !train_offsets || !test_offsets || !params || B < 1 || N < 0 || M < 0 || N + M < 1 ||
+      N + M > PSSGP_NMAX || (N > 0 && (!t_train || !y_train)) || (M > 0 && (!t_test || !mean_test || !var_test)))
+    return PSSGP_EINVAL;
+  const double ell0 = model->lengthscale, var0 = model->variance;
+  if (!(ell0 > 0.0) || !(var0 > 0.0) || !std::isfinite(ell0) || !std::isfinite(var0)) return PSSGP_EMODEL;
+  const int64_t n = N + M;
+  const Plan p = make_plan(model->d, n, 0);
+  const PredBatchLayout lay = pred_batch_layout(model->d, n, B);
+  if (!ws) return PSSGP_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0 || (int64_t)ws_bytes < lay.total) return PSSGP_EWORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScanArgs a = base_args(p, ws);
+  double* t = reinterpret_cast<double*>(ws_ptr(ws, p.o_t));
+  double* y = reinterpret_cast<double*>(ws_ptr(ws, p.o_y));
+  uint8_t* mask = reinterpret_cast<uint8_t*>(ws_ptr(ws, p.o_mask));
+  int64_t* tpos = reinterpret_cast<int64_t*>(ws_ptr(ws, p.o_tpos));
+  double* fmean = reinterpret_cast<double*>(ws_ptr(ws, p.o_fmean));
+  double* fvar = reinterpret_cast<double*>(ws_ptr(ws, p.o_fvar));
+  int64_t* mo = reinterpret_cast<int64_t*>(ws_ptr(ws, lay.o_mo));
+  BatchArgs bt;
+  bt.ell0 = ell0; bt.var0 = var0; bt.offsets = mo; bt.B = B; bt.params = params;
+  bt.Rstep = reinterpret_cast<double*>(ws_ptr(ws, p.o_rstep));
+  bt.seg = reinterpret_cast<uint8_t*>(ws_ptr(ws, p.o_seg));
+  bt.su = reinterpret_cast<double*>(ws_ptr(ws, lay.o_su));
+  bt.sq = reinterpret_cast<double*>(ws_ptr(ws, lay.o_sq));
+  bt.sr = reinterpret_cast<double*>(ws_ptr(ws, lay.o_sr));
+  bt.sf = reinterpret_cast<int*>(ws_ptr(ws, lay.o_sf));
+  bt.scales_ready = true;
+  // times and mask are cleared first: the merge leaves gaps only in a series
+  // whose times are not sorted (flagged, NaN outputs), and a gap must read as
+  // a missing step at time 0 (a decreasing time, which the discretisation
+  // turns into a zero-length step) whatever stale bytes it held, so that
+  // nothing non-finite can reach the other series
+  if (cudaMemsetAsync(a.status, 0, sizeof(int), s) != cudaSuccess ||
+      cudaMemsetAsync(mask, 0, (size_t)n, s) != cudaSuccess ||
+      cudaMemsetAsync(t, 0, (size_t)n * 8, s) != cudaSuccess)
+    return PSSGP_ECUDA;
+  {
+    Timed tm(s, T_MERGE);
+    k_merged_offsets<<<(unsigned)((B + 1 + 255) / 256), 256, 0, s>>>(train_offsets, test_offsets, B, mo);
+    after_launch();
+    k_series_scales<<<(unsigned)((B + 127) / 128), 128, 0, s>>>(ell0, var0, mo, B, params, n, bt.su, bt.sq, bt.sr,
+                                                                 bt.sf, a.status);
+    after_launch();
+    k_merge_batched<<<(unsigned)((n + BLOCK - 1) / BLOCK), BLOCK, 0, s>>>(
+        train_offsets, test_offsets, B, t_train, y_train, N, t_test, M, t, y, mask, tpos, bt.sf, a.status);
+    after_launch();
+  }
+  a.t = t; a.y = y; a.mask = mask; a.R = bt.Rstep; a.R_per_step = 1;
+  a.fuse_smoother = 1;
+  a.seg_start = bt.seg;
+  a.ll_step = reinterpret_cast<double*>(ws_ptr(ws, p.o_llstep));
+  a.f_mean = fmean; a.f_var = fvar;
+  a.ld = n;
+  PSSGP_DISPATCH(model->d, {
+    const DevModel<D> m = dev_model<D>(model);
+    run_filter<D>(m, p, a, s, &bt);
+    run_smoother_tail<D>(m, p, a, s);
+  });
+  if (M > 0) {
+    Timed tm(s, T_GATHER);
+    k_gather_batched<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(fmean, fvar, tpos, test_offsets, mo, B, bt.sf, M,
+                                                                  mean_test, var_test);
+    after_launch();
+  }
+  if (loglik) {
+    Timed tm(s, T_LL);
+    k_segment_pieces<<<segment_grid(B), 32 * SEG_WARPS, 0, s>>>(a.ll_step, 1, n, p.L, mo, B, loglik, 1, bt.sf);
     after_launch();
   }
   return end_call();
