@@ -891,6 +891,10 @@ __global__ void __launch_bounds__(BLOCK) k_filter_ks(const double* in, double* o
                                                      int* status) {
   constexpr int NF = FAggSize<D>::N;
   __shared__ double sm[BLOCK / 32][WarpFilterSmem<D>::N];
+  // programmatic dependent launch (level2_launch): wait for the previous
+  // grid's results; the next round may be scheduled meanwhile
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * (BLOCK / 32) + wid;
   if (i >= P2) return;                       // whole warp
@@ -1364,6 +1368,8 @@ template <int D>
 __global__ void __launch_bounds__(BLOCK) k_smoother_ks(const double* in, double* out, int64_t P2, int64_t off) {
   constexpr int NS = SAggSize<D>::N;
   __shared__ double sm[BLOCK / 32][WarpSmootherSmem<D>::N];
+  asm volatile("griddepcontrol.wait;" ::: "memory");   // as in k_filter_ks
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * (BLOCK / 32) + wid;
   if (i >= P2) return;
@@ -2149,6 +2155,24 @@ ScanArgs base_args(const Plan& p, void* ws) {
   return a;
 }
 
+// a level-2 round, launched so that it may be scheduled while the grid
+// before it drains (programmatic dependent launch; the kernels start with
+// griddepcontrol.wait, so nothing is read before that grid has finished)
+template <typename... KArgs, typename... Args>
+void level2_launch(void (*kern)(KArgs...), int grid, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(BLOCK);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // level-2 rounds; returns the buffer that holds the final inclusive result
 template <int D>
 const double* run_filter_level2(const Plan& p, double* buf0, int* status, cudaStream_t s) {
@@ -2157,7 +2181,7 @@ const double* run_filter_level2(const Plan& p, double* buf0, int* status, cudaSt
   const int grid = (int)((p.P2 + BLOCK / 32 - 1) / (BLOCK / 32));
   for (int64_t off = 1; off < p.P2; off <<= 1) {
     Timed tm(s, T_FL2);
-    k_filter_ks<D><<<grid, BLOCK, 0, s>>>(in, out, p.P2, off, status);
+    level2_launch(k_filter_ks<D>, grid, s, (const double*)in, out, p.P2, off, status);
     after_launch();
     std::swap(in, out);
   }
@@ -2170,7 +2194,7 @@ const double* run_smoother_level2(const Plan& p, double* buf0, cudaStream_t s) {
   const int grid = (int)((p.P2 + BLOCK / 32 - 1) / (BLOCK / 32));
   for (int64_t off = 1; off < p.P2; off <<= 1) {
     Timed tm(s, T_SL2);
-    k_smoother_ks<D><<<grid, BLOCK, 0, s>>>(in, out, p.P2, off);
+    level2_launch(k_smoother_ks<D>, grid, s, (const double*)in, out, p.P2, off);
     after_launch();
     std::swap(in, out);
   }
@@ -2299,7 +2323,7 @@ void run_grad(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s, 
     const int g2 = (int)((p.P2 + BLOCK / 32 - 1) / (BLOCK / 32));
     for (int64_t off = 1; off < p.P2; off <<= 1) {
       Timed tm(s, T_AL2);
-      k_smoother_ks<D><<<g2, BLOCK, 0, s>>>(in, out, p.P2, off);
+      level2_launch(k_smoother_ks<D>, g2, s, (const double*)in, out, p.P2, off);
       after_launch();
       std::swap(in, out);
     }
@@ -2317,7 +2341,7 @@ void run_grad(const DevModel<D>& m, const Plan& p, ScanArgs& a, cudaStream_t s, 
     const int g2 = (int)((p.P2 + BLOCK / 32 - 1) / (BLOCK / 32));
     for (int64_t off = 1; off < p.P2; off <<= 1) {
       Timed tm(s, T_AL2);
-      k_smoother_ks<D><<<g2, BLOCK, 0, s>>>(in, out, p.P2, off);
+      level2_launch(k_smoother_ks<D>, g2, s, (const double*)in, out, p.P2, off);
       after_launch();
       std::swap(in, out);
     }
