@@ -449,12 +449,13 @@ def predict(model: Model, t_train, y_train, t_test, R: float, ws=None, out=None,
 
 
 def predict_batched(model: Model, train_offsets, test_offsets, params, t_train, y_train, t_test, ws=None,
-                    with_loglik=True):
+                    with_loglik=True, out=None):
     """Posterior mean and variance at the prediction times of B series, and
     each series' log-likelihood, in one pass (pssgp_predict_batched).  Offsets:
     device int64[B + 1] into the training (t_train, y_train) and prediction
     (t_test) arrays; params: device float64[B, 3] (lengthscale, variance,
-    noise variance).  Returns (mean[M], var[M], loglik[B] or None, ws)."""
+    noise variance); out: optional (mean[M], var[M], loglik[B]) buffers
+    (needed inside a Graph capture).  Returns (mean, var, loglik or None, ws)."""
     dev = t_train.device if t_train.numel() else t_test.device
     B = train_offsets.numel() - 1
     N, M = t_train.numel(), t_test.numel()
@@ -465,9 +466,12 @@ def predict_batched(model: Model, train_offsets, test_offsets, params, t_train, 
     if ws is None:
         ws = _empty(int(lib().pssgp_predict_batched_workspace_size(model.d, N, M, B)), dtype=torch.uint8,
                     device=dev)
-    mean = _empty(M, dtype=torch.float64, device=dev)
-    var = _empty(M, dtype=torch.float64, device=dev)
-    ll = _empty(B, dtype=torch.float64, device=dev) if with_loglik else None
+    if out is not None:
+        mean, var, ll = out
+    else:
+        mean = _empty(M, dtype=torch.float64, device=dev)
+        var = _empty(M, dtype=torch.float64, device=dev)
+        ll = _empty(B, dtype=torch.float64, device=dev) if with_loglik else None
     rc = lib().pssgp_predict_batched(ctypes.byref(model.raw), _ptr(train_offsets), _ptr(test_offsets), B,
                                      _ptr(params), _ptr(t_train), _ptr(y_train), N, _ptr(t_test), M, _ptr(mean),
                                      _ptr(var), _ptr(ll), _ptr(ws), ws.numel(), _stream())

@@ -166,3 +166,31 @@ def test_batched_prediction_large_batch_sampled(report):
         worst = max(worst, check_series("matern52", s, sub.offsets, uoff, sub.params(), sub.t, sub.y, u, mean, var,
                                         ll, report, "large"))
     report("batched prediction, 2,048-series Matern-5/2 batch, sampled series vs oracle", worst, 1e-9)
+
+
+def test_batched_prediction_replays_from_a_cuda_graph():
+    """The call captured once (P.Graph) and replayed gives the direct call's
+    outputs bit for bit, also after the per-series parameters change in
+    place between replays."""
+    n_train = [400, 0, 900, 33]
+    n_test = [40, 3, 9, 1]
+    toff, uoff, params, t, y, u = make_batch(75, n_train, n_test)
+    m = P.build_model("matern52", 1.0, 1.0)
+    to, uo, pa = dev(toff, torch.int64), dev(uoff, torch.int64), dev(params)
+    tt, yy, uu = dev(t), dev(y), dev(u)
+    mean0, var0, ll0, ws = P.predict_batched(m, to, uo, pa, tt, yy, uu)
+    assert P.status(ws) == 0
+    ref = [(mean0.clone(), var0.clone(), ll0.clone())]
+    mean, var, ll = torch.empty_like(mean0), torch.empty_like(var0), torch.empty_like(ll0)
+    g = P.Graph()
+    with g:
+        P.predict_batched(m, to, uo, pa, tt, yy, uu, ws=ws, out=(mean, var, ll))
+    g.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(mean, ref[0][0]) and torch.equal(var, ref[0][1]) and torch.equal(ll, ref[0][2])
+    pa.mul_(1.5)                                    # new hyperparameters, same buffers
+    g.launch()
+    torch.cuda.synchronize()
+    m2, v2, l2, ws2 = P.predict_batched(m, to, uo, pa, tt, yy, uu)
+    assert torch.equal(mean, m2) and torch.equal(var, v2) and torch.equal(ll, l2)
+    assert not torch.equal(mean, ref[0][0])
