@@ -32,7 +32,7 @@ import workloads as wl
 pytestmark = pytest.mark.gpu
 
 TOL = {"matern12": 1e-8, "matern32": 1e-8, "matern52": 1e-8, "rbf": 1e-6}
-# the log-likelihood itself: |d loglik| <= tol * max(|loglik|, n_obs) (reading r13)
+# the log-likelihood itself: |d loglik| <= tol * max(|loglik|, n_obs)
 LLTOL = {"matern12": 1e-9, "matern32": 1e-9, "matern52": 1e-9, "rbf": 1e-6}
 
 

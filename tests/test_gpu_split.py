@@ -119,7 +119,8 @@ def test_split_filter_states_equal_the_unsplit_filter(kind, report):
         worst = max(worst, dx, dP)
     report(f"split filter states vs unsplit library filter, {kind}", worst, 1e-9)
     assert worst <= 1e-9
-    # log-likelihood only (no per-step outputs, no smoother): the chunk sums of reading r21
+    # log-likelihood only (no per-step outputs, no smoother): the per-chunk closed form (each
+    # chunk's terms given the state 0 before it, corrected by the Gaussian integral over that state)
     tot = 0.0
     nan = float("nan")
     ends = [(nan if r == 0 else float(t[bounds[r - 1][1] - 1]), nan if r + 1 == len(bounds) else float(t[b]))
