@@ -37,8 +37,8 @@ METRIC = "filter+smoother time steps/s at N=2^20,d=6 FP64"
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels at the
 # 2^20 workload itself; a launch's traffic is this x n.  Reset an entry to None
 # whenever its kernel changes.
-PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1375.0, "filter_reduce": 477.6, "discretize": 415.3,
-                                "smoother_propagate": 682.8}
+PROFILED_DRAM_BYTES_PER_STEP = {"filter_propagate": 1414.8, "filter_reduce": 478.0, "discretize": 415.4,
+                                "smoother_propagate": 682.3}
 UNIT = "steps/s"
 BATCH_SIM_SEED = 300          # prior simulation of the batched workload (family i: seed + i)
 WORKLOADS = {
