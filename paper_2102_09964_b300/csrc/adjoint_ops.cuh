@@ -74,10 +74,15 @@ __device__ __forceinline__ double load_adj_M(const double* rec, int64_t k, int i
 template <int D>
 __device__ __forceinline__ void load_F(const double* rec, int64_t k, int fqs, Mat<D>& F) {
   const double* p = rec + k * fqs;
+  // 16-byte loads (every record starts on a 16-byte boundary), a scalar tail for odd d * d
+  const double2* q = reinterpret_cast<const double2*>(p);
 #pragma unroll
-  for (int i = 0; i < D; ++i)
-#pragma unroll
-    for (int j = 0; j < D; ++j) F[i][j] = p[i * D + j];
+  for (int e = 0; e + 1 < D * D; e += 2) {
+    const double2 v = q[e / 2];
+    F[e / D][e % D] = v.x;
+    F[(e + 1) / D][(e + 1) % D] = v.y;
+  }
+  if constexpr ((D * D) % 2 == 1) F[D - 1][D - 1] = p[D * D - 1];
 }
 
 // ---------------------------------------------------------------------------
