@@ -125,6 +125,7 @@ struct Plan {
   int64_t L;         // steps per lane
   int warps;         // the tuning the plan was made for (lanes per SM / 32)
   int nf, ns;        // aggregate sizes (doubles)
+  int fnext;         // split series: offset (doubles) of the F/Q record after the chunk in the o_bnd slot
   int fqs, egs;      // per-step record strides (doubles, even)
   // byte offsets into the workspace
   int64_t o_status, o_fq, o_egl, o_laggf, o_waggf, o_laggs, o_waggs, o_llp, o_fmean, o_fvar, o_t, o_y, o_mask,
@@ -173,7 +174,8 @@ Plan make_plan(int d, int64_t n, int64_t lanes_req, int warps = 0, bool grad = f
   p.o_rstep = o; o += align256(n * 8);     // batched: noise variance per step
   p.o_seg = o; o += align256(n);           // batched: 1 at each series' first step
   p.o_llstep = o; o += align256(n * 8);    // batched: log-likelihood pieces per step
-  p.o_bnd = o; o += align256((p.nf + p.fqs) * 8);   // split series: the folded aggregate of the other
+  p.fnext = (p.nf + 1) / 2 * 2;                       // the record after the aggregate, 16-byte aligned
+  p.o_bnd = o; o += align256((p.fnext + p.fqs) * 8);  // split series: the folded aggregate of the other
                                                     // chunks, then the F/Q record of the step after the chunk
   p.o_adj = p.o_tauq = p.o_lpi = p.o_lmbar = p.o_lgj = p.o_gpart = p.o_gstep = -1;
   if (grad) {                                // gradient: forward moments, scan state
@@ -2823,9 +2825,9 @@ extern "C" int pssgp_split_filter_finish(const pssgp_model* model, const double*
   PSSGP_DISPATCH(model->d, {
     const DevModel<D> m = dev_model<D>(model);
     if (grad) {   // the transition after the chunk (zero when the series ends with it)
-      k_discretize_next<D><<<1, 32, 0, s>>>(m, t, n, t_next, bnd + p.nf, a.status);
+      k_discretize_next<D><<<1, 32, 0, s>>>(m, t, n, t_next, bnd + p.fnext, a.status);
       after_launch();
-      a.f_next = bnd + p.nf;
+      a.f_next = bnd + p.fnext;
     }
     if (rank > 0) {   // the filter state before the chunk: chunks 0 .. rank-1 folded
       k_fold_filter_range<D><<<1, 32, 0, s>>>(aggs, 0, rank, bnd, a.status);
@@ -2969,7 +2971,7 @@ extern "C" int pssgp_split_grad_finish(const pssgp_model* model, const double* R
   a.R = R; a.R_per_step = R_per_step;
   a.wfin_a = level2_result(p, a.wagg_a, p.ns);
   double* bnd = reinterpret_cast<double*>(ws_ptr(ws, p.o_bnd));
-  a.f_next = bnd + p.nf;   // written by the filter pass (zero after the series' last chunk)
+  a.f_next = bnd + p.fnext;   // written by the filter pass (zero after the series' last chunk)
   const int grid = (int)(p.P0 / BLOCK);
   PSSGP_DISPATCH(model->d, {
     const DevModel<D> m = dev_model<D>(model);
