@@ -683,11 +683,12 @@ template <int D, int RMODE, bool L1S>
 __global__ void __launch_bounds__(BLOCK, 1) k_filter_reduce(const DevModel<D> m, const ScanArgs a) {
   constexpr int RB = BLOCK;   // threads per block (stride of the per-thread arrays)
   constexpr bool LL = RMODE == RED_LL;
-  // 16-byte record loads (load_record): faster in the gradient's instance and
-  // in every instance with the shared-memory warp scan (prediction 1.948 ->
-  // 1.876 ms at 2^20 RBF-6); with the scan on register/local operands they
-  // cost more register spills than they save
-  constexpr bool VECMODE = RMODE == RED_ADJ || (L1S && (RMODE == RED_SMOOTH || RMODE == RED_LL));
+  // 16-byte record loads (load_record): faster in the gradient's instance, in
+  // every instance with the shared-memory warp scan (prediction 1.948 ->
+  // 1.876 ms at 2^20 RBF-6) and in the prediction's register-scan instance
+  // at d >= 4 (eight concurrent predictions 240.0 -> 240.8 M steps/s); not
+  // in the log-likelihood's instance at d <= 3 (batched: 10.53 -> 10.64 ms)
+  constexpr bool VECMODE = RMODE == RED_ADJ || (D >= 4 && RMODE == RED_SMOOTH) || (L1S && RMODE == RED_LL);
   extern __shared__ double smem[];
   constexpr int NF = FAggSize<D>::N;
   double* sB0 = smem + threadIdx.x;                    // level-1 buffer 0 (shared-memory scan)
