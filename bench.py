@@ -286,6 +286,7 @@ def roofline_peak_fields(measured, nominal, sm_mhz):
 
 
 CPU_SAMPLE_TRAIN = 1 << 19
+REFERENCE_TIMED_S = 120.0     # the reference arm's timed runs stop after about this long
 
 
 def _oracle_sample_run(wl_params, n_sample_train):
@@ -347,18 +348,23 @@ def run_reference(args, wl_params):
     n_full = int(full.N + full.M)       # merged steps of the timed workload (the sample is a prefix)
     d = om.make_model(wl_params["kind"], wl_params["lengthscale"], wl_params["variance"],
                       order=wl_params["order"] or 6).d
+    wdt = 0.0
     for _ in range(max(args.warmup, 1)):
-        _oracle_sample_run(wl_params, CPU_SAMPLE_TRAIN)
+        _, wdt, _ = _oracle_sample_run(wl_params, CPU_SAMPLE_TRAIN)
+    # at most about two minutes of timed runs: K runs of the 2^19-point sample
+    # when they fit, else as many as fit (the value is the best run either way)
+    runs = max(1, min(args.steps, max(3, int(REFERENCE_TIMED_S / max(wdt, 1e-3)))))
     dts = []
-    for _ in range(max(args.steps, 1)):
+    for _ in range(runs):
         n, dt, s = _oracle_sample_run(wl_params, CPU_SAMPLE_TRAIN)
         dts.append(dt)
     v = n / min(dts)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    capped = f" ({args.steps} requested; capped to about {REFERENCE_TIMED_S:.0f} s)" if runs < args.steps else ""
     sample = _oracle_sample_desc(s, n, dts, cores,
-                                 f"best of {len(dts)} timed runs after {max(args.warmup, 1)} warm-up runs")
+                                 f"best of {len(dts)} timed runs{capped} after {max(args.warmup, 1)} warm-up runs")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": min(dts) * 1e3 * n_full / n,
+            "steps": len(dts), "warmup": args.warmup, "ms_per_step": min(dts) * 1e3 * n_full / n,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args.workload, d, n_full),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
